@@ -1,0 +1,361 @@
+"""Benchmark of the seed-location filter on GB300.
+
+Default workload (N=1): 100 Mbp repeat-rich synthetic reference (70% i.i.d.
+ACGT + 30% planted repeat families at 10-20% divergence), q=5, 256 bp bins +
+150 bp overlap; 1M reads of 150 bp (4% substitutions, 1% indels), E=7;
+candidates = bins of all exact 12-mer seed hits from a CPU index, capped at
+1,000 per read.  One step = one gather-form filter pass over the whole read
+batch (read tokenisation, every (read, candidate bin) check, pass mask out);
+the bank is built once beforehand, as in the paper (Sec. 6.1: bitvectors
+are generated once per reference) and reported on its own.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "(read,bin) checks/s & reads/s at E=0.05·L; frac of HBM/INT8 roofline vs plain"
+UNIT = "checks/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one gather launch, from an
+# ncu capture, valid only for the kernel source it was taken on.
+TRAFFIC_BY_SOURCE: dict[str, dict] = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--reads", type=int, default=1_000_000, help="reads per GPU (weak scaling)")
+    ap.add_argument("--ref-bp", type=int, default=100_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def make_workload(args, rank):
+    import synth
+    # same reference on every rank; each rank its own read batch (weak scaling)
+    return synth.gather_seeds(ref_len=args.ref_bp, n_reads=args.reads, read_seed=synth.SEED_READS + 1000 * rank)
+
+
+def config_of(w, n_gpus):
+    c = np.diff(w.cand_offsets)
+    return {
+        "workload": f"gather, {w.ref_len / 1e6:g} Mbp repeat-rich reference "
+                    f"({int(w.meta['repeat_frac'] * 100)}% repeats), {w.n_reads} x {int(np.diff(w.read_offsets)[0])} bp "
+                    f"reads/GPU, 12-mer seed candidates (cap 1000)",
+        "ref_bp": w.ref_len, "q": w.q, "bin_len": w.bin_len, "overlap": w.overlap, "n_bins": w.n_bins,
+        "reads_per_gpu": w.n_reads, "read_len": int(np.diff(w.read_offsets)[0]), "E": int(w.E[0]),
+        "checks_per_gpu_step": w.n_checks, "cands_per_read_mean": round(float(c.mean()), 2),
+        "cands_per_read_max": int(c.max()), "sub": w.meta["sub"], "indel": w.meta["indel"],
+        "l2": "flushed between timed steps (256 MiB write, outside the events)",
+        "parallelism": f"replicas x{n_gpus} (read batches sharded, no collective)",
+    }
+
+
+def algorithmic_bytes(w, row_bytes):
+    """Bytes one gather launch must move: per check the bin row, the candidate
+    id and the pass byte; per read its bases, two offsets and E."""
+    return w.n_checks * (row_bytes + 4 + 1) + int(w.read_offsets[-1]) + (w.n_reads + 1) * 16 + w.n_reads * 2
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks + throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for ln in out.splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in ("gather.cu", "grim_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1711_01177_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def cpu_baseline(w, seconds):
+    """The oracle, single-threaded, on the first reads of the workload."""
+    import oracle
+    o = oracle.Oracle()
+    t0 = time.perf_counter()
+    ob = o.build_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
+    t_bank = time.perf_counter() - t0
+
+    def run(n):
+        co = w.cand_offsets[:n + 1]
+        ro = w.read_offsets[:n + 1]
+        t = time.perf_counter()
+        o.filter(ob, w.q, w.bases[:ro[-1]], ro, w.cand_bins[:co[-1]], co, w.E[:n])
+        return time.perf_counter() - t, int(co[-1])
+
+    dt, nc = run(min(2000, w.n_reads))
+    n = min(w.n_reads, max(2000, int(2000 * seconds / max(dt, 1e-6))))
+    dt, nc = run(n)
+    return {"value": nc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} reads ({nc} checks) of the same workload, oracle bank prebuilt "
+                      f"({t_bank:.1f} s, not timed), single thread",
+            "reads_per_s": n / dt, "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    w = synth.gather_seeds(ref_len=args.ref_bp, n_reads=args.reads)
+    o = oracle.Oracle()
+    ob = o.build_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
+    # size one step at about (budget / steps) seconds of oracle work
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+
+    def step(n):
+        co, ro = w.cand_offsets[:n + 1], w.read_offsets[:n + 1]
+        t = time.perf_counter()
+        o.filter(ob, w.q, w.bases[:ro[-1]], ro, w.cand_bins[:co[-1]], co, w.E[:n])
+        return time.perf_counter() - t, int(co[-1])
+
+    dt, _ = step(1000)
+    n = min(w.n_reads, max(1000, int(1000 * per_step / max(dt, 1e-6))))
+    for _ in range(args.warmup):
+        step(n)
+    times, checks = [], 0
+    for _ in range(args.steps):
+        dt, nc = step(n)
+        times.append(dt)
+        checks += nc
+    value = checks / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": config_of(w, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {n} reads ({checks // args.steps} checks) per step, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1711_01177_gb300 as grim
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    grim.build()
+    grim.load()
+    w = make_workload(args, rank)
+
+    def dev(a):
+        a = np.ascontiguousarray(a)
+        if a.dtype == np.uint32:
+            a = a.view(np.int32)
+        elif a.dtype == np.uint16:
+            a = a.view(np.int16)
+        return torch.from_numpy(a).cuda()
+
+    stream = torch.cuda.current_stream()
+    # bank build, once per reference (timed on its own)
+    ref_d = dev(w.ref2bit)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bank = grim.grim_build_bank(ref_d, w.ref_len, w.q, w.bin_len, w.overlap)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bank_ms = e0.elapsed_time(e1)
+    st, flags = grim.grim_bank_status(bank)
+    assert st == grim.GRIM_OK, (st, flags)
+    bank_bytes = bank.n_bins * bank.row_words * 4 + len(w.ref2bit)
+
+    reads_d, roff_d = dev(w.bases), dev(w.read_offsets)
+    cb_d, co_d, E_d = dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)
+    pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        grim.grim_filter(bank, reads_d, roff_d, cb_d, co_d, E_d, pass_out=pass_d)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    st, flags = grim.grim_bank_status(bank)
+    assert st == grim.GRIM_OK, (st, flags)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i)
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    launches = args.steps  # one gather kernel per step
+
+    # end to end through the public API: pinned host buffers in, pass mask out
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(
+        {np.dtype(np.uint32): np.int32, np.dtype(np.uint16): np.int16}.get(a.dtype, a.dtype))).pin_memory()
+    h_in = [pin(w.bases), pin(w.read_offsets), pin(w.cand_bins), pin(w.cand_offsets), pin(w.E)]
+    d_in = [reads_d, roff_d, cb_d, co_d, E_d]
+    h_out = torch.empty(w.n_checks, dtype=torch.uint8).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
+    d2h = h_out.numel()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for h, d in zip(h_in, d_in):
+            d.copy_(h, non_blocking=True)
+        grim.grim_filter(bank, *d_in, pass_out=pass_d)
+        h_out.copy_(pass_d, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_total = float(sum(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    st, flags = grim.grim_bank_status(bank)
+    assert st == grim.GRIM_OK, (st, flags)
+    pass_rate = float(pass_d.float().mean().item())
+
+    checks_all = w.n_checks * world
+    value = checks_all * args.steps / (total_ms / 1e3)
+    avg_launch_ms = float(np.mean(step_ms))
+    row_bytes = bank.row_words * 4
+    alg = algorithmic_bytes(w, row_bytes)
+    peak, peak_kind = load_peaks()
+    achieved = alg / (avg_launch_ms / 1e3) / 1e9
+    sha = source_sha()
+    traffic = TRAFFIC_BY_SOURCE.get(sha, {}).get("bytes")
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": config_of(w, world),
+            "reads_per_s": w.n_reads * world * args.steps / (total_ms / 1e3),
+            "pass_rate": pass_rate,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+                         "kernel": f"gather_kernel<{w.q}>", "algorithmic_bytes_per_launch": alg,
+                         "avg_launch_ms": avg_launch_ms, "source_sha": sha,
+                         "note": "bank (50 MB) fits the 129 MB L2 between candidate rows; frac counts "
+                                 "algorithmic bytes, not DRAM bytes"},
+            "e2e": {"value": checks_all * args.steps / (e2e_total / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "bank_build": {"ms": bank_ms, "ref_bp": w.ref_len, "mbp_per_s": w.ref_len / 1e6 / (bank_ms / 1e3),
+                           "gb_per_s": bank_bytes / 1e9 / (bank_ms / 1e3), "bank_bytes": bank.n_bins * row_bytes},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        else:
+            line["cpu_baseline"] = None
+        print(json.dumps(line), flush=True)
+    bank.free()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

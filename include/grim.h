@@ -1,0 +1,129 @@
+/*
+ * grim.h - C ABI of the GB300 seed-location filter (GRIM-Filter: Kim et al.,
+ * BMC Genomics 2018, arXiv 1711.01177).
+ *
+ * The reference genome is cut into overlapping bins; every bin gets a
+ * 4^q-bit existence bitvector over all q-grams ("tokens").  For a read and
+ * a candidate bin the filter counts the read's tokens present in the bin
+ * (the accumulation sum) and passes the location when the sum reaches
+ * T = (L - q + 1) - q*E for E tolerated edits.
+ *
+ * Conventions for every entry point:
+ *  - pointers named "device" are CUDA device pointers (or managed memory)
+ *    on the current device; "host" pointers are ordinary host memory;
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream); every call only enqueues work on that stream and returns; the
+ *    caller synchronises before reading outputs or freeing inputs;
+ *  - the library never frees or keeps caller memory; the bank is owned by
+ *    the library from grim_build_bank until grim_bank_free;
+ *  - every call returns a status code (GRIM_OK = 0).  Host-side argument
+ *    checks return GRIM_EINVAL / GRIM_ENOTSUP without enqueuing anything.
+ *    Problems found in the DATA on the device (a base code > 3, a bin id
+ *    >= n_bins, decreasing offsets, an over-long read) never fault: the
+ *    affected outputs are written as "discard" (pass 0, sum 0) and a flag is
+ *    raised in the bank's status word, read and cleared by grim_bank_status.
+ *
+ * Base codes: A=0, C=1, G=2, T=3.  Token value: the q bases read as a
+ * base-4 number, first base most significant.
+ */
+#ifndef GRIM_H
+#define GRIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define GRIM_OK 0
+#define GRIM_EINVAL 1    /* bad argument, found on the host */
+#define GRIM_EDATA 2     /* bad input data, found on the device */
+#define GRIM_ENOMEM 3    /* device allocation failed */
+#define GRIM_ECUDA 4     /* a CUDA runtime call failed (see grim_last_cuda_error) */
+#define GRIM_EOVERFLOW 5 /* an output list exceeded the capacity given */
+#define GRIM_ETIMEOUT 6  /* a bounded device-side wait ran out */
+#define GRIM_ENOTSUP 7   /* parameters outside what the kernels implement */
+
+/* ---- device status flags (grim_bank_status) --------------------------- */
+#define GRIM_FLAG_BAD_BASE 0x1u    /* a read holds a code > 3 */
+#define GRIM_FLAG_BAD_BIN 0x2u     /* a candidate bin id >= n_bins */
+#define GRIM_FLAG_BAD_OFFSETS 0x4u /* read or candidate offsets decrease */
+#define GRIM_FLAG_LONG_READ 0x8u   /* a read longer than GRIM_MAX_READ_LEN */
+#define GRIM_FLAG_OVERFLOW 0x10u   /* a pair list exceeded its capacity */
+#define GRIM_FLAG_TIMEOUT 0x20u    /* a bounded device-side wait ran out */
+
+#define GRIM_MAX_Q 6               /* token sizes 1..6 (the paper sweeps 4-6, Sec. 6.1) */
+#define GRIM_MAX_READ_LEN 65535    /* so that every sum fits 16 bits */
+
+typedef struct grim_bank grim_bank;
+
+/* Text for a status code (static storage). */
+const char* grim_strerror(int status);
+
+/* cudaError_t of the most recent GRIM_ECUDA / GRIM_ENOMEM on this thread. */
+int grim_last_cuda_error(void);
+
+/*
+ * Build the bank: the existence bitvector of every bin (Sec. 3.1, Fig. 2;
+ * generated once per reference).
+ *   ref2bit  device, (len+3)/4 bytes: base k in bits 2*(k%4) of byte k/4.
+ *   len      number of bases, >= 1.
+ *   q        token size, 1..GRIM_MAX_Q.
+ *   bin_len  bases per bin core, >= 1.  n_bins = ceil(len / bin_len) must
+ *            fit 32 bits.
+ *   overlap  bases each bin extends past its core (>= 0).  Bin b spans
+ *            [b*bin_len, min(len, (b+1)*bin_len + overlap)); a token belongs
+ *            to the bin when all its bases lie in the span.  Choose
+ *            overlap >= the longest read (plus tolerated insertions) so a
+ *            read starting in a core fits in that bin (Sec. 3.2).
+ *   out      host, receives the bank handle.
+ * Layout in HBM: bin-major rows of row_words 32-bit words (row_words =
+ * max(4, 4^q/32), 16-byte aligned rows); bit t of bin b is bit (t & 31)
+ * of word b*row_words + (t >> 5).  Allocates the bank with cudaMalloc and
+ * enqueues the build on `stream`.
+ */
+int grim_build_bank(const uint8_t* ref2bit, int64_t len, int q, int bin_len, int overlap, void* stream,
+                    grim_bank** out);
+
+/* Geometry and device address of a bank (any output pointer may be NULL). */
+int grim_bank_info(const grim_bank* bank, int64_t* len, int64_t* n_bins, int* q, int* bin_len, int* overlap,
+                   int64_t* row_words, const uint32_t** bits);
+
+/* Synchronise `stream`, then read and clear the bank's device status word.
+ * *flags (nullable) receives the GRIM_FLAG_* bits raised since the last
+ * call by any call that used this bank.  Returns GRIM_EDATA if a data flag
+ * is set, GRIM_EOVERFLOW / GRIM_ETIMEOUT for those flags, else GRIM_OK. */
+int grim_bank_status(grim_bank* bank, void* stream, uint32_t* flags);
+
+/* Free the bank (synchronises the device first). NULL is a no-op. */
+int grim_bank_free(grim_bank* bank);
+
+/*
+ * Gather-form filter: the Filter Bitmask Generator of Sec. 3.3 over a
+ * candidate list (the seed locations a read mapper found), implementing the
+ * five steps of Sec. 3.2 / Fig. 3 for every (read, candidate bin) pair.
+ *   reads         device u8 codes 0..3, read r = reads[read_offsets[r] ..
+ *                 read_offsets[r+1]); length <= GRIM_MAX_READ_LEN.
+ *   read_offsets  device int64, n_reads + 1 entries, non-decreasing.
+ *   n_reads       >= 0 (0 enqueues nothing).
+ *   cand_bins     device u32 bin ids; read r's candidates are
+ *                 cand_bins[cand_offsets[r] .. cand_offsets[r+1]).
+ *   cand_offsets  device int64, n_reads + 1 entries, non-decreasing.
+ *   E             device u16, tolerated edits per read.
+ *   pass          device u8 output aligned with cand_bins: 1 = align this
+ *                 location, 0 = discard (the seed location filter bitmask,
+ *                 one byte per location).
+ *   sums          device u16 output aligned with cand_bins, or NULL.
+ * Duplicate candidates are checked independently; a read shorter than q
+ * has sum 0 and passes iff its threshold is <= 0.
+ */
+int grim_filter(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
+                uint16_t* sums, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRIM_H */

@@ -1,0 +1,182 @@
+"""Python binding of libgrim, the GB300 seed-location filter.
+
+Argument marshalling only: every step of the filter runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current stream.  The
+functions carry the C ABI's names (include/grim.h); a failing status raises
+GrimError.  There is no CPU fallback: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from ._build import LIB as _LIB_PATH
+from ._build import build as _build_lib
+
+GRIM_OK, GRIM_EINVAL, GRIM_EDATA, GRIM_ENOMEM, GRIM_ECUDA, GRIM_EOVERFLOW, GRIM_ETIMEOUT, GRIM_ENOTSUP = range(8)
+GRIM_FLAG_BAD_BASE = 0x1
+GRIM_FLAG_BAD_BIN = 0x2
+GRIM_FLAG_BAD_OFFSETS = 0x4
+GRIM_FLAG_LONG_READ = 0x8
+GRIM_FLAG_OVERFLOW = 0x10
+GRIM_FLAG_TIMEOUT = 0x20
+GRIM_MAX_Q = 6
+GRIM_MAX_READ_LEN = 65535
+
+# every symbol include/grim.h declares, with (restype, argtypes)
+_P, _I64, _I32, _U32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32
+SIGNATURES = {
+    "grim_strerror": (ctypes.c_char_p, [_I32]),
+    "grim_last_cuda_error": (_I32, []),
+    "grim_build_bank": (_I32, [_P, _I64, _I32, _I32, _I32, _P, ctypes.POINTER(_P)]),
+    "grim_bank_info": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "grim_bank_status": (_I32, [_P, _P, ctypes.POINTER(_U32)]),
+    "grim_bank_free": (_I32, [_P]),
+    "grim_filter": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
+}
+
+_lib = None
+
+
+class GrimError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = load().grim_strerror(status).decode()
+        if status in (GRIM_ECUDA, GRIM_ENOMEM):
+            msg += f" (cudaError {load().grim_last_cuda_error()})"
+        super().__init__(f"{what}: {msg} [status {status}]")
+
+
+def build(force: bool = False) -> str:
+    """Compile libgrim.so for sm_103a (nvcc) next to this file."""
+    return _build_lib(force=force)
+
+
+def load(path: str | None = None):
+    """The loaded libgrim (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = path or _LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libgrim.so is not built ({p}); call paper_1711_01177_gb300.build()")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != GRIM_OK:
+        raise GrimError(status, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+_DUMMY = {}
+
+
+def _dev_ptr(t: torch.Tensor | None, name: str, elem_size: int | None = None, nullable: bool = False):
+    if t is None:
+        if nullable:
+            return None
+        raise ValueError(f"{name} is required")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if elem_size is not None and t.element_size() != elem_size:
+        raise ValueError(f"{name} must have {elem_size}-byte elements")
+    if t.numel() == 0:  # the C ABI wants a valid pointer even for empty arrays
+        key = (t.device.index, elem_size or 1)
+        if key not in _DUMMY:
+            _DUMMY[key] = torch.zeros(16, dtype=torch.uint8, device=t.device)
+        return ctypes.c_void_p(_DUMMY[key].data_ptr())
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ holder to view library memory."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, True),
+                                         "version": 3, "strides": None}
+
+
+class Bank:
+    """A built bank: existence bitvectors of every bin, owned by libgrim."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        L, nb, rw = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        q, bl, ov = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        bits = ctypes.c_void_p()
+        _check(load().grim_bank_info(handle, ctypes.byref(L), ctypes.byref(nb), ctypes.byref(q), ctypes.byref(bl),
+                                     ctypes.byref(ov), ctypes.byref(rw), ctypes.byref(bits)), "grim_bank_info")
+        self.len, self.n_bins, self.row_words = L.value, nb.value, rw.value
+        self.q, self.bin_len, self.overlap = q.value, bl.value, ov.value
+        self.bits_ptr = bits.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def bits(self) -> torch.Tensor:
+        """Zero-copy int32 view (n_bins, row_words) of the bank in HBM."""
+        arr = _CudaArray(self.bits_ptr, (self.n_bins, self.row_words), "<i4")
+        return torch.as_tensor(arr, device="cuda")
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            _check(load().grim_bank_free(self._h), "grim_bank_free")
+        self._h = None
+
+    def __del__(self):
+        try:
+            if self._h is not None and self._h.value and _lib is not None:
+                _lib.grim_bank_free(self._h)
+        except Exception:
+            pass
+
+
+def grim_build_bank(ref2bit: torch.Tensor, length: int, q: int, bin_len: int, overlap: int, stream=None) -> Bank:
+    """Existence bitvectors of every bin of a 2-bit packed reference (Sec. 3.1)."""
+    h = ctypes.c_void_p()
+    _check(load().grim_build_bank(_dev_ptr(ref2bit, "ref2bit", 1), length, q, bin_len, overlap, _stream_ptr(stream),
+                                  ctypes.byref(h)), "grim_build_bank")
+    return Bank(h)
+
+
+def grim_bank_status(bank: Bank, stream=None):
+    """Synchronise and read+clear the bank's device flags: (status, flags)."""
+    f = ctypes.c_uint32()
+    st = load().grim_bank_status(bank.handle, _stream_ptr(stream), ctypes.byref(f))
+    return st, f.value
+
+
+def grim_filter(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, cand_bins: torch.Tensor,
+                cand_offsets: torch.Tensor, E: torch.Tensor, pass_out: torch.Tensor | None = None,
+                sums: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Seed location filter bitmask (one u8 per candidate) for every
+    (read, candidate bin) pair (Sec. 3.2-3.3).  Returns pass_out."""
+    n_reads = read_offsets.numel() - 1
+    if n_reads < 0:
+        raise ValueError("read_offsets needs n_reads + 1 entries")
+    if cand_offsets.numel() != n_reads + 1 or E.numel() != n_reads:
+        raise ValueError("cand_offsets / E sizes do not match read_offsets")
+    if pass_out is None:
+        pass_out = torch.empty(cand_bins.numel(), dtype=torch.uint8, device=cand_bins.device)
+    _check(load().grim_filter(bank.handle, _dev_ptr(reads, "reads", 1), _dev_ptr(read_offsets, "read_offsets", 8),
+                              n_reads, _dev_ptr(cand_bins, "cand_bins", 4), _dev_ptr(cand_offsets, "cand_offsets", 8),
+                              _dev_ptr(E, "E", 2), _dev_ptr(pass_out, "pass", 1), _dev_ptr(sums, "sums", 2, True),
+                              _stream_ptr(stream)), "grim_filter")
+    return pass_out

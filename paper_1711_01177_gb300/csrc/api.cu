@@ -1,0 +1,158 @@
+// Host side of the C ABI: argument checks, bank ownership, status word.
+#include <string.h>
+
+#include "grim_internal.cuh"
+
+namespace grim {
+
+static thread_local int g_last_cuda_error = 0;
+
+void set_last_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
+
+int check_device(const grim_bank* bank) {
+    int dev = -1;
+    GRIM_CUDA_TRY(cudaGetDevice(&dev));
+    return dev == bank->device ? GRIM_OK : GRIM_EINVAL;
+}
+
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cached[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+}  // namespace grim
+
+extern "C" {
+
+const char* grim_strerror(int status) {
+    switch (status) {
+        case GRIM_OK: return "ok";
+        case GRIM_EINVAL: return "invalid argument";
+        case GRIM_EDATA: return "invalid input data found on the device";
+        case GRIM_ENOMEM: return "device allocation failed";
+        case GRIM_ECUDA: return "CUDA runtime error";
+        case GRIM_EOVERFLOW: return "output capacity exceeded";
+        case GRIM_ETIMEOUT: return "bounded device-side wait ran out";
+        case GRIM_ENOTSUP: return "parameters not supported by the kernels";
+        default: return "unknown status";
+    }
+}
+
+int grim_last_cuda_error(void) { return grim::g_last_cuda_error; }
+
+int grim_build_bank(const uint8_t* ref2bit, int64_t len, int q, int bin_len, int overlap, void* stream,
+                    grim_bank** out) {
+    if (!out) return GRIM_EINVAL;
+    *out = nullptr;
+    if (!ref2bit || len < 1 || bin_len < 1 || overlap < 0) return GRIM_EINVAL;
+    if (q < 1 || q > GRIM_MAX_Q) return GRIM_ENOTSUP;
+    const int64_t n_bins = (len + bin_len - 1) / bin_len;
+    if (n_bins > (int64_t)0xFFFFFFFFu) return GRIM_ENOTSUP;
+    const int64_t rw = grim::row_words_for(q);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    grim_bank* bank = new grim_bank();
+    bank->len = len;
+    bank->n_bins = n_bins;
+    bank->row_words = rw;
+    bank->q = q;
+    bank->bin_len = bin_len;
+    bank->overlap = overlap;
+    if (cudaGetDevice(&bank->device) != cudaSuccess) {
+        delete bank;
+        return GRIM_ECUDA;
+    }
+    const size_t bytes = (size_t)n_bins * (size_t)rw * 4;
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, bytes + 256);
+    if (e != cudaSuccess) {
+        grim::set_last_cuda_error(e);
+        delete bank;
+        return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
+    }
+    bank->bits = (uint32_t*)mem;
+    bank->status = (uint32_t*)((char*)mem + ((bytes + 255) & ~(size_t)255));
+    int rc = GRIM_OK;
+    e = cudaMemsetAsync(bank->status, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) {
+        grim::set_last_cuda_error(e);
+        rc = GRIM_ECUDA;
+    } else {
+        rc = grim::launch_bank_build(ref2bit, bank, s);
+    }
+    if (rc != GRIM_OK) {
+        cudaFree(mem);
+        delete bank;
+        return rc;
+    }
+    *out = bank;
+    return GRIM_OK;
+}
+
+int grim_bank_info(const grim_bank* bank, int64_t* len, int64_t* n_bins, int* q, int* bin_len, int* overlap,
+                   int64_t* row_words, const uint32_t** bits) {
+    if (!bank) return GRIM_EINVAL;
+    if (len) *len = bank->len;
+    if (n_bins) *n_bins = bank->n_bins;
+    if (q) *q = bank->q;
+    if (bin_len) *bin_len = bank->bin_len;
+    if (overlap) *overlap = bank->overlap;
+    if (row_words) *row_words = bank->row_words;
+    if (bits) *bits = bank->bits;
+    return GRIM_OK;
+}
+
+int grim_bank_status(grim_bank* bank, void* stream, uint32_t* flags) {
+    if (!bank) return GRIM_EINVAL;
+    int rc = grim::check_device(bank);
+    if (rc != GRIM_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t f = 0;
+    GRIM_CUDA_TRY(cudaStreamSynchronize(s));
+    GRIM_CUDA_TRY(cudaMemcpyAsync(&f, bank->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GRIM_CUDA_TRY(cudaMemsetAsync(bank->status, 0, sizeof(uint32_t), s));
+    GRIM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (flags) *flags = f;
+    if (f & (GRIM_FLAG_BAD_BASE | GRIM_FLAG_BAD_BIN | GRIM_FLAG_BAD_OFFSETS | GRIM_FLAG_LONG_READ))
+        return GRIM_EDATA;
+    if (f & GRIM_FLAG_OVERFLOW) return GRIM_EOVERFLOW;
+    if (f & GRIM_FLAG_TIMEOUT) return GRIM_ETIMEOUT;
+    return GRIM_OK;
+}
+
+int grim_bank_free(grim_bank* bank) {
+    if (!bank) return GRIM_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != bank->device) cudaSetDevice(bank->device);
+    cudaError_t e1 = cudaDeviceSynchronize();
+    cudaError_t e2 = cudaFree(bank->bits);
+    if (prev >= 0 && prev != bank->device) cudaSetDevice(prev);
+    delete bank;
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        grim::set_last_cuda_error(e1 != cudaSuccess ? e1 : e2);
+        return GRIM_ECUDA;
+    }
+    return GRIM_OK;
+}
+
+int grim_filter(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
+                uint16_t* sums, void* stream) {
+    if (!bank || n_reads < 0) return GRIM_EINVAL;
+    if (n_reads == 0) return GRIM_OK;
+    if (!reads || !read_offsets || !cand_bins || !cand_offsets || !E || !pass) return GRIM_EINVAL;
+    int rc = grim::check_device(bank);
+    if (rc != GRIM_OK) return rc;
+    return grim::launch_gather(bank, reads, read_offsets, n_reads, cand_bins, cand_offsets, E, pass, sums,
+                               (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// Internal definitions shared by the CUDA translation units of libgrim.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "grim.h"
+
+struct grim_bank {
+    int64_t len;        // reference length in bases
+    int64_t n_bins;     // ceil(len / bin_len)
+    int64_t row_words;  // 32-bit words per bin row (>= 4, 16-byte rows)
+    int q, bin_len, overlap;
+    int device;
+    uint32_t* bits;    // device, n_bins * row_words words, bin-major
+    uint32_t* status;  // device, one word of GRIM_FLAG_* bits
+};
+
+namespace grim {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Row geometry for token size Q: 4^Q bits per bin, rows padded to 16 bytes.
+template <int Q>
+struct Geo {
+    static constexpr int kBits = 1 << (2 * Q);
+    static constexpr int kRowWords = (kBits / 32) < 4 ? 4 : (kBits / 32);
+};
+
+inline int64_t row_words_for(int q) {
+    int64_t w = (int64_t(1) << (2 * q)) / 32;
+    return w < 4 ? 4 : w;
+}
+
+// Records the CUDA error of a failing call for grim_last_cuda_error.
+void set_last_cuda_error(cudaError_t e);
+
+// Current device must be the bank's device.
+int check_device(const grim_bank* bank);
+
+int launch_bank_build(const uint8_t* ref2bit, grim_bank* bank, cudaStream_t stream);
+int launch_gather(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                  const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
+                  uint16_t* sums, cudaStream_t stream);
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+}  // namespace grim
+
+#define GRIM_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t grim_err_ = (expr);                       \
+        if (grim_err_ != cudaSuccess) {                       \
+            grim::set_last_cuda_error(grim_err_);             \
+            return grim_err_ == cudaErrorMemoryAllocation     \
+                       ? GRIM_ENOMEM                          \
+                       : GRIM_ECUDA;                          \
+        }                                                     \
+    } while (0)

@@ -217,13 +217,13 @@ def gather_iid(ref_len: int = 1_000_000, n_reads: int = 10_000, L: int = 100, q:
 def gather_seeds(ref_len: int = 100_000_000, n_reads: int = 1_000_000, L: int = 150, q: int = 5,
                  bin_len: int = 256, overlap: int = 150, E: int = 7, cap: int = 1000, repeat_frac: float = 0.30,
                  div_lo: float = 0.10, div_hi: float = 0.20, sub: float = 0.04, indel: float = 0.01,
-                 seed_k: int = 12) -> Workload:
+                 seed_k: int = 12, read_seed: int = SEED_READS) -> Workload:
     """Repeat-rich reference (i.i.d. + planted families); reads at uniform
     positions; candidates = bins of all exact 12-mer seed hits from a CPU
     index, capped per read.  Defaults: the 100 Mbp / 1M x 150 bp workload."""
     codes = ref_with_repeats(ref_len, SEED_REF, repeat_frac, div_lo=div_lo, div_hi=div_hi)
-    off = read_offsets(n_reads, L, L, SEED_READS)
-    bases, starts = reads(codes, off, SEED_READS, sub, indel)
+    off = read_offsets(n_reads, L, L, read_seed)
+    bases, starts = reads(codes, off, read_seed, sub, indel)
     n_bins = -(-ref_len // bin_len)
     idx = seed_index(codes, seed_k)
     cb, co = cands_seeds(idx, bases, off, bin_len, n_bins, cap, seed_k)

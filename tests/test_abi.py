@@ -1,0 +1,75 @@
+"""The C-ABI library builds for sm_103a, loads on a CPU-only host, and
+exports every entry point declared in include/grim.h (no compute calls)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1711_01177_gb300 as grim
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(grim_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    grim.build()
+    return grim.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("grim_build_bank", "grim_filter", "grim_bank_free", "grim_bank_status"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    out = subprocess.run(["nm", "-D", "--defined-only", grim._LIB_PATH], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    missing = names - exported
+    assert not missing, f"declared but not exported: {missing}"
+    # and the Python binding knows every one of them, with the same names
+    assert names == set(grim.SIGNATURES), names ^ set(grim.SIGNATURES)
+    for n in names:
+        assert getattr(lib, n) is not None
+
+
+def test_strerror_without_gpu(lib):
+    assert lib.grim_strerror(grim.GRIM_OK) == b"ok"
+    assert b"invalid" in lib.grim_strerror(grim.GRIM_EINVAL)
+    assert lib.grim_strerror(12345) == b"unknown status"
+
+
+def test_host_side_argument_checks_need_no_gpu(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    # rejected before any CUDA call is made
+    assert lib.grim_build_bank(None, 100, 5, 256, 100, None, ctypes.byref(h)) == grim.GRIM_EINVAL
+    assert lib.grim_build_bank(ctypes.c_void_p(16), 100, 7, 256, 100, None, ctypes.byref(h)) == grim.GRIM_ENOTSUP
+    assert lib.grim_build_bank(ctypes.c_void_p(16), 100, 5, 0, 100, None, ctypes.byref(h)) == grim.GRIM_EINVAL
+    assert lib.grim_filter(None, None, None, 0, None, None, None, None, None, None) == grim.GRIM_EINVAL
+    assert lib.grim_bank_free(None) == grim.GRIM_OK
+
+
+def test_no_oracle_in_product_path():
+    # the package must not import, load or run anything under oracle/
+    pkg = os.path.join(ROOT, "paper_1711_01177_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"(import\s+oracle|from\s+oracle|liboracle|grim_oracle|oracle_\w+\()", text), f
