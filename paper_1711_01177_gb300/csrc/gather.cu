@@ -10,68 +10,201 @@
 // per token.  Reads of 100-150 bases need two or three planes.
 //
 // One warp per read (grid-stride over reads):
-//   1. lanes load 32 bases at a time and roll each lane's token out of the
-//      q following bases with warp shuffles (the q-gram window of Sec. 3.2
-//      step 1);
+//   0. the first batch of candidate rows is requested before anything else,
+//      so its latency hides behind the token work;
+//   1. lanes load the read 32 bases at a time; two ballots per 32 bases give
+//      the low and high bits of every base code, and a funnel shift puts the
+//      q bases starting at the lane's position side by side; a per-CTA
+//      table of 4^q entries turns those 2q bits into the token value
+//      (the q-gram window of Sec. 3.2 step 1);
 //   2. each token is added to the read's bit-sliced count planes in shared
 //      memory with a carry chain of atomicXor (bit p flips; a bit that was
 //      set carries into plane p+1);
-//   3. every lane keeps its 16-byte slice of the first four planes in
-//      registers;
-//   4. candidate rows are fetched as 16-byte vectors, lanes_per_bin lanes
-//      per row (8 for q=5: one 128-byte row per 8 lanes, 4 rows per warp
-//      step, 8 steps = 32 rows in flight per warp), ANDed with the planes,
-//      popcounted, reduced with xor-shuffles, compared with the threshold;
-//   5. the 32 results of a batch are gathered into lane order and stored as
-//      one coalesced run of pass bytes (and sums).
+//   3. every lane keeps its slice of the planes in registers (reads with up
+//      to two planes) or reads it from shared memory (more planes);
+//   4. candidate rows are fetched as 16-byte vectors, lanes_per_row lanes per
+//      row (4 lanes x 32 bytes for q=5: 8 rows per warp step, 32 rows in
+//      flight per warp), ANDed with the planes, popcounted and reduced with
+//      xor-shuffles, then compared with the threshold (steps 3-5);
+//   5. the results of a batch are gathered into lane order and stored as one
+//      coalesced run of pass bytes (and sums).
 #include "grim_internal.cuh"
 
 namespace grim {
 
 constexpr int kGatherWarps = 8;
-constexpr int kPlanes = 16;    // sums and counts stay below 2^16
-constexpr int kRegPlanes = 4;  // planes held in registers; more go through shared memory
+constexpr int kPlanes = 16;  // sums and counts stay below 2^16
 
 template <int Q>
 struct GatherGeo {
     static constexpr int kRowWords = Geo<Q>::kRowWords;
-    static constexpr int kLanesPerBin = kRowWords / 4;
-    static constexpr int kBinsPerStep = 32 / kLanesPerBin;
-    static constexpr int kSteps = (8 * kBinsPerStep) <= 32 ? 8 : (32 / kBinsPerStep);
-    static constexpr int kBatch = kSteps * kBinsPerStep;  // <= 32 candidates per batch
-    static_assert(kLanesPerBin >= 1 && kLanesPerBin <= 32, "row must fit one warp of 16-byte slices");
+    static constexpr int kRowVecs = kRowWords / 4;             // 16-byte vectors per row
+    static constexpr int kVPL = kRowWords >= 32 ? 2 : 1;        // vectors per lane per row
+    static constexpr int kLPB = kRowVecs / kVPL;               // lanes per row
+    static constexpr int kBPS = 32 / kLPB;                     // rows per warp step
+    static constexpr int kStepsA = 32 / kBPS;
+    static constexpr int kStepsB = 8 / kVPL;
+    static constexpr int kSteps = kStepsA < kStepsB ? kStepsA : kStepsB;
+    static constexpr int kBatch = kSteps * kBPS;               // candidates per batch (<= 32)
+    static constexpr int kTab = 1 << (2 * Q);                  // token table entries
+    static constexpr int kTabWords = (kTab * 2 + 15) / 16 * 4;  // u16 table, 16-byte padded
+    static constexpr int kPlaneWords = kPlanes * kRowWords;    // per warp
+    static_assert(kLPB >= 1 && kLPB <= 32 && kBatch <= 32, "bad gather geometry");
 };
+
+template <int Q>
+constexpr size_t gather_smem_bytes() {
+    return 4 * ((size_t)GatherGeo<Q>::kTabWords + (size_t)kGatherWarps * GatherGeo<Q>::kPlaneWords);
+}
 
 __device__ __forceinline__ uint32_t and_popc(const uint4& a, const uint4& b) {
     return __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
 }
 
+// One batch of candidate rows held in registers.
 template <int Q>
-__global__ void __launch_bounds__(kGatherWarps * 32)
+struct Batch {
+    using G = GatherGeo<Q>;
+    uint4 v[G::kSteps][G::kVPL];
+    uint32_t id;  // this lane's candidate id (lane < cnt)
+    int cnt;
+};
+
+template <int Q>
+__device__ __forceinline__ void load_batch(Batch<Q>& bt, const uint32_t* __restrict__ cand_bins, int64_t cb,
+                                           int64_t ce, const uint32_t* __restrict__ bank, int64_t n_bins,
+                                           int lane) {
+    using G = GatherGeo<Q>;
+    bt.cnt = (ce - cb) < G::kBatch ? (int)(ce - cb) : G::kBatch;
+    bt.id = (lane < bt.cnt) ? __ldg(cand_bins + cb + lane) : 0u;
+    const int s = lane % G::kLPB;
+#pragma unroll
+    for (int t = 0; t < G::kSteps; t++) {
+        if (t * G::kBPS >= bt.cnt) break;  // warp-uniform: the rest of the batch is empty
+        const int j = t * G::kBPS + lane / G::kLPB;
+        const uint32_t b = __shfl_sync(kFull, bt.id, j & 31);
+        const bool ok = j < bt.cnt && (int64_t)b < n_bins;
+        const uint4* row = reinterpret_cast<const uint4*>(bank) + (size_t)b * G::kRowVecs + s;
+#pragma unroll
+        for (int u = 0; u < G::kVPL; u++) bt.v[t][u] = ok ? __ldg(row + u * G::kLPB) : make_uint4(0, 0, 0, 0);
+    }
+}
+
+// Score every batch of one read.  NP > 0: NP planes held in registers;
+// NP == 0: P planes read from shared memory.
+template <int Q, int NP>
+__device__ __forceinline__ void score_read(Batch<Q>& bt, const uint4* __restrict__ planes, int P, int T,
+                                           int64_t co, int64_t ce, const uint32_t* __restrict__ cand_bins,
+                                           const uint32_t* __restrict__ bank, int64_t n_bins,
+                                           uint8_t* __restrict__ pass, uint16_t* __restrict__ sums, int lane,
+                                           uint32_t& flags) {
+    using G = GatherGeo<Q>;
+    const int s = lane % G::kLPB;
+    uint4 pl[NP > 0 ? NP : 1][G::kVPL];
+    if (NP > 0) {
+#pragma unroll
+        for (int p = 0; p < (NP > 0 ? NP : 1); p++)
+#pragma unroll
+            for (int u = 0; u < G::kVPL; u++) pl[p][u] = planes[p * G::kRowVecs + s + u * G::kLPB];
+    }
+    for (int64_t cb = co; cb < ce; cb += G::kBatch) {
+        uint32_t mine = 0;
+#pragma unroll
+        for (int t = 0; t < G::kSteps; t++) {
+            if (t * G::kBPS >= bt.cnt) break;  // warp-uniform
+            uint32_t part = 0;
+            if (NP > 0) {
+#pragma unroll
+                for (int p = 0; p < (NP > 0 ? NP : 1); p++) {
+                    uint32_t q = 0;
+#pragma unroll
+                    for (int u = 0; u < G::kVPL; u++) q += and_popc(bt.v[t][u], pl[p][u]);
+                    part += q << p;
+                }
+            } else {
+                for (int p = 0; p < P; p++) {
+                    uint32_t q = 0;
+#pragma unroll
+                    for (int u = 0; u < G::kVPL; u++)
+                        q += and_popc(bt.v[t][u], planes[p * G::kRowVecs + s + u * G::kLPB]);
+                    part += q << p;
+                }
+            }
+#pragma unroll
+            for (int o = G::kLPB / 2; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+            const uint32_t got = __shfl_sync(kFull, part, (lane % G::kBPS) * G::kLPB);
+            if (lane / G::kBPS == t) mine = got;
+        }
+        if (lane < bt.cnt) {
+            const bool in_range = (int64_t)bt.id < n_bins;
+            if (!in_range) flags |= GRIM_FLAG_BAD_BIN;
+            const uint32_t sum = in_range ? mine : 0u;
+            pass[cb + lane] = (in_range && (int)sum >= T) ? 1 : 0;
+            if (sums) sums[cb + lane] = (uint16_t)sum;
+        }
+        if (cb + G::kBatch < ce) load_batch<Q>(bt, cand_bins, cb + G::kBatch, ce, bank, n_bins, lane);
+    }
+}
+
+// Outputs of a read whose sum is 0 for every candidate (no tokens, or a
+// read rejected for bad data: then nothing passes).
+__device__ __forceinline__ void write_constant(int64_t co, int64_t ce, const uint32_t* __restrict__ cand_bins,
+                                               int64_t n_bins, bool pass0, uint8_t* __restrict__ pass,
+                                               uint16_t* __restrict__ sums, int lane, uint32_t& flags) {
+    for (int64_t c = co + lane; c < ce; c += 32) {
+        const bool in_range = (int64_t)__ldg(cand_bins + c) < n_bins;
+        if (!in_range) flags |= GRIM_FLAG_BAD_BIN;
+        pass[c] = (in_range && pass0) ? 1 : 0;
+        if (sums) sums[c] = 0;
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kGatherWarps * 32, 3)
 gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* __restrict__ reads,
               const int64_t* __restrict__ read_offsets, int64_t n_reads, const uint32_t* __restrict__ cand_bins,
               const int64_t* __restrict__ cand_offsets, const uint16_t* __restrict__ E,
               uint8_t* __restrict__ pass, uint16_t* __restrict__ sums, uint32_t* __restrict__ status) {
     using G = GatherGeo<Q>;
     constexpr int RW = G::kRowWords;
-    extern __shared__ uint4 gather_smem[];  // kGatherWarps x kPlanes x RW words
+    constexpr uint32_t kQMask = (1u << Q) - 1;
+    extern __shared__ uint4 gather_smem[];
+    uint16_t* tab = reinterpret_cast<uint16_t*>(gather_smem);
+    uint32_t* planes_all = reinterpret_cast<uint32_t*>(gather_smem) + G::kTabWords;
+
+    // token table: index (high bits of q bases << q) | (low bits) -> token,
+    // bit k of each half belonging to the k-th base of the window
+    for (int idx = threadIdx.x; idx < G::kTab; idx += blockDim.x) {
+        uint32_t tok = 0;
+#pragma unroll
+        for (int k = 0; k < Q; k++) {
+            const uint32_t code = (((idx >> (Q + k)) & 1u) << 1) | ((idx >> k) & 1u);
+            tok = (tok << 2) | code;
+        }
+        tab[idx] = (uint16_t)tok;
+    }
+    for (int i = threadIdx.x; i < kGatherWarps * G::kPlaneWords; i += blockDim.x) planes_all[i] = 0;
+    __syncthreads();
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int slice = lane % G::kLanesPerBin;  // which 16-byte slice of a row this lane handles
-    uint32_t* planes = reinterpret_cast<uint32_t*>(gather_smem) + warp * (kPlanes * RW);
-    for (int i = lane; i < kPlanes * RW; i += 32) planes[i] = 0;
-    __syncwarp();
+    uint32_t* planes = planes_all + warp * G::kPlaneWords;
+    const uint4* planes4 = reinterpret_cast<const uint4*>(planes);
 
     uint32_t flags = 0;
     const int64_t warp_stride = (int64_t)gridDim.x * kGatherWarps;
     for (int64_t r = (int64_t)blockIdx.x * kGatherWarps + warp; r < n_reads; r += warp_stride) {
         const int64_t ro = read_offsets[r], re = read_offsets[r + 1];
         const int64_t co = cand_offsets[r], ce = cand_offsets[r + 1];
+        const int e = E[r];
         if (ce < co) {  // nothing sensible to write for this read
             flags |= GRIM_FLAG_BAD_OFFSETS;
             continue;
         }
+        // 0. first candidate batch in flight while the tokens are built
+        Batch<Q> bt;
+        if (co < ce) load_batch<Q>(bt, cand_bins, co, ce, bank, n_bins, lane);
+
         bool bad_read = false;
         int L = 0;
         if (re < ro) {
@@ -85,33 +218,40 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
         }
         const uint8_t* rd = reads + ro;
 
-        // steps 1-2: tokens into bit-sliced count planes
+        // 1-2. tokens into bit-sliced count planes, 256 bases per round
         uint32_t bad_base = 0;
         int top = -1;  // highest plane this lane set
-        uint32_t cur = (lane < L) ? rd[lane] : 0u;
-        for (int c0 = 0; c0 < L; c0 += 32) {
-            const int i = c0 + lane;
-            const uint32_t nxt = (i + 32 < L) ? rd[i + 32] : 0u;
-            bad_base |= (uint32_t)((i < L) && (cur > 3u));
-            uint32_t tok = 0;
+        for (int s0 = 0; s0 < L; s0 += 256) {
+            uint32_t c[9];
 #pragma unroll
-            for (int k = 0; k < Q; k++) {
-                const int src = lane + k;
-                const uint32_t a = __shfl_sync(kFull, cur, src & 31);
-                const uint32_t b = __shfl_sync(kFull, nxt, src & 31);
-                tok = (tok << 2) | (((src < 32) ? a : b) & 3u);
+            for (int k = 0; k < 9; k++) {
+                const int i = s0 + 32 * k + lane;
+                c[k] = (s0 + 32 * k < L && i < L) ? __ldg(rd + i) : 0u;
+                bad_base |= (uint32_t)(c[k] > 3u);
             }
-            if (i + Q <= L) {
-                const uint32_t w = tok >> 5, m = 1u << (tok & 31);
-                int p = 0;
-                while (p < kPlanes) {
-                    const uint32_t old = atomicXor(&planes[p * RW + w], m);
-                    if (!(old & m)) break;
-                    ++p;
+            uint32_t lo_c = __ballot_sync(kFull, c[0] & 1u), hi_c = __ballot_sync(kFull, c[0] & 2u);
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (s0 + 32 * k >= L) break;  // warp-uniform
+                const uint32_t lo_n = __ballot_sync(kFull, c[k + 1] & 1u);
+                const uint32_t hi_n = __ballot_sync(kFull, c[k + 1] & 2u);
+                const int i = s0 + 32 * k + lane;
+                if (i + Q <= L) {
+                    const uint32_t xl = __funnelshift_r(lo_c, lo_n, lane) & kQMask;
+                    const uint32_t xh = __funnelshift_r(hi_c, hi_n, lane) & kQMask;
+                    const uint32_t tok = tab[(xh << Q) | xl];
+                    const uint32_t w = tok >> 5, m = 1u << (tok & 31);
+                    int p = 0;
+                    while (p < kPlanes) {
+                        const uint32_t old = atomicXor(&planes[p * RW + w], m);
+                        if (!(old & m)) break;
+                        ++p;
+                    }
+                    top = p > top ? p : top;
                 }
-                top = p > top ? p : top;
+                lo_c = lo_n;
+                hi_c = hi_n;
             }
-            cur = nxt;
         }
         const int used = (int)__reduce_max_sync(kFull, (unsigned)(top + 1));
         if (__any_sync(kFull, bad_base)) {
@@ -119,50 +259,19 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
             bad_read = true;
         }
         __syncwarp();
-        const int P = bad_read ? 0 : used;
         const int n_tok = L - Q + 1 > 0 ? L - Q + 1 : 0;
-        const int T = n_tok - Q * (int)E[r];
+        const int T = n_tok - Q * e;
 
-        // step 3: this lane's slices of the low planes
-        uint4 pl[kRegPlanes];
-#pragma unroll
-        for (int p = 0; p < kRegPlanes; p++)
-            pl[p] = (p < P) ? *reinterpret_cast<const uint4*>(&planes[p * RW + 4 * slice]) : make_uint4(0, 0, 0, 0);
-
-        // steps 4-5 over the candidate list
-        for (int64_t cb = co; cb < ce; cb += G::kBatch) {
-            const int cnt = (ce - cb) < G::kBatch ? (int)(ce - cb) : G::kBatch;
-            const uint32_t my_bin = (lane < cnt) ? cand_bins[cb + lane] : 0u;
-            uint4 v[G::kSteps];
-#pragma unroll
-            for (int t = 0; t < G::kSteps; t++) {
-                const int j = t * G::kBinsPerStep + lane / G::kLanesPerBin;
-                const uint32_t b = __shfl_sync(kFull, my_bin, j & 31);
-                v[t] = make_uint4(0, 0, 0, 0);
-                if (j < cnt && b < n_bins)
-                    v[t] = __ldg(reinterpret_cast<const uint4*>(bank + (size_t)b * RW) + slice);
-            }
-            uint32_t mine = 0;
-#pragma unroll
-            for (int t = 0; t < G::kSteps; t++) {
-                uint32_t part = 0;
-#pragma unroll
-                for (int p = 0; p < kRegPlanes; p++)
-                    if (p < P) part += and_popc(v[t], pl[p]) << p;
-                for (int p = kRegPlanes; p < P; p++)
-                    part += and_popc(v[t], *reinterpret_cast<const uint4*>(&planes[p * RW + 4 * slice])) << p;
-#pragma unroll
-                for (int o = G::kLanesPerBin / 2; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-                const uint32_t got = __shfl_sync(kFull, part, (lane % G::kBinsPerStep) * G::kLanesPerBin);
-                if (lane / G::kBinsPerStep == t) mine = got;
-            }
-            if (lane < cnt) {
-                const bool in_range = my_bin < n_bins;
-                if (!in_range) flags |= GRIM_FLAG_BAD_BIN;
-                const uint32_t sum = (in_range && !bad_read) ? mine : 0u;
-                pass[cb + lane] = (in_range && !bad_read && (int)sum >= T) ? 1 : 0;
-                if (sums) sums[cb + lane] = (uint16_t)sum;
-            }
+        // 3-5. score the candidates
+        if (co < ce) {
+            if (bad_read || used == 0)
+                write_constant(co, ce, cand_bins, n_bins, !bad_read && T <= 0, pass, sums, lane, flags);
+            else if (used == 1)
+                score_read<Q, 1>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
+            else if (used == 2)
+                score_read<Q, 2>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
+            else
+                score_read<Q, 0>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
         }
 
         // leave the planes zeroed for the warp's next read
@@ -178,7 +287,7 @@ template <int Q>
 static int launch_q(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                     const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
                     uint16_t* sums, cudaStream_t s) {
-    constexpr size_t smem = (size_t)kGatherWarps * kPlanes * Geo<Q>::kRowWords * 4;
+    constexpr size_t smem = gather_smem_bytes<Q>();
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
         if (smem > 48 * 1024)
@@ -192,8 +301,8 @@ static int launch_q(const grim_bank* bank, const uint8_t* reads, const int64_t* 
     const int64_t cap = (int64_t)sm_count() * blocks_per_sm * 8;
     const int64_t blocks = need < cap ? need : cap;
     gather_kernel<Q><<<(unsigned)blocks, kGatherWarps * 32, smem, s>>>(bank->bits, bank->n_bins, reads, read_offsets,
-                                                                    n_reads, cand_bins, cand_offsets, E, pass, sums,
-                                                                    bank->status);
+                                                                       n_reads, cand_bins, cand_offsets, E, pass,
+                                                                       sums, bank->status);
     GRIM_CUDA_TRY(cudaGetLastError());
     return GRIM_OK;
 }
