@@ -54,6 +54,7 @@ extern "C" {
 #define GRIM_FLAG_TIMEOUT 0x20u    /* a bounded device-side wait ran out */
 
 #define GRIM_MAX_Q 6               /* token sizes 1..6 (the paper sweeps 4-6, Sec. 6.1) */
+#define GRIM_MAX_SCAN_Q 5          /* token sizes of the full-scan form */
 #define GRIM_MAX_READ_LEN 65535    /* so that every sum fits 16 bits */
 
 typedef struct grim_bank grim_bank;
@@ -121,6 +122,29 @@ int grim_bank_free(grim_bank* bank);
 int grim_filter(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                 const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
                 uint16_t* sums, void* stream);
+
+/*
+ * Full-scan form: the filter of Sec. 3.2 for every read against every bin
+ * of the window [bin_begin, bin_end) (the paper's bin window, Sec. 6.1,
+ * with every bin checked), computed as the contraction
+ * Sum[r, b] = sum_t count_r(t) * bit_b(t) on the tcgen05 tensor cores
+ * (exact: small-integer products and sums in f32).
+ *   reads, read_offsets, n_reads, E   as for grim_filter.
+ *   bin_begin, bin_end  0 <= bin_begin <= bin_end <= n_bins.
+ *   pair_read, pair_bin device u32 outputs, capacity `cap` entries each;
+ *                       passing pairs (Sum >= T) in no particular order.
+ *   pair_sum            device u16 output (cap entries) or NULL.
+ *   cap                 >= 0; pairs beyond cap are counted, not written,
+ *                       and raise GRIM_FLAG_OVERFLOW.
+ *   n_pairs             device int64, receives the number of passing pairs
+ *                       (which may exceed cap).
+ *   read_pass           device u32 [n_reads] or NULL: passing bins per read.
+ * Token sizes 1..5 (GRIM_ENOTSUP above).  Allocates its scratch with
+ * cudaMallocAsync on `stream` and frees it with cudaFreeAsync.
+ */
+int grim_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+              const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,
+              uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* stream);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,7 @@ GRIM_FLAG_LONG_READ = 0x8
 GRIM_FLAG_OVERFLOW = 0x10
 GRIM_FLAG_TIMEOUT = 0x20
 GRIM_MAX_Q = 6
+GRIM_MAX_SCAN_Q = 5
 GRIM_MAX_READ_LEN = 65535
 
 # every symbol include/grim.h declares, with (restype, argtypes)
@@ -36,6 +37,7 @@ SIGNATURES = {
     "grim_bank_status": (_I32, [_P, _P, ctypes.POINTER(_U32)]),
     "grim_bank_free": (_I32, [_P]),
     "grim_filter": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
+    "grim_scan": (_I32, [_P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P]),
 }
 
 _lib = None
@@ -180,3 +182,44 @@ def grim_filter(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, can
                               _dev_ptr(E, "E", 2), _dev_ptr(pass_out, "pass", 1), _dev_ptr(sums, "sums", 2, True),
                               _stream_ptr(stream)), "grim_filter")
     return pass_out
+
+
+class ScanResult:
+    """Passing (read, bin) pairs of a full scan, in no particular order."""
+
+    def __init__(self, pair_read, pair_bin, pair_sum, n_pairs, read_pass):
+        self.pair_read, self.pair_bin, self.pair_sum = pair_read, pair_bin, pair_sum
+        self.n_pairs_dev, self.read_pass = n_pairs, read_pass
+
+    @property
+    def n_pairs(self) -> int:
+        return int(self.n_pairs_dev.item())
+
+
+def grim_scan(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, E: torch.Tensor, bin_begin: int = 0,
+              bin_end: int | None = None, cap: int = 1 << 20, with_sums: bool = True, with_read_pass: bool = False,
+              out: ScanResult | None = None, stream=None) -> ScanResult:
+    """Every read against every bin of [bin_begin, bin_end) on the tensor
+    cores (Sec. 3.2 over the bin window of Sec. 6.1).  Pairs beyond `cap`
+    are counted but not written (GRIM_FLAG_OVERFLOW)."""
+    n_reads = read_offsets.numel() - 1
+    if n_reads < 0 or E.numel() != n_reads:
+        raise ValueError("read_offsets / E sizes do not match")
+    if bin_end is None:
+        bin_end = bank.n_bins
+    dev = read_offsets.device
+    if out is None:
+        out = ScanResult(torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
+                         torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
+                         torch.empty(max(cap, 1), dtype=torch.int16, device=dev) if with_sums else None,
+                         torch.zeros(1, dtype=torch.int64, device=dev),
+                         torch.empty(max(n_reads, 1), dtype=torch.int32, device=dev) if with_read_pass else None)
+        cap_eff = cap
+    else:
+        cap_eff = out.pair_read.numel()
+    _check(load().grim_scan(bank.handle, _dev_ptr(reads, "reads", 1), _dev_ptr(read_offsets, "read_offsets", 8),
+                            n_reads, _dev_ptr(E, "E", 2), bin_begin, bin_end, _dev_ptr(out.pair_read, "pair_read", 4),
+                            _dev_ptr(out.pair_bin, "pair_bin", 4), _dev_ptr(out.pair_sum, "pair_sum", 2, True), cap_eff,
+                            _dev_ptr(out.n_pairs_dev, "n_pairs", 8), _dev_ptr(out.read_pass, "read_pass", 4, True),
+                            _stream_ptr(stream)), "grim_scan")
+    return out

@@ -155,4 +155,31 @@ int grim_filter(const grim_bank* bank, const uint8_t* reads, const int64_t* read
                                (cudaStream_t)stream);
 }
 
+int grim_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+              const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,
+              uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* stream) {
+    if (!bank || n_reads < 0 || cap < 0 || !n_pairs) return GRIM_EINVAL;
+    if (bin_begin < 0 || bin_end > bank->n_bins || bin_begin > bin_end) return GRIM_EINVAL;
+    if (cap > 0 && (!pair_read || !pair_bin)) return GRIM_EINVAL;
+    if (bank->q > GRIM_MAX_SCAN_Q) return GRIM_ENOTSUP;
+    if (n_reads > ((int64_t)1 << 30)) return GRIM_ENOTSUP;
+    int rc = grim::check_device(bank);
+    if (rc != GRIM_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_reads == 0 || bin_begin == bin_end) {
+        GRIM_CUDA_TRY(cudaMemsetAsync(n_pairs, 0, sizeof(int64_t), s));
+        if (read_pass && n_reads > 0) GRIM_CUDA_TRY(cudaMemsetAsync(read_pass, 0, (size_t)n_reads * 4, s));
+        return GRIM_OK;
+    }
+    if (!reads || !read_offsets || !E) return GRIM_EINVAL;
+    void* scratch = nullptr;
+    GRIM_CUDA_TRY(cudaMallocAsync(&scratch, grim::scan_scratch_bytes(bank->q, n_reads), s));
+    rc = grim::launch_scan(bank, reads, read_offsets, n_reads, E, bin_begin, bin_end, pair_read, pair_bin, pair_sum,
+                           cap, n_pairs, read_pass, scratch, s);
+    cudaError_t e = cudaFreeAsync(scratch, s);
+    if (rc != GRIM_OK) return rc;
+    GRIM_CUDA_TRY(e);
+    return GRIM_OK;
+}
+
 }  // extern "C"

@@ -29,6 +29,7 @@
 //   5. the results of a batch are gathered into lane order and stored as one
 //      coalesced run of pass bytes (and sums).
 #include "grim_internal.cuh"
+#include "tokens.cuh"
 
 namespace grim {
 
@@ -46,8 +47,7 @@ struct GatherGeo {
     static constexpr int kStepsB = 8 / kVPL;
     static constexpr int kSteps = kStepsA < kStepsB ? kStepsA : kStepsB;
     static constexpr int kBatch = kSteps * kBPS;               // candidates per batch (<= 32)
-    static constexpr int kTab = 1 << (2 * Q);                  // token table entries
-    static constexpr int kTabWords = (kTab * 2 + 15) / 16 * 4;  // u16 table, 16-byte padded
+    static constexpr int kTabWords = TokenTable<Q>::kWords;
     static constexpr int kPlaneWords = kPlanes * kRowWords;    // per warp
     static_assert(kLPB >= 1 && kLPB <= 32 && kBatch <= 32, "bad gather geometry");
 };
@@ -167,22 +167,11 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
               uint8_t* __restrict__ pass, uint16_t* __restrict__ sums, uint32_t* __restrict__ status) {
     using G = GatherGeo<Q>;
     constexpr int RW = G::kRowWords;
-    constexpr uint32_t kQMask = (1u << Q) - 1;
     extern __shared__ uint4 gather_smem[];
     uint16_t* tab = reinterpret_cast<uint16_t*>(gather_smem);
     uint32_t* planes_all = reinterpret_cast<uint32_t*>(gather_smem) + G::kTabWords;
 
-    // token table: index (high bits of q bases << q) | (low bits) -> token,
-    // bit k of each half belonging to the k-th base of the window
-    for (int idx = threadIdx.x; idx < G::kTab; idx += blockDim.x) {
-        uint32_t tok = 0;
-#pragma unroll
-        for (int k = 0; k < Q; k++) {
-            const uint32_t code = (((idx >> (Q + k)) & 1u) << 1) | ((idx >> k) & 1u);
-            tok = (tok << 2) | code;
-        }
-        tab[idx] = (uint16_t)tok;
-    }
+    build_token_table<Q>(tab);
     for (int i = threadIdx.x; i < kGatherWarps * G::kPlaneWords; i += blockDim.x) planes_all[i] = 0;
     __syncthreads();
 
@@ -218,41 +207,19 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
         }
         const uint8_t* rd = reads + ro;
 
-        // 1-2. tokens into bit-sliced count planes, 256 bases per round
+        // 1-2. tokens into bit-sliced count planes
         uint32_t bad_base = 0;
         int top = -1;  // highest plane this lane set
-        for (int s0 = 0; s0 < L; s0 += 256) {
-            uint32_t c[9];
-#pragma unroll
-            for (int k = 0; k < 9; k++) {
-                const int i = s0 + 32 * k + lane;
-                c[k] = (s0 + 32 * k < L && i < L) ? __ldg(rd + i) : 0u;
-                bad_base |= (uint32_t)(c[k] > 3u);
+        for_each_token<Q>(rd, L, lane, tab, bad_base, [&](uint32_t tok) {
+            const uint32_t w = tok >> 5, m = 1u << (tok & 31);
+            int p = 0;
+            while (p < kPlanes) {
+                const uint32_t old = atomicXor(&planes[p * RW + w], m);
+                if (!(old & m)) break;
+                ++p;
             }
-            uint32_t lo_c = __ballot_sync(kFull, c[0] & 1u), hi_c = __ballot_sync(kFull, c[0] & 2u);
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                if (s0 + 32 * k >= L) break;  // warp-uniform
-                const uint32_t lo_n = __ballot_sync(kFull, c[k + 1] & 1u);
-                const uint32_t hi_n = __ballot_sync(kFull, c[k + 1] & 2u);
-                const int i = s0 + 32 * k + lane;
-                if (i + Q <= L) {
-                    const uint32_t xl = __funnelshift_r(lo_c, lo_n, lane) & kQMask;
-                    const uint32_t xh = __funnelshift_r(hi_c, hi_n, lane) & kQMask;
-                    const uint32_t tok = tab[(xh << Q) | xl];
-                    const uint32_t w = tok >> 5, m = 1u << (tok & 31);
-                    int p = 0;
-                    while (p < kPlanes) {
-                        const uint32_t old = atomicXor(&planes[p * RW + w], m);
-                        if (!(old & m)) break;
-                        ++p;
-                    }
-                    top = p > top ? p : top;
-                }
-                lo_c = lo_n;
-                hi_c = hi_n;
-            }
-        }
+            top = p > top ? p : top;
+        });
         const int used = (int)__reduce_max_sync(kFull, (unsigned)(top + 1));
         if (__any_sync(kFull, bad_base)) {
             flags |= GRIM_FLAG_BAD_BASE;

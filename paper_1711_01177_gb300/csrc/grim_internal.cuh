@@ -43,6 +43,12 @@ int launch_gather(const grim_bank* bank, const uint8_t* reads, const int64_t* re
                   const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
                   uint16_t* sums, cudaStream_t stream);
 
+size_t scan_scratch_bytes(int q, int64_t n_reads);
+int launch_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,
+                uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* scratch,
+                cudaStream_t stream);
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 

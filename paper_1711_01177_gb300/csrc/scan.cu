@@ -1,0 +1,742 @@
+// Full-scan form: every read of a batch against every bin of a window
+// (the filter of Sec. 3.2 applied to all bins, as the paper's bin window of
+// Sec. 6.1 checks consecutive bins in lockstep), written as the dense
+// contraction it is:
+//     Sum[b, r] = sum_t bit_b(t) * count_r(t)        (K = 4^q tokens)
+// on the tcgen05 tensor cores, exactly.
+//
+// Exactness.  sm_103a has no integer tcgen05 kind, so the contraction runs
+// on kind::f8f6f4 with e4m3 operands and f32 accumulation.  A = bank bits as
+// e4m3 0.0 / 1.0.  B = the read's token counts split in base-16 digits
+// (count = sum_d 16^d * digit_d, digit_d in [0, 15], each digit exact in
+// e4m3); every digit of every read is its own B row, so one MMA yields
+// sum_t bit * digit_d for all (read, digit) rows at once, and the epilogue
+// recombines Sum = sum_d 16^d * acc_d.  Every product is 0 or a small
+// integer and every partial sum is below 2^24, so f32 accumulation is exact
+// and the pass decision is bit-identical to counting tokens one by one.
+// Reads whose counts stay below 16 (nearly all) take one row; reads with
+// counts up to 255 take two, longer repeats four; the prep kernel packs
+// reads into tiles of 128 rows by digit class (128 x 1, 64 x 2, 32 x 4).
+//
+// Data flow per CTA (persistent, one per SM; a work item = one read tile x
+// one run of bin tiles):
+//   B   : the read tile's 128 digit rows x K bytes, staged once per work item
+//         in shared memory in the 128-byte-swizzled K-major layout;
+//   bank: tiles of 128 bin rows stream through a 4-deep shared-memory ring
+//         by 1-D TMA bulk copies (warp 0);
+//   A   : warps 2-5 (one thread per bin = per TMEM lane) expand 128 bits of
+//         their bin's row into 128 e4m3 bytes and store them straight into
+//         tensor memory (4 stages of 32 columns) - the expanded operand never
+//         touches shared memory;
+//   MMA : warp 1 issues M=128 (bins) x N=128 (rows) x K=32 tcgen05.mma with A
+//         from TMEM, B from shared memory, accumulating in TMEM (two 128-column
+//         accumulators);
+//   out : warps 6-9 read the accumulators with tcgen05.ld, recombine digits,
+//         compare with each read's threshold and append the rare passing
+//         (read, bin, sum) triples with warp-aggregated atomics.
+// Every wait is an mbarrier try_wait bounded by a time limit; on expiry the
+// CTA raises GRIM_FLAG_TIMEOUT, drains and frees its tensor memory.
+#include "grim_internal.cuh"
+#include "tokens.cuh"
+
+namespace grim {
+
+// ------------------------------------------------------------ constants
+
+constexpr int kScanThreads = 320;   // 10 warps: TMA, MMA, 4 expand, 4 epilogue
+constexpr int kBinTile = 128;       // bins per MMA tile (M, TMEM lanes)
+constexpr int kRowsTile = 128;      // B rows per read tile (N)
+constexpr int kBankStages = 4;
+constexpr int kAStages = 4;
+constexpr int kACols = 32;          // TMEM columns per A stage (128 K bytes)
+constexpr int kAccCol = 0;          // two accumulators: columns [0, 256)
+constexpr int kACol = 256;          // A stages: columns [256, 384)
+constexpr int kTmemCols = 512;
+constexpr int kPrepWarps = 8;
+constexpr int kNumClasses = 3;      // digit classes: 1, 2, 4 digits
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+__host__ __device__ constexpr int class_digits(int c) { return c == 0 ? 1 : (c == 1 ? 2 : 4); }
+__host__ __device__ constexpr int class_reads(int c) { return kRowsTile / class_digits(c); }
+
+template <int Q>
+struct ScanGeo {
+    static constexpr int kRowWords = Geo<Q>::kRowWords;
+    static constexpr int kRowBytes = kRowWords * 4;
+    static constexpr int kK = (1 << (2 * Q)) < 128 ? 128 : (1 << (2 * Q));  // padded token count
+    static constexpr int kChunks = kK / 128;                                  // 128-token K chunks
+    static constexpr int kBBytes = kRowsTile * kK;                            // staged B tile
+    static constexpr int kBankTileBytes = kBinTile * kRowBytes;
+    static_assert(kRowBytes * 8 == kK, "a bank row holds exactly the padded K bits");
+};
+
+// Scratch written by the prep kernel and read by the scan kernel.
+struct ScanScratch {
+    int32_t* class_count;  // [3] reads per digit class
+    int32_t* work;         // [1] work-item counter
+    uint8_t* rows[kNumClasses];   // digit rows, tiles of 128 rows x K bytes
+    int32_t* T[kNumClasses];      // thresholds per slot (INT_MAX: never passes)
+    uint32_t* rid[kNumClasses];   // read index per slot
+};
+
+struct ScanOut {
+    uint32_t* pair_read;
+    uint32_t* pair_bin;
+    uint16_t* pair_sum;          // nullable
+    int64_t cap;
+    unsigned long long* n_pairs;  // device counter
+    uint32_t* read_pass;         // nullable, per read
+};
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false when the CTA is aborting or the time limit expired
+// (then the abort flag is raised for every role of the CTA).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (now_ns() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(
+            taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]),
+        "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]),
+        "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// D[tmem] (+)= A[tmem] x B[smem], kind::f8f6f4.
+__device__ __forceinline__ void mma_f8f6f4_tmemA(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+// Shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);   // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: f32 accumulate, A and B e4m3, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f8(int M, int N) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// e4m3 bit pattern of an integer 0..15
+__device__ __forceinline__ uint32_t e4m3_small_int(uint32_t k) {
+    if (k == 0) return 0;
+    const uint32_t e = 31 - __clz(k);
+    const uint32_t m = ((k << 3) >> e) & 7u;
+    return ((e + 7u) << 3) | m;
+}
+
+// four bits -> four bytes, 0x00 or 0x38 (e4m3 1.0), bit i in byte i
+__device__ __forceinline__ uint32_t expand_nibble(uint32_t n) {
+    return ((n * 0x00204081u) & 0x01010101u) * 0x38u;
+}
+
+// ------------------------------------------------------------ prep kernel
+
+// Per read: token counts -> digit class -> digit rows (e4m3), threshold and
+// read index at the read's slot in its class.
+template <int Q>
+__global__ void __launch_bounds__(kPrepWarps * 32)
+scan_prep_kernel(const uint8_t* __restrict__ reads, const int64_t* __restrict__ read_offsets, int64_t n_reads,
+                 const uint16_t* __restrict__ E, ScanScratch sc, uint32_t* __restrict__ status) {
+    using G = ScanGeo<Q>;
+    constexpr int kCountWords = (G::kK + 1) / 2;  // u16 counts, two per word
+    extern __shared__ uint4 prep_smem[];
+    uint16_t* tab = reinterpret_cast<uint16_t*>(prep_smem);
+    uint32_t* counts_all = reinterpret_cast<uint32_t*>(prep_smem) + TokenTable<Q>::kWords;
+    build_token_table<Q>(tab);
+    for (int i = threadIdx.x; i < kPrepWarps * kCountWords; i += blockDim.x) counts_all[i] = 0;
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t* counts = counts_all + warp * kCountWords;
+    constexpr int kTPL = G::kK / 32;  // tokens (bytes of a row) per lane
+    uint32_t flags = 0;
+    const int64_t stride = (int64_t)gridDim.x * kPrepWarps;
+    for (int64_t r = (int64_t)blockIdx.x * kPrepWarps + warp; r < n_reads; r += stride) {
+        const int64_t ro = read_offsets[r], re = read_offsets[r + 1];
+        bool bad = false;
+        int L = 0;
+        if (re < ro) {
+            flags |= GRIM_FLAG_BAD_OFFSETS;
+            bad = true;
+        } else if (re - ro > GRIM_MAX_READ_LEN) {
+            flags |= GRIM_FLAG_LONG_READ;
+            bad = true;
+        } else {
+            L = (int)(re - ro);
+        }
+        uint32_t bad_base = 0;
+        for_each_token<Q>(reads + ro, L, lane, tab, bad_base, [&](uint32_t tok) {
+            atomicAdd(&counts[tok >> 1], 1u << (16 * (tok & 1)));
+        });
+        if (__any_sync(kFull, bad_base)) {
+            flags |= GRIM_FLAG_BAD_BASE;
+            bad = true;
+        }
+        __syncwarp();
+        // this lane's tokens [lane*kTPL, (lane+1)*kTPL)
+        uint32_t mx = 0;
+#pragma unroll
+        for (int j = 0; j < kTPL; j++) {
+            const int t = lane * kTPL + j;
+            const uint32_t cnt = (counts[t >> 1] >> (16 * (t & 1))) & 0xFFFFu;
+            mx = cnt > mx ? cnt : mx;
+        }
+        mx = __reduce_max_sync(kFull, mx);
+        const int cls = bad ? 0 : (mx <= 15u ? 0 : (mx <= 255u ? 1 : 2));
+        int slot = 0;
+        if (lane == 0) slot = atomicAdd(&sc.class_count[cls], 1);
+        slot = __shfl_sync(kFull, slot, 0);
+        const int nD = class_digits(cls), nR = class_reads(cls);
+        const int tile = slot / nR, n = slot % nR;
+        uint8_t* tile_rows = sc.rows[cls] + (size_t)tile * kRowsTile * G::kK;
+        for (int d = 0; d < nD; d++) {
+            uint32_t packed[kTPL / 4 > 0 ? kTPL / 4 : 1];
+#pragma unroll
+            for (int w = 0; w < (kTPL / 4 > 0 ? kTPL / 4 : 1); w++) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    const int t = lane * kTPL + 4 * w + b;
+                    const uint32_t cnt = bad ? 0u : ((counts[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
+                    word |= e4m3_small_int((cnt >> (4 * d)) & 15u) << (8 * b);
+                }
+                packed[w] = word;
+            }
+            uint32_t* dst = reinterpret_cast<uint32_t*>(tile_rows + (size_t)(d * nR + n) * G::kK + lane * kTPL);
+#pragma unroll
+            for (int w = 0; w < (kTPL / 4 > 0 ? kTPL / 4 : 1); w++) dst[w] = packed[w];
+        }
+        if (lane == 0) {
+            const int n_tok = L - Q + 1 > 0 ? L - Q + 1 : 0;
+            sc.T[cls][slot] = bad ? 0x7fffffff : n_tok - Q * (int)E[r];
+            sc.rid[cls][slot] = (uint32_t)r;
+        }
+        __syncwarp();
+        for (int i = lane; i < kCountWords; i += 32) counts[i] = 0;
+        __syncwarp();
+    }
+    flags = __reduce_or_sync(kFull, flags);
+    if (lane == 0 && flags) atomicOr(status, flags);
+}
+
+// ------------------------------------------------------------ scan kernel
+
+template <int Q>
+struct ScanSmem {
+    using G = ScanGeo<Q>;
+    static constexpr size_t kB = 0;                                     // 1024-aligned
+    static constexpr size_t kBank = kB + G::kBBytes;                    // 1024-aligned
+    static constexpr size_t kT = kBank + (size_t)kBankStages * G::kBankTileBytes;
+    static constexpr size_t kRid = kT + 4 * kRowsTile;
+    static constexpr size_t kBars = kRid + 4 * kRowsTile;
+    static constexpr size_t kMisc = kBars + 8 * (2 * kBankStages + 2 * kAStages + 5);
+    static constexpr size_t kTotal = kMisc + 64;
+    static constexpr size_t kAlloc = kTotal + 1024;  // slack to align the base
+};
+
+struct ScanParams {
+    const uint32_t* bank;
+    int64_t n_bins;
+    int64_t bin_begin, bin_end;
+    int64_t btiles_per_item;
+    ScanScratch sc;
+    ScanOut out;
+    uint32_t* status;
+};
+
+// Epilogue of one work item for reads with D base-16 digits (N = 128 / D
+// reads per tile): thread = bin row = TMEM lane of its warp's quadrant.
+template <int D>
+__device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem, uint64_t* acc_full,
+                                              uint64_t* acc_empty, volatile int* abort_flag,
+                                              const int32_t* __restrict__ sT, const uint32_t* __restrict__ sRid,
+                                              int valid_reads, int64_t bt0, int64_t bt1, uint32_t& acc_cnt) {
+    constexpr int N = kRowsTile / D;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quad = warp & 3;
+    const int m = quad * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    for (int64_t bt = bt0; bt < bt1; bt++) {
+        const uint32_t buf = acc_cnt & 1, phb = (acc_cnt >> 1) & 1;
+        if (!__all_sync(kFull, mbar_wait(&acc_full[buf], phb, abort_flag))) break;
+        tc_fence_after();
+        uint32_t v[kRowsTile];
+#pragma unroll
+        for (int cb = 0; cb < kRowsTile / 32; cb++)
+            tmem_ld32(tmem + lane_base + kAccCol + buf * kRowsTile + cb * 32, v + cb * 32);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        acc_cnt++;
+
+        const int64_t b = P.bin_begin + bt * kBinTile + m;
+        const bool bin_ok = b < P.bin_end;
+        // Sum(read n) = sum_d 16^d * acc[d*N + n]; partial sums are exact in f32
+        uint32_t any = 0;
+#pragma unroll
+        for (int n = 0; n < N; n++) {
+            int sum = 0;
+#pragma unroll
+            for (int d = 0; d < D; d++) sum += (int)__uint_as_float(v[d * N + n]) << (4 * d);
+            v[n] = (uint32_t)sum;
+            any |= (uint32_t)(sum >= sT[n]);
+        }
+        if (!__any_sync(kFull, bin_ok && any)) continue;
+        // rare: some (read, bin) passes; walk the reads with warp-aggregated appends
+        uint32_t loc[N];
+#pragma unroll
+        for (int n = 0; n < N; n++) loc[n] = v[n];
+        for (int n = 0; n < valid_reads; n++) {
+            const int sum = (int)loc[n];
+            const bool p = bin_ok && sum >= sT[n];
+            const uint32_t bal = __ballot_sync(kFull, p);
+            if (!bal) continue;
+            const int leader = __ffs(bal) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) {
+                base = atomicAdd(P.out.n_pairs, (unsigned long long)__popc(bal));
+                if (P.out.read_pass) atomicAdd(&P.out.read_pass[sRid[n]], (uint32_t)__popc(bal));
+            }
+            base = __shfl_sync(kFull, base, leader);
+            if (p) {
+                const unsigned long long idx = base + __popc(bal & ((1u << lane) - 1u));
+                if ((long long)idx < P.out.cap) {
+                    P.out.pair_read[idx] = sRid[n];
+                    P.out.pair_bin[idx] = (uint32_t)b;
+                    if (P.out.pair_sum) P.out.pair_sum[idx] = (uint16_t)sum;
+                } else {
+                    atomicOr(P.status, GRIM_FLAG_OVERFLOW);
+                }
+            }
+        }
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
+    using G = ScanGeo<Q>;
+    using S = ScanSmem<Q>;
+    extern __shared__ uint8_t scan_smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)scan_smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sB = smem + S::kB;
+    uint8_t* sBank = smem + S::kBank;
+    int32_t* sT = reinterpret_cast<int32_t*>(smem + S::kT);
+    uint32_t* sRid = reinterpret_cast<uint32_t*>(smem + S::kRid);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kBars);
+    uint64_t* bank_full = bars;
+    uint64_t* bank_empty = bars + kBankStages;
+    uint64_t* a_full = bars + 2 * kBankStages;
+    uint64_t* a_empty = a_full + kAStages;
+    uint64_t* acc_full = a_empty + kAStages;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain_bar = acc_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kMisc);
+    volatile int* s_item = reinterpret_cast<volatile int*>(smem + S::kMisc + 4);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + S::kMisc + 8);
+    volatile int* s_cls = reinterpret_cast<volatile int*>(smem + S::kMisc + 12);
+    volatile int* s_valid = reinterpret_cast<volatile int*>(smem + S::kMisc + 16);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kBankStages; i++) {
+            mbar_init(&bank_full[i], 1);
+            mbar_init(&bank_empty[i], 4);
+        }
+        for (int i = 0; i < kAStages; i++) {
+            mbar_init(&a_full[i], 4);
+            mbar_init(&a_empty[i], 1);
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 4);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    // work decomposition: classes' tile counts come from the prep kernel
+    int n_tiles[kNumClasses];
+    int total_tiles = 0;
+    for (int c = 0; c < kNumClasses; c++) {
+        const int cnt = P.sc.class_count[c];
+        n_tiles[c] = (cnt + class_reads(c) - 1) / class_reads(c);
+        total_tiles += n_tiles[c];
+    }
+    const int64_t n_btiles = (P.bin_end - P.bin_begin + kBinTile - 1) / kBinTile;
+    const int64_t n_chunks = (n_btiles + P.btiles_per_item - 1) / P.btiles_per_item;
+    const int64_t n_items = (int64_t)total_tiles * n_chunks;
+    constexpr uint32_t kIdesc = idesc_f8(kBinTile, kRowsTile);
+
+    // running pipeline counters (each role uses its own)
+    uint32_t bank_cnt = 0, a_cnt = 0, acc_cnt = 0;
+
+    while (true) {
+        if (threadIdx.x == 0) *s_item = atomicAdd(P.sc.work, 1);
+        __syncthreads();
+        const int64_t item = *s_item;
+        if (item >= n_items || *abort_flag) break;
+        const int64_t chunk = item / total_tiles;
+        int tile = (int)(item % total_tiles);
+        int cls = 0;
+        while (cls < kNumClasses - 1 && tile >= n_tiles[cls]) tile -= n_tiles[cls++];
+        const int nR = class_reads(cls);
+        const int valid_reads = min(nR, P.sc.class_count[cls] - tile * nR);
+        const int64_t bt0 = chunk * P.btiles_per_item;
+        const int64_t bt1 = min(n_btiles, bt0 + P.btiles_per_item);
+
+        // stage the read tile's digit rows (swizzled K-major), thresholds, read ids
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(P.sc.rows[cls] + (size_t)tile * G::kBBytes);
+            constexpr int kChunksPerRow = G::kK / 16;
+            for (int i = threadIdx.x; i < kRowsTile * kChunksPerRow; i += kScanThreads) {
+                const int row = i / kChunksPerRow, j = i % kChunksPerRow;
+                const int kb = j >> 3, cj = j & 7;
+                uint4 v = __ldg(src + i);
+                *reinterpret_cast<uint4*>(sB + kb * (kRowsTile * 128) + row * 128 + ((cj ^ (row & 7)) << 4)) = v;
+            }
+            for (int n = threadIdx.x; n < kRowsTile; n += kScanThreads) {
+                sT[n] = n < valid_reads ? P.sc.T[cls][tile * nR + n] : 0x7fffffff;
+                sRid[n] = n < valid_reads ? P.sc.rid[cls][tile * nR + n] : 0u;
+            }
+            if (threadIdx.x == 0) {
+                *s_cls = cls;
+                *s_valid = valid_reads;
+            }
+            fence_proxy_async_smem();
+        }
+        __syncthreads();
+
+        if (warp == 0) {
+            // ---- TMA producer: bank tiles into the ring
+            if (lane == 0) {
+                for (int64_t bt = bt0; bt < bt1; bt++) {
+                    const uint32_t s = bank_cnt % kBankStages, ph = (bank_cnt / kBankStages) & 1;
+                    if (!mbar_wait(&bank_empty[s], ph ^ 1, abort_flag)) break;
+                    const int64_t b0 = P.bin_begin + bt * kBinTile;
+                    const int rows = (int)((P.bin_end - b0) < kBinTile ? (P.bin_end - b0) : (int64_t)kBinTile);
+                    const uint32_t bytes = (uint32_t)rows * G::kRowBytes;
+                    mbar_arrive_expect_tx(&bank_full[s], bytes);
+                    bulk_copy_g2s(sBank + (size_t)s * G::kBankTileBytes, P.bank + (size_t)b0 * G::kRowWords, bytes,
+                                  &bank_full[s]);
+                    bank_cnt++;
+                }
+            }
+        } else if (warp == 1) {
+            // ---- MMA issuer
+            if (lane == 0) {
+                for (int64_t bt = bt0; bt < bt1; bt++) {
+                    const uint32_t buf = acc_cnt & 1, phb = (acc_cnt >> 1) & 1;
+                    if (!mbar_wait(&acc_empty[buf], phb ^ 1, abort_flag)) break;
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem + kAccCol + buf * kRowsTile;
+                    bool ok = true;
+                    for (int c = 0; c < G::kChunks; c++) {
+                        const uint32_t sa = a_cnt % kAStages, pha = (a_cnt / kAStages) & 1;
+                        if (!mbar_wait(&a_full[sa], pha, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+#pragma unroll
+                        for (int kk = 0; kk < 4; kk++) {
+                            const uint32_t a_tmem = tmem + kACol + sa * kACols + kk * 8;
+                            const uint64_t bdesc = smem_desc_sw128(smem_addr(sB) + c * (kRowsTile * 128) + kk * 32);
+                            mma_f8f6f4_tmemA(d_tmem, a_tmem, bdesc, kIdesc, (c | kk) != 0);
+                        }
+                        mma_commit(&a_empty[sa]);
+                        a_cnt++;
+                    }
+                    if (!ok) break;
+                    mma_commit(&acc_full[buf]);
+                    acc_cnt++;
+                }
+            }
+        } else if (warp < 6) {
+            // ---- expanders: thread = bin row = TMEM lane
+            const int quad = warp & 3;
+            const int m = quad * 32 + lane;
+            const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+            for (int64_t bt = bt0; bt < bt1; bt++) {
+                const uint32_t s = bank_cnt % kBankStages, ph = (bank_cnt / kBankStages) & 1;
+                if (!__all_sync(kFull, mbar_wait(&bank_full[s], ph, abort_flag))) break;
+                const int64_t b0 = P.bin_begin + bt * kBinTile;
+                const int rows = (int)((P.bin_end - b0) < kBinTile ? (P.bin_end - b0) : (int64_t)kBinTile);
+                const uint4* myrow = reinterpret_cast<const uint4*>(sBank + (size_t)s * G::kBankTileBytes +
+                                                                    (size_t)m * G::kRowBytes);
+                bool ok = true;
+                for (int c = 0; c < G::kChunks; c++) {
+                    const uint4 bits = (m < rows) ? myrow[c] : make_uint4(0, 0, 0, 0);
+                    const uint32_t sa = a_cnt % kAStages, pha = (a_cnt / kAStages) & 1;
+                    if (!__all_sync(kFull, mbar_wait(&a_empty[sa], pha ^ 1, abort_flag))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    uint32_t v[32];
+                    const uint32_t w[4] = {bits.x, bits.y, bits.z, bits.w};
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+#pragma unroll
+                        for (int i = 0; i < 8; i++) v[j * 8 + i] = expand_nibble((w[j] >> (4 * i)) & 0xFu);
+                    tmem_st32(tmem + lane_base + kACol + sa * kACols, v);
+                    tmem_wait_st();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&a_full[sa]);
+                    a_cnt++;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bank_empty[s]);
+                bank_cnt++;
+                if (!ok) break;
+            }
+        } else {
+            // ---- epilogue: thread = bin row = TMEM lane
+            const int cls_now = *s_cls;
+            if (cls_now == 0)
+                scan_epilogue<1>(P, tmem, acc_full, acc_empty, abort_flag, sT, sRid, *s_valid, bt0, bt1, acc_cnt);
+            else if (cls_now == 1)
+                scan_epilogue<2>(P, tmem, acc_full, acc_empty, abort_flag, sT, sRid, *s_valid, bt0, bt1, acc_cnt);
+            else
+                scan_epilogue<4>(P, tmem, acc_full, acc_empty, abort_flag, sT, sRid, *s_valid, bt0, bt1, acc_cnt);
+        }
+        __syncthreads();  // the item is drained before B is overwritten
+    }
+
+    // drain: no bulk copy or MMA may still target this CTA's memory
+    __syncthreads();
+    if (*abort_flag) {
+        if (threadIdx.x == 0) {
+            atomicOr(P.status, GRIM_FLAG_TIMEOUT);
+            // the newest copy issued into each ring stage (older ones completed before it was issued)
+            for (uint32_t g = bank_cnt > kBankStages ? bank_cnt - kBankStages : 0; g < bank_cnt; g++) {
+                const unsigned long long t0 = now_ns();
+                while (!mbar_try_wait(&bank_full[g % kBankStages], (g / kBankStages) & 1) &&
+                       now_ns() - t0 < kWaitLimitNs) {
+                }
+            }
+        }
+        if (threadIdx.x == 32) {  // every MMA this thread issued has finished once drain_bar completes
+            mma_commit(drain_bar);
+            const unsigned long long t0 = now_ns();
+            while (!mbar_try_wait(drain_bar, 0) && now_ns() - t0 < kWaitLimitNs) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ------------------------------------------------------------ host launch
+
+template <int Q>
+static int launch_scan_q(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                         const uint16_t* E, int64_t bin_begin, int64_t bin_end, const ScanOut& out, void* scratch,
+                         cudaStream_t s) {
+    using G = ScanGeo<Q>;
+    // scratch layout (see scan_scratch_bytes)
+    uint8_t* p = (uint8_t*)scratch;
+    ScanScratch sc;
+    sc.class_count = (int32_t*)p;
+    sc.work = (int32_t*)(p + 16);
+    p += 256;
+    for (int c = 0; c < kNumClasses; c++) {
+        const int64_t tiles = (n_reads + class_reads(c) - 1) / class_reads(c);
+        sc.rows[c] = p;
+        p += (size_t)tiles * G::kBBytes;
+        sc.T[c] = (int32_t*)p;
+        p += ((size_t)tiles * class_reads(c) * 4 + 255) & ~(size_t)255;
+        sc.rid[c] = (uint32_t*)p;
+        p += ((size_t)tiles * class_reads(c) * 4 + 255) & ~(size_t)255;
+    }
+    GRIM_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
+    GRIM_CUDA_TRY(cudaMemsetAsync(out.n_pairs, 0, sizeof(unsigned long long), s));
+    if (out.read_pass) GRIM_CUDA_TRY(cudaMemsetAsync(out.read_pass, 0, (size_t)n_reads * 4, s));
+
+    {
+        constexpr size_t smem = 4 * ((size_t)TokenTable<Q>::kWords + (size_t)kPrepWarps * ((G::kK + 1) / 2));
+        const int64_t need = (n_reads + kPrepWarps - 1) / kPrepWarps;
+        const int64_t cap = (int64_t)sm_count() * 16;
+        const int64_t blocks = need < cap ? need : cap;
+        scan_prep_kernel<Q><<<(unsigned)blocks, kPrepWarps * 32, smem, s>>>(reads, read_offsets, n_reads, E, sc,
+                                                                            bank->status);
+        GRIM_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        constexpr size_t smem = ScanSmem<Q>::kAlloc;
+        static bool attr = false;
+        if (!attr) {
+            GRIM_CUDA_TRY(cudaFuncSetAttribute(scan_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = true;
+        }
+        ScanParams P;
+        P.bank = bank->bits;
+        P.n_bins = bank->n_bins;
+        P.bin_begin = bin_begin;
+        P.bin_end = bin_end;
+        const int64_t n_btiles = (bin_end - bin_begin + kBinTile - 1) / kBinTile;
+        const int64_t read_tiles = (n_reads + kRowsTile - 1) / kRowsTile;
+        const int64_t want_items = 4LL * sm_count();
+        int64_t per = (n_btiles * read_tiles + want_items - 1) / want_items;
+        per = per < 1 ? 1 : (per > 1024 ? 1024 : per);
+        P.btiles_per_item = per;
+        P.sc = sc;
+        P.out = out;
+        P.status = bank->status;
+        scan_kernel<Q><<<sm_count(), kScanThreads, smem, s>>>(P);
+        GRIM_CUDA_TRY(cudaGetLastError());
+    }
+    return GRIM_OK;
+}
+
+size_t scan_scratch_bytes(int q, int64_t n_reads) {
+    const int64_t K = (int64_t(1) << (2 * q)) < 128 ? 128 : (int64_t(1) << (2 * q));
+    size_t total = 256;
+    for (int c = 0; c < kNumClasses; c++) {
+        const int64_t tiles = (n_reads + class_reads(c) - 1) / class_reads(c);
+        total += (size_t)tiles * kRowsTile * K;
+        total += 2 * (((size_t)tiles * class_reads(c) * 4 + 255) & ~(size_t)255);
+    }
+    return total;
+}
+
+int launch_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,
+                uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* scratch,
+                cudaStream_t s) {
+    ScanOut out;
+    out.pair_read = pair_read;
+    out.pair_bin = pair_bin;
+    out.pair_sum = pair_sum;
+    out.cap = cap;
+    out.n_pairs = reinterpret_cast<unsigned long long*>(n_pairs);
+    out.read_pass = read_pass;
+    switch (bank->q) {
+        case 1: return launch_scan_q<1>(bank, reads, read_offsets, n_reads, E, bin_begin, bin_end, out, scratch, s);
+        case 2: return launch_scan_q<2>(bank, reads, read_offsets, n_reads, E, bin_begin, bin_end, out, scratch, s);
+        case 3: return launch_scan_q<3>(bank, reads, read_offsets, n_reads, E, bin_begin, bin_end, out, scratch, s);
+        case 4: return launch_scan_q<4>(bank, reads, read_offsets, n_reads, E, bin_begin, bin_end, out, scratch, s);
+        case 5: return launch_scan_q<5>(bank, reads, read_offsets, n_reads, E, bin_begin, bin_end, out, scratch, s);
+        default: return GRIM_ENOTSUP;
+    }
+}
+
+}  // namespace grim

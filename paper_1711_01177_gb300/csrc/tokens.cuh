@@ -1,0 +1,68 @@
+// Warp-level q-gram token roller shared by the gather and full-scan kernels
+// (Sec. 3.2 step 1: every token of the read).
+//
+// A warp reads a read 32 bases at a time.  Two ballots per 32 bases give the
+// low and high bits of every base code; a funnel shift lines up the q bases
+// starting at a lane's position; a table of 4^q entries (built once per CTA
+// in shared memory) maps those 2q bits to the token value, first base most
+// significant.
+#pragma once
+
+#include "grim_internal.cuh"
+
+namespace grim {
+
+template <int Q>
+struct TokenTable {
+    static constexpr int kEntries = 1 << (2 * Q);
+    static constexpr int kWords = (kEntries * 2 + 15) / 16 * 4;  // u16 entries, 16-byte padded
+};
+
+// All threads of the CTA; follow with __syncthreads().
+template <int Q>
+__device__ __forceinline__ void build_token_table(uint16_t* tab) {
+    for (int idx = threadIdx.x; idx < TokenTable<Q>::kEntries; idx += blockDim.x) {
+        uint32_t tok = 0;
+#pragma unroll
+        for (int k = 0; k < Q; k++) {
+            const uint32_t code = (((idx >> (Q + k)) & 1u) << 1) | ((idx >> k) & 1u);
+            tok = (tok << 2) | code;
+        }
+        tab[idx] = (uint16_t)tok;
+    }
+}
+
+// Calls f(token) on the lane that owns each token position i (i + Q <= L).
+// Whole warp, L warp-uniform.  bad_base collects codes > 3 (then the tokens
+// use the code's low two bits; the caller rejects the read).
+template <int Q, typename F>
+__device__ __forceinline__ void for_each_token(const uint8_t* __restrict__ rd, int L, int lane,
+                                               const uint16_t* __restrict__ tab, uint32_t& bad_base, F&& f) {
+    constexpr uint32_t kQMask = (1u << Q) - 1;
+    for (int s0 = 0; s0 < L; s0 += 256) {
+        uint32_t c[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const int i = s0 + 32 * k + lane;
+            c[k] = (s0 + 32 * k < L && i < L) ? __ldg(rd + i) : 0u;
+            bad_base |= (uint32_t)(c[k] > 3u);
+        }
+        uint32_t lo_c = __ballot_sync(kFull, c[0] & 1u), hi_c = __ballot_sync(kFull, c[0] & 2u);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if (s0 + 32 * k >= L) break;  // warp-uniform
+            const uint32_t lo_n = __ballot_sync(kFull, c[k + 1] & 1u);
+            const uint32_t hi_n = __ballot_sync(kFull, c[k + 1] & 2u);
+            const int i = s0 + 32 * k + lane;
+            if (i + Q <= L) {
+                const uint32_t xl = __funnelshift_r(lo_c, lo_n, lane) & kQMask;
+                const uint32_t xh = __funnelshift_r(hi_c, hi_n, lane) & kQMask;
+                f((uint32_t)tab[(xh << Q) | xl]);
+            }
+            lo_c = lo_n;
+            hi_c = hi_n;
+        }
+    }
+}
+
+}  // namespace grim
