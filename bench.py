@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--ref-bp", type=int, default=100_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--workload", default="gather", choices=["gather", "fullscan"],
+                    help="gather: 100 Mbp / 1M x 150 bp seed candidates; fullscan: 3.1 Gbp, 65,536 x 100 bp, all bins")
+    ap.add_argument("--no-full-scan", action="store_true", help="skip the full-scan sub-measurement")
+    ap.add_argument("--scan-ref-bp", type=int, default=3_100_000_000)
+    ap.add_argument("--scan-reads", type=int, default=65_536)
+    ap.add_argument("--scan-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -89,6 +95,80 @@ def load_peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def load_fp8_peak():
+    """Dense e4m3 tensor peak: the measured bf16 cuBLAS peak x the nominal
+    fp8 / bf16 ratio (4.5 / 2.25 PFLOP/s)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["bf16_tflops"]) * 2.0, float(d.get("bf16_tflops_sustained", d["bf16_tflops"])) * 2.0, "measured bf16 x 2"
+    return 1900.0 * 2.0, 1700.0 * 2.0, "fallback bf16 x 2"
+
+
+def measure_full_scan(args, rank, dev, stream, with_cpu):
+    """Full-scan form: one batch of reads against every bin of a genome-scale
+    reference on the tensor cores.  Returns a dict (one grim_scan per step)."""
+    import torch
+
+    import paper_1711_01177_gb300 as grim
+    import synth
+    w = synth.fullscan(ref_len=args.scan_ref_bp, n_reads=args.scan_reads)
+    bank = grim.grim_build_bank(dev(w.ref2bit), w.ref_len, w.q, w.bin_len, w.overlap)
+    st, flags = grim.grim_bank_status(bank)
+    assert st == grim.GRIM_OK, (st, flags)
+    reads_d, roff_d, E_d = dev(w.bases), dev(w.read_offsets), dev(w.E)
+    cap = 1 << 24
+    res = grim.grim_scan(bank, reads_d, roff_d, E_d, cap=cap)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    for _ in range(1):
+        flush.fill_(1)
+        grim.grim_scan(bank, reads_d, roff_d, E_d, out=res)
+    torch.cuda.synchronize()
+    times = []
+    for i in range(args.scan_steps):
+        flush.fill_(i)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        grim.grim_scan(bank, reads_d, roff_d, E_d, out=res)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    st, flags = grim.grim_bank_status(bank)
+    assert st == grim.GRIM_OK, (st, flags)
+    n_pairs = res.n_pairs
+    ms = float(np.mean(times))
+    checks = w.n_reads * w.n_bins
+    flops = 2.0 * checks * (4 ** w.q)
+    peak, peak_sust, src = load_fp8_peak()
+    achieved = flops / (ms / 1e3) / 1e12
+    out = {"workload": f"full scan, {w.ref_len / 1e9:g} Gbp repeat-rich reference "
+                       f"({int(w.meta['repeat_frac'] * 100)}% repeats), {w.n_bins} bins, batch of {w.n_reads} x "
+                       f"{int(np.diff(w.read_offsets)[0])} bp reads, E={int(w.E[0])}",
+           "value": checks / (ms / 1e3), "unit": UNIT, "reads_per_s": w.n_reads / (ms / 1e3), "ms_per_batch": ms,
+           "steps": args.scan_steps, "pairs_passing": n_pairs,
+           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "peak_source": f"{src} (e4m3 dense), burst", "kernel": f"scan_kernel<{w.q}> (+ scan_prep)",
+                        "algorithmic_flops_per_launch": flops, "avg_launch_ms": ms,
+                        "frac_of_sustained": achieved / peak_sust},
+           "dtype": "e4m3 x e4m3 -> f32 (exact small integers)"}
+    if with_cpu:
+        import oracle
+        o = oracle.Oracle()
+        nb = 20_000
+        prefix = nb * w.bin_len + w.overlap
+        ob = o.build_bank(synth.pack2bit(w.codes[:prefix]), prefix, w.q, w.bin_len, w.overlap)[:nb]
+        nr = 64
+        t = time.perf_counter()
+        o.scan(ob, w.q, w.bases[:w.read_offsets[nr]], w.read_offsets[:nr + 1], w.E[:nr])
+        dt = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": nr * nb / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"first {nr} reads x first {nb} bins of the same workload, single thread"}
+    bank.free()
+    del res
+    return out
 
 
 class ClockSampler:
@@ -346,8 +426,15 @@ def run_ours(args):
             line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
         else:
             line["cpu_baseline"] = None
-        print(json.dumps(line), flush=True)
     bank.free()
+    del reads_d, roff_d, cb_d, co_d, E_d, pass_d, flush, h_in, h_out
+    torch.cuda.empty_cache()
+    if not args.no_full_scan:
+        fs = measure_full_scan(args, rank, dev, stream, with_cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+        if rank == 0:
+            line["full_scan"] = fs
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
