@@ -44,6 +44,7 @@ extern "C" {
 #define GRIM_EOVERFLOW 5 /* an output list exceeded the capacity given */
 #define GRIM_ETIMEOUT 6  /* a bounded device-side wait ran out */
 #define GRIM_ENOTSUP 7   /* parameters outside what the kernels implement */
+#define GRIM_ESCRATCH 8  /* the request needs more than grim_scan_noalloc's fixed scratch */
 
 /* ---- device status flags (grim_bank_status) --------------------------- */
 #define GRIM_FLAG_BAD_BASE 0x1u    /* a read holds a code > 3 */
@@ -145,6 +146,34 @@ int grim_filter(const grim_bank* bank, const uint8_t* reads, const int64_t* read
 int grim_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
               const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,
               uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* stream);
+
+/*
+ * grim_scan_noalloc - grim_scan that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they call the filter, for example a
+ * process whose device memory is all owned by its own pool allocator (so a
+ * cudaMallocAsync from this library could fail or fragment that pool), or
+ * a service that fixes its device footprint at start-up and must not grow
+ * it while serving.  Arguments, outputs and results are those of grim_scan.
+ *
+ * Its working memory is one array of GRIM_SCAN_NOALLOC_SCRATCH_BYTES
+ * (64 MiB) compiled into the library: every GPU on which the library is
+ * loaded holds it until the process exits.  A call needing more is
+ * rejected with GRIM_ESCRATCH before anything is enqueued; the need is
+ * 256 + sum over c = 0, 1, 2 of ceil(n_reads / (128 >> c)) * 128 * K bytes
+ * (K = max(128, 4^q)) plus two small index arrays per c, which allows at
+ * most 9,312 reads per call at q = 5, 36,928 at q = 4, 72,928 at q <= 3.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any
+ * stream capture.  Every call uses the same array and finds the previous
+ * call's contents in it (each call clears what must start at zero), so
+ * calls whose work overlaps on the GPU - on different streams or from
+ * different host threads - race on it: the caller must serialise them.
+ */
+#define GRIM_SCAN_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int grim_scan_noalloc(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                      const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,
+                      uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* stream);
 
 #ifdef __cplusplus
 }

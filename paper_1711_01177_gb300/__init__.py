@@ -16,7 +16,9 @@ import torch
 from ._build import LIB as _LIB_PATH
 from ._build import build as _build_lib
 
-GRIM_OK, GRIM_EINVAL, GRIM_EDATA, GRIM_ENOMEM, GRIM_ECUDA, GRIM_EOVERFLOW, GRIM_ETIMEOUT, GRIM_ENOTSUP = range(8)
+(GRIM_OK, GRIM_EINVAL, GRIM_EDATA, GRIM_ENOMEM, GRIM_ECUDA, GRIM_EOVERFLOW, GRIM_ETIMEOUT, GRIM_ENOTSUP,
+ GRIM_ESCRATCH) = range(9)
+GRIM_SCAN_NOALLOC_SCRATCH_BYTES = 64 << 20
 GRIM_FLAG_BAD_BASE = 0x1
 GRIM_FLAG_BAD_BIN = 0x2
 GRIM_FLAG_BAD_OFFSETS = 0x4
@@ -38,6 +40,7 @@ SIGNATURES = {
     "grim_bank_free": (_I32, [_P]),
     "grim_filter": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
     "grim_scan": (_I32, [_P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P]),
+    "grim_scan_noalloc": (_I32, [_P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P]),
 }
 
 _lib = None
@@ -198,7 +201,7 @@ class ScanResult:
 
 def grim_scan(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, E: torch.Tensor, bin_begin: int = 0,
               bin_end: int | None = None, cap: int = 1 << 20, with_sums: bool = True, with_read_pass: bool = False,
-              out: ScanResult | None = None, stream=None) -> ScanResult:
+              out: ScanResult | None = None, stream=None, _entry: str = "grim_scan") -> ScanResult:
     """Every read against every bin of [bin_begin, bin_end) on the tensor
     cores (Sec. 3.2 over the bin window of Sec. 6.1).  Pairs beyond `cap`
     are counted but not written (GRIM_FLAG_OVERFLOW)."""
@@ -217,9 +220,19 @@ def grim_scan(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, E: to
         cap_eff = cap
     else:
         cap_eff = out.pair_read.numel()
-    _check(load().grim_scan(bank.handle, _dev_ptr(reads, "reads", 1), _dev_ptr(read_offsets, "read_offsets", 8),
+    _check(getattr(load(), _entry)(bank.handle, _dev_ptr(reads, "reads", 1), _dev_ptr(read_offsets, "read_offsets", 8),
                             n_reads, _dev_ptr(E, "E", 2), bin_begin, bin_end, _dev_ptr(out.pair_read, "pair_read", 4),
                             _dev_ptr(out.pair_bin, "pair_bin", 4), _dev_ptr(out.pair_sum, "pair_sum", 2, True), cap_eff,
                             _dev_ptr(out.n_pairs_dev, "n_pairs", 8), _dev_ptr(out.read_pass, "read_pass", 4, True),
-                            _stream_ptr(stream)), "grim_scan")
+                            _stream_ptr(stream)), _entry)
     return out
+
+
+def grim_scan_noalloc(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, E: torch.Tensor,
+                      bin_begin: int = 0, bin_end: int | None = None, cap: int = 1 << 20, with_sums: bool = True,
+                      with_read_pass: bool = False, out: ScanResult | None = None, stream=None) -> ScanResult:
+    """grim_scan without device allocation, for callers that cannot allocate
+    when they call the filter: the library's fixed 64 MiB scratch is used
+    instead (GRIM_ESCRATCH beyond it; overlapping calls race on it)."""
+    return grim_scan(bank, reads, read_offsets, E, bin_begin, bin_end, cap, with_sums, with_read_pass, out, stream,
+                     _entry="grim_scan_noalloc")

@@ -41,6 +41,7 @@ const char* grim_strerror(int status) {
         case GRIM_EOVERFLOW: return "output capacity exceeded";
         case GRIM_ETIMEOUT: return "bounded device-side wait ran out";
         case GRIM_ENOTSUP: return "parameters not supported by the kernels";
+        case GRIM_ESCRATCH: return "request exceeds the fixed scratch of the allocation-free scan";
         default: return "unknown status";
     }
 }
@@ -180,6 +181,32 @@ int grim_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_o
     if (rc != GRIM_OK) return rc;
     GRIM_CUDA_TRY(e);
     return GRIM_OK;
+}
+
+int grim_scan_noalloc(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                      const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,
+                      uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* stream) {
+    if (!bank || n_reads < 0 || cap < 0 || !n_pairs) return GRIM_EINVAL;
+    if (bin_begin < 0 || bin_end > bank->n_bins || bin_begin > bin_end) return GRIM_EINVAL;
+    if (cap > 0 && (!pair_read || !pair_bin)) return GRIM_EINVAL;
+    if (bank->q > GRIM_MAX_SCAN_Q) return GRIM_ENOTSUP;
+    if (n_reads > ((int64_t)1 << 30)) return GRIM_ESCRATCH;
+    int rc = grim::check_device(bank);
+    if (rc != GRIM_OK) return rc;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    rc = grim::scan_noalloc_scratch(&scratch, &scratch_bytes);
+    if (rc != GRIM_OK) return rc;
+    if (grim::scan_scratch_bytes(bank->q, n_reads) > scratch_bytes) return GRIM_ESCRATCH;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_reads == 0 || bin_begin == bin_end) {
+        GRIM_CUDA_TRY(cudaMemsetAsync(n_pairs, 0, sizeof(int64_t), s));
+        if (read_pass && n_reads > 0) GRIM_CUDA_TRY(cudaMemsetAsync(read_pass, 0, (size_t)n_reads * 4, s));
+        return GRIM_OK;
+    }
+    if (!reads || !read_offsets || !E) return GRIM_EINVAL;
+    return grim::launch_scan(bank, reads, read_offsets, n_reads, E, bin_begin, bin_end, pair_read, pair_bin, pair_sum,
+                             cap, n_pairs, read_pass, scratch, s);
 }
 
 }  // extern "C"

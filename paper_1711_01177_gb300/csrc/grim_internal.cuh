@@ -49,6 +49,10 @@ int launch_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read
                 uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* scratch,
                 cudaStream_t stream);
 
+// Device address and size of the fixed scratch of grim_scan_noalloc
+// (looked up once per device, with that device current).
+int scan_noalloc_scratch(void** ptr, size_t* bytes);
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 

@@ -36,10 +36,18 @@
 //         (read, bin, sum) triples with warp-aggregated atomics.
 // Every wait is an mbarrier try_wait bounded by a time limit; on expiry the
 // CTA raises GRIM_FLAG_TIMEOUT, drains and frees its tensor memory.
+#include <mutex>
+
 #include "grim_internal.cuh"
 #include "tokens.cuh"
 
 namespace grim {
+
+// Working memory of grim_scan_noalloc: a fixed array in every device image
+// of the library, for callers that cannot allocate device memory.  Host code
+// must not pass the name itself to a kernel (on the host it is a stand-in,
+// not a device address); scan_noalloc_scratch() looks the address up.
+static __device__ __align__(256) uint8_t g_scan_scratch[GRIM_SCAN_NOALLOC_SCRATCH_BYTES];
 
 // ------------------------------------------------------------ constants
 
@@ -704,6 +712,23 @@ static int launch_scan_q(const grim_bank* bank, const uint8_t* reads, const int6
         scan_kernel<Q><<<sm_count(), kScanThreads, smem, s>>>(P);
         GRIM_CUDA_TRY(cudaGetLastError());
     }
+    return GRIM_OK;
+}
+
+int scan_noalloc_scratch(void** ptr, size_t* bytes) {
+    static std::mutex mu;
+    static void* addr[64] = {nullptr};
+    int dev = -1;
+    GRIM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GRIM_ENOTSUP;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        GRIM_CUDA_TRY(cudaGetSymbolAddress(&p, g_scan_scratch));
+        addr[dev] = p;
+    }
+    *ptr = addr[dev];
+    *bytes = sizeof(g_scan_scratch);
     return GRIM_OK;
 }
 
