@@ -125,6 +125,45 @@ int grim_filter(const grim_bank* bank, const uint8_t* reads, const int64_t* read
                 uint16_t* sums, void* stream);
 
 /*
+ * Launch shape of the batched filter.  Zero fields take defaults.
+ */
+typedef struct grim_tune {
+    int32_t warps_per_cta;   /* 4 or 8 (default 8) */
+    int32_t reads_per_claim; /* reads a warp claims from the work counter at a time (default 1) */
+    int32_t ctas_per_sm;     /* resident CTAs per SM, up to the occupancy limit (default: the limit) */
+    int32_t use_graph;       /* 1: capture the launches in a CUDA graph, replayed by identical calls */
+    int64_t batch_reads;     /* reads per persistent launch (default 262,144) */
+} grim_tune;
+
+/*
+ * Batched gather filter: the same outputs as grim_filter, computed by one
+ * persistent launch per batch of `batch_reads` reads in which every warp
+ * claims reads from a device work counter, so reads of uneven length and
+ * uneven candidate lists balance across the GPU.  With use_graph, the
+ * call's launches are captured once into a CUDA graph and an identical
+ * later call (same pointers, sizes, tune and stream) replays it; a stream
+ * that is already capturing simply records the launches.  tune == NULL
+ * uses the last grim_autotune result for this bank's q on this device,
+ * else the defaults with use_graph = 1.  The work counters live in the
+ * bank: batched calls on one bank that overlap on the GPU without a graph
+ * of their own must be serialised.
+ */
+int grim_filter_batched(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                        const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
+                        uint16_t* sums, const grim_tune* tune, void* stream);
+
+/*
+ * Autotuner of the batched filter: times every launch shape it knows
+ * (warps per CTA x reads per claim x CTAs per SM) on the first batch of the
+ * given workload, writes the fastest to *out (host), and remembers it for
+ * grim_filter_batched(tune = NULL) with this bank's q on this device.
+ * Synchronises `stream`; `pass` is overwritten.
+ */
+int grim_autotune(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                  const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
+                  grim_tune* out, void* stream);
+
+/*
  * Full-scan form: the filter of Sec. 3.2 for every read against every bin
  * of the window [bin_begin, bin_end) (the paper's bin window, Sec. 6.1,
  * with every bin checked), computed as the contraction

@@ -41,7 +41,18 @@ SIGNATURES = {
     "grim_filter": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
     "grim_scan": (_I32, [_P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P]),
     "grim_scan_noalloc": (_I32, [_P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P]),
+    "grim_filter_batched": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
+    "grim_autotune": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
 }
+
+
+class GrimTune(ctypes.Structure):
+    """Launch shape of grim_filter_batched (zero fields take defaults)."""
+    _fields_ = [("warps_per_cta", ctypes.c_int32), ("reads_per_claim", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("batch_reads", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 _lib = None
 
@@ -236,3 +247,38 @@ def grim_scan_noalloc(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tenso
     instead (GRIM_ESCRATCH beyond it; overlapping calls race on it)."""
     return grim_scan(bank, reads, read_offsets, E, bin_begin, bin_end, cap, with_sums, with_read_pass, out, stream,
                      _entry="grim_scan_noalloc")
+
+
+def grim_filter_batched(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, cand_bins: torch.Tensor,
+                        cand_offsets: torch.Tensor, E: torch.Tensor, pass_out: torch.Tensor | None = None,
+                        sums: torch.Tensor | None = None, tune: GrimTune | None = None, stream=None) -> torch.Tensor:
+    """grim_filter's outputs from persistent launches, one per batch of reads,
+    captured in a CUDA graph that identical later calls replay."""
+    n_reads = read_offsets.numel() - 1
+    if n_reads < 0 or cand_offsets.numel() != n_reads + 1 or E.numel() != n_reads:
+        raise ValueError("read_offsets / cand_offsets / E sizes do not match")
+    if pass_out is None:
+        pass_out = torch.empty(cand_bins.numel(), dtype=torch.uint8, device=cand_bins.device)
+    _check(load().grim_filter_batched(bank.handle, _dev_ptr(reads, "reads", 1),
+                                      _dev_ptr(read_offsets, "read_offsets", 8), n_reads,
+                                      _dev_ptr(cand_bins, "cand_bins", 4), _dev_ptr(cand_offsets, "cand_offsets", 8),
+                                      _dev_ptr(E, "E", 2), _dev_ptr(pass_out, "pass", 1),
+                                      _dev_ptr(sums, "sums", 2, True), ctypes.byref(tune) if tune is not None else None,
+                                      _stream_ptr(stream)), "grim_filter_batched")
+    return pass_out
+
+
+def grim_autotune(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, cand_bins: torch.Tensor,
+                  cand_offsets: torch.Tensor, E: torch.Tensor, pass_out: torch.Tensor | None = None,
+                  stream=None) -> GrimTune:
+    """Time the batched filter's launch shapes on the first batch; returns the
+    fastest (also remembered for grim_filter_batched(tune=None))."""
+    n_reads = read_offsets.numel() - 1
+    if pass_out is None:
+        pass_out = torch.empty(cand_bins.numel(), dtype=torch.uint8, device=cand_bins.device)
+    t = GrimTune()
+    _check(load().grim_autotune(bank.handle, _dev_ptr(reads, "reads", 1), _dev_ptr(read_offsets, "read_offsets", 8),
+                                n_reads, _dev_ptr(cand_bins, "cand_bins", 4),
+                                _dev_ptr(cand_offsets, "cand_offsets", 8), _dev_ptr(E, "E", 2),
+                                _dev_ptr(pass_out, "pass", 1), ctypes.byref(t), _stream_ptr(stream)), "grim_autotune")
+    return t

@@ -71,15 +71,19 @@ int grim_build_bank(const uint8_t* ref2bit, int64_t len, int q, int bin_len, int
         return GRIM_ECUDA;
     }
     const size_t bytes = (size_t)n_bins * (size_t)rw * 4;
+    const size_t tail = ((bytes + 255) & ~(size_t)255);  // status word, then the work counters
     void* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, bytes + 256);
+    cudaError_t e = cudaMalloc(&mem, tail + 256 + 8 * (1 + grim::kGraphCache));
     if (e != cudaSuccess) {
         grim::set_last_cuda_error(e);
         delete bank;
         return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
     }
     bank->bits = (uint32_t*)mem;
-    bank->status = (uint32_t*)((char*)mem + ((bytes + 255) & ~(size_t)255));
+    bank->status = (uint32_t*)((char*)mem + tail);
+    bank->counters = (unsigned long long*)((char*)mem + tail + 256);
+    bank->graphs = new std::vector<grim::GraphEntry>();
+    bank->graph_clock = 0;
     int rc = GRIM_OK;
     e = cudaMemsetAsync(bank->status, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) {
@@ -90,6 +94,7 @@ int grim_build_bank(const uint8_t* ref2bit, int64_t len, int q, int bin_len, int
     }
     if (rc != GRIM_OK) {
         cudaFree(mem);
+        delete bank->graphs;
         delete bank;
         return rc;
     }
@@ -134,6 +139,10 @@ int grim_bank_free(grim_bank* bank) {
     cudaGetDevice(&prev);
     if (prev != bank->device) cudaSetDevice(bank->device);
     cudaError_t e1 = cudaDeviceSynchronize();
+    if (bank->graphs) {
+        for (grim::GraphEntry& g : *bank->graphs) cudaGraphExecDestroy(g.exec);
+        delete bank->graphs;
+    }
     cudaError_t e2 = cudaFree(bank->bits);
     if (prev >= 0 && prev != bank->device) cudaSetDevice(prev);
     delete bank;

@@ -53,8 +53,8 @@ struct GatherGeo {
 };
 
 template <int Q>
-constexpr size_t gather_smem_bytes() {
-    return 4 * ((size_t)GatherGeo<Q>::kTabWords + (size_t)kGatherWarps * GatherGeo<Q>::kPlaneWords);
+constexpr size_t gather_smem_bytes(int warps = kGatherWarps) {
+    return 4 * ((size_t)GatherGeo<Q>::kTabWords + (size_t)warps * GatherGeo<Q>::kPlaneWords);
 }
 
 __device__ __forceinline__ uint32_t and_popc(const uint4& a, const uint4& b) {
@@ -159,6 +159,94 @@ __device__ __forceinline__ void write_constant(int64_t co, int64_t ce, const uin
     }
 }
 
+// Shared-memory set-up of a gather CTA: token table and zeroed count planes.
+template <int Q>
+__device__ __forceinline__ void gather_cta_setup(uint4* smem, int warps) {
+    using G = GatherGeo<Q>;
+    build_token_table<Q>(reinterpret_cast<uint16_t*>(smem));
+    uint32_t* planes_all = reinterpret_cast<uint32_t*>(smem) + G::kTabWords;
+    for (int i = threadIdx.x; i < warps * G::kPlaneWords; i += blockDim.x) planes_all[i] = 0;
+    __syncthreads();
+}
+
+// The whole filter for read r, by one warp (steps 0-5 above).  The warp's
+// count planes are zero on entry and left zero on exit.
+template <int Q>
+__device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restrict__ bank, int64_t n_bins,
+                                            const uint8_t* __restrict__ reads,
+                                            const int64_t* __restrict__ read_offsets,
+                                            const uint32_t* __restrict__ cand_bins,
+                                            const int64_t* __restrict__ cand_offsets,
+                                            const uint16_t* __restrict__ E, uint8_t* __restrict__ pass,
+                                            uint16_t* __restrict__ sums, const uint16_t* __restrict__ tab,
+                                            uint32_t* __restrict__ planes, int lane, uint32_t& flags) {
+    constexpr int RW = GatherGeo<Q>::kRowWords;
+    const uint4* planes4 = reinterpret_cast<const uint4*>(planes);
+    const int64_t ro = read_offsets[r], re = read_offsets[r + 1];
+    const int64_t co = cand_offsets[r], ce = cand_offsets[r + 1];
+    const int e = E[r];
+    if (ce < co) {  // nothing sensible to write for this read
+        flags |= GRIM_FLAG_BAD_OFFSETS;
+        return;
+    }
+    // 0. first candidate batch in flight while the tokens are built
+    Batch<Q> bt;
+    if (co < ce) load_batch<Q>(bt, cand_bins, co, ce, bank, n_bins, lane);
+
+    bool bad_read = false;
+    int L = 0;
+    if (re < ro) {
+        flags |= GRIM_FLAG_BAD_OFFSETS;
+        bad_read = true;
+    } else if (re - ro > GRIM_MAX_READ_LEN) {
+        flags |= GRIM_FLAG_LONG_READ;
+        bad_read = true;
+    } else {
+        L = (int)(re - ro);
+    }
+    const uint8_t* rd = reads + ro;
+
+    // 1-2. tokens into bit-sliced count planes
+    uint32_t bad_base = 0;
+    int top = -1;  // highest plane this lane set
+    for_each_token<Q>(rd, L, lane, tab, bad_base, [&](uint32_t tok) {
+        const uint32_t w = tok >> 5, m = 1u << (tok & 31);
+        int p = 0;
+        while (p < kPlanes) {
+            const uint32_t old = atomicXor(&planes[p * RW + w], m);
+            if (!(old & m)) break;
+            ++p;
+        }
+        top = p > top ? p : top;
+    });
+    const int used = (int)__reduce_max_sync(kFull, (unsigned)(top + 1));
+    if (__any_sync(kFull, bad_base)) {
+        flags |= GRIM_FLAG_BAD_BASE;
+        bad_read = true;
+    }
+    __syncwarp();
+    const int n_tok = L - Q + 1 > 0 ? L - Q + 1 : 0;
+    const int T = n_tok - Q * e;
+
+    // 3-5. score the candidates
+    if (co < ce) {
+        if (bad_read || used == 0)
+            write_constant(co, ce, cand_bins, n_bins, !bad_read && T <= 0, pass, sums, lane, flags);
+        else if (used == 1)
+            score_read<Q, 1>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
+        else if (used == 2)
+            score_read<Q, 2>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
+        else
+            score_read<Q, 0>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
+    }
+
+    // leave the planes zeroed for the warp's next read
+    __syncwarp();
+    for (int i = lane; i < used * RW; i += 32) planes[i] = 0;
+    __syncwarp();
+}
+
+// Plain gather: warps walk the reads grid-stride.
 template <int Q>
 __global__ void __launch_bounds__(kGatherWarps * 32, 3)
 gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* __restrict__ reads,
@@ -166,85 +254,51 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
               const int64_t* __restrict__ cand_offsets, const uint16_t* __restrict__ E,
               uint8_t* __restrict__ pass, uint16_t* __restrict__ sums, uint32_t* __restrict__ status) {
     using G = GatherGeo<Q>;
-    constexpr int RW = G::kRowWords;
     extern __shared__ uint4 gather_smem[];
-    uint16_t* tab = reinterpret_cast<uint16_t*>(gather_smem);
-    uint32_t* planes_all = reinterpret_cast<uint32_t*>(gather_smem) + G::kTabWords;
-
-    build_token_table<Q>(tab);
-    for (int i = threadIdx.x; i < kGatherWarps * G::kPlaneWords; i += blockDim.x) planes_all[i] = 0;
-    __syncthreads();
-
+    gather_cta_setup<Q>(gather_smem, kGatherWarps);
+    const uint16_t* tab = reinterpret_cast<const uint16_t*>(gather_smem);
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    uint32_t* planes = planes_all + warp * G::kPlaneWords;
-    const uint4* planes4 = reinterpret_cast<const uint4*>(planes);
+    uint32_t* planes = reinterpret_cast<uint32_t*>(gather_smem) + G::kTabWords + warp * G::kPlaneWords;
 
     uint32_t flags = 0;
     const int64_t warp_stride = (int64_t)gridDim.x * kGatherWarps;
-    for (int64_t r = (int64_t)blockIdx.x * kGatherWarps + warp; r < n_reads; r += warp_stride) {
-        const int64_t ro = read_offsets[r], re = read_offsets[r + 1];
-        const int64_t co = cand_offsets[r], ce = cand_offsets[r + 1];
-        const int e = E[r];
-        if (ce < co) {  // nothing sensible to write for this read
-            flags |= GRIM_FLAG_BAD_OFFSETS;
-            continue;
-        }
-        // 0. first candidate batch in flight while the tokens are built
-        Batch<Q> bt;
-        if (co < ce) load_batch<Q>(bt, cand_bins, co, ce, bank, n_bins, lane);
+    for (int64_t r = (int64_t)blockIdx.x * kGatherWarps + warp; r < n_reads; r += warp_stride)
+        gather_read<Q>(r, bank, n_bins, reads, read_offsets, cand_bins, cand_offsets, E, pass, sums, tab, planes,
+                       lane, flags);
+    flags = __reduce_or_sync(kFull, flags);
+    if (lane == 0 && flags) atomicOr(status, flags);
+}
 
-        bool bad_read = false;
-        int L = 0;
-        if (re < ro) {
-            flags |= GRIM_FLAG_BAD_OFFSETS;
-            bad_read = true;
-        } else if (re - ro > GRIM_MAX_READ_LEN) {
-            flags |= GRIM_FLAG_LONG_READ;
-            bad_read = true;
-        } else {
-            L = (int)(re - ro);
-        }
-        const uint8_t* rd = reads + ro;
+// Persistent gather: a grid sized to fill the GPU once; every warp claims
+// `claim` consecutive reads at a time from a device counter until the batch
+// is exhausted, so uneven read lengths and candidate lists balance across
+// the GPU.  No warp ever waits for another.
+template <int Q, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 24 / WARPS)
+gather_persistent_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* __restrict__ reads,
+                         const int64_t* __restrict__ read_offsets, int64_t n_reads,
+                         const uint32_t* __restrict__ cand_bins, const int64_t* __restrict__ cand_offsets,
+                         const uint16_t* __restrict__ E, uint8_t* __restrict__ pass, uint16_t* __restrict__ sums,
+                         uint32_t* __restrict__ status, unsigned long long* __restrict__ counter, int claim) {
+    using G = GatherGeo<Q>;
+    extern __shared__ uint4 gather_smem[];
+    gather_cta_setup<Q>(gather_smem, WARPS);
+    const uint16_t* tab = reinterpret_cast<const uint16_t*>(gather_smem);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    uint32_t* planes = reinterpret_cast<uint32_t*>(gather_smem) + G::kTabWords + warp * G::kPlaneWords;
 
-        // 1-2. tokens into bit-sliced count planes
-        uint32_t bad_base = 0;
-        int top = -1;  // highest plane this lane set
-        for_each_token<Q>(rd, L, lane, tab, bad_base, [&](uint32_t tok) {
-            const uint32_t w = tok >> 5, m = 1u << (tok & 31);
-            int p = 0;
-            while (p < kPlanes) {
-                const uint32_t old = atomicXor(&planes[p * RW + w], m);
-                if (!(old & m)) break;
-                ++p;
-            }
-            top = p > top ? p : top;
-        });
-        const int used = (int)__reduce_max_sync(kFull, (unsigned)(top + 1));
-        if (__any_sync(kFull, bad_base)) {
-            flags |= GRIM_FLAG_BAD_BASE;
-            bad_read = true;
-        }
-        __syncwarp();
-        const int n_tok = L - Q + 1 > 0 ? L - Q + 1 : 0;
-        const int T = n_tok - Q * e;
-
-        // 3-5. score the candidates
-        if (co < ce) {
-            if (bad_read || used == 0)
-                write_constant(co, ce, cand_bins, n_bins, !bad_read && T <= 0, pass, sums, lane, flags);
-            else if (used == 1)
-                score_read<Q, 1>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
-            else if (used == 2)
-                score_read<Q, 2>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
-            else
-                score_read<Q, 0>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
-        }
-
-        // leave the planes zeroed for the warp's next read
-        __syncwarp();
-        for (int i = lane; i < used * RW; i += 32) planes[i] = 0;
-        __syncwarp();
+    uint32_t flags = 0;
+    while (true) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(counter, (unsigned long long)claim);
+        base = __shfl_sync(kFull, base, 0);
+        if ((int64_t)base >= n_reads) break;
+        const int64_t end = (int64_t)base + claim < n_reads ? (int64_t)base + claim : n_reads;
+        for (int64_t r = (int64_t)base; r < end; r++)
+            gather_read<Q>(r, bank, n_bins, reads, read_offsets, cand_bins, cand_offsets, E, pass, sums, tab, planes,
+                           lane, flags);
     }
     flags = __reduce_or_sync(kFull, flags);
     if (lane == 0 && flags) atomicOr(status, flags);
@@ -272,6 +326,57 @@ static int launch_q(const grim_bank* bank, const uint8_t* reads, const int64_t* 
                                                                        sums, bank->status);
     GRIM_CUDA_TRY(cudaGetLastError());
     return GRIM_OK;
+}
+
+template <int Q, int WARPS>
+static int launch_persistent_qw(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
+                                unsigned long long* counter, cudaStream_t s) {
+    constexpr size_t smem = gather_smem_bytes<Q>(WARPS);
+    static int max_blocks = 0;
+    if (max_blocks == 0) {
+        if (smem > 48 * 1024)
+            GRIM_CUDA_TRY(cudaFuncSetAttribute(gather_persistent_kernel<Q, WARPS>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int b = 0;
+        GRIM_CUDA_TRY(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gather_persistent_kernel<Q, WARPS>, WARPS * 32, smem));
+        max_blocks = b > 0 ? b : 1;
+    }
+    const int per_sm = (t.ctas_per_sm > 0 && t.ctas_per_sm < max_blocks) ? t.ctas_per_sm : max_blocks;
+    const int claim = t.reads_per_claim > 0 ? t.reads_per_claim : 1;
+    const int64_t batch = t.batch_reads > 0 ? t.batch_reads : (int64_t)262144;
+    for (int64_t r0 = 0; r0 < a.n_reads; r0 += batch) {
+        const int64_t n = (a.n_reads - r0) < batch ? (a.n_reads - r0) : batch;
+        int64_t blocks = (int64_t)sm_count() * per_sm;
+        const int64_t need = (n + (int64_t)WARPS * claim - 1) / ((int64_t)WARPS * claim);
+        if (need < blocks) blocks = need;
+        GRIM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+        gather_persistent_kernel<Q, WARPS><<<(unsigned)blocks, WARPS * 32, smem, s>>>(
+            bank->bits, bank->n_bins, a.reads, a.read_offsets + r0, n, a.cand_bins, a.cand_offsets + r0, a.E + r0,
+            a.pass, a.sums, bank->status, counter, claim);
+        GRIM_CUDA_TRY(cudaGetLastError());
+    }
+    return GRIM_OK;
+}
+
+template <int Q>
+static int launch_persistent_q(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
+                               unsigned long long* counter, cudaStream_t s) {
+    if (t.warps_per_cta == 4) return launch_persistent_qw<Q, 4>(bank, a, t, counter, s);
+    return launch_persistent_qw<Q, 8>(bank, a, t, counter, s);
+}
+
+int launch_gather_persistent(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
+                             unsigned long long* counter, cudaStream_t s) {
+    switch (bank->q) {
+        case 1: return launch_persistent_q<1>(bank, a, t, counter, s);
+        case 2: return launch_persistent_q<2>(bank, a, t, counter, s);
+        case 3: return launch_persistent_q<3>(bank, a, t, counter, s);
+        case 4: return launch_persistent_q<4>(bank, a, t, counter, s);
+        case 5: return launch_persistent_q<5>(bank, a, t, counter, s);
+        case 6: return launch_persistent_q<6>(bank, a, t, counter, s);
+        default: return GRIM_ENOTSUP;
+    }
 }
 
 int launch_gather(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,

@@ -4,7 +4,23 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "grim.h"
+
+namespace grim {
+// A captured and instantiated CUDA graph of one batched-filter call.
+struct GraphEntry {
+    const void* key[8];
+    int64_t n_reads;
+    grim_tune tune;
+    cudaStream_t stream;
+    int slot;  // work counter owned by this graph
+    cudaGraphExec_t exec;
+    uint64_t last_use;
+};
+constexpr int kGraphCache = 15;  // counters: slot 0 for direct launches, 1..15 for graphs
+}  // namespace grim
 
 struct grim_bank {
     int64_t len;        // reference length in bases
@@ -14,6 +30,9 @@ struct grim_bank {
     int device;
     uint32_t* bits;    // device, n_bins * row_words words, bin-major
     uint32_t* status;  // device, one word of GRIM_FLAG_* bits
+    unsigned long long* counters;  // device, 1 + kGraphCache work counters of the batched filter
+    std::vector<grim::GraphEntry>* graphs;
+    uint64_t graph_clock;
 };
 
 namespace grim {
@@ -42,6 +61,19 @@ int launch_bank_build(const uint8_t* ref2bit, grim_bank* bank, cudaStream_t stre
 int launch_gather(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                   const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
                   uint16_t* sums, cudaStream_t stream);
+
+struct GatherArgs {
+    const uint8_t* reads;
+    const int64_t* read_offsets;
+    int64_t n_reads;
+    const uint32_t* cand_bins;
+    const int64_t* cand_offsets;
+    const uint16_t* E;
+    uint8_t* pass;
+    uint16_t* sums;
+};
+int launch_gather_persistent(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
+                             unsigned long long* counter, cudaStream_t stream);
 
 size_t scan_scratch_bytes(int q, int64_t n_reads);
 int launch_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,

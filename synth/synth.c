@@ -167,9 +167,35 @@ int synth_reads(uint64_t seed, const uint8_t* codes, int64_t len, int64_t n, con
 
 /* ---------------------------------------------------------- candidates */
 
-static int cmp_u32(const void* a, const void* b) {
-    uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
-    return (x > y) - (x < y);
+/* sort u32 ascending: insertion sort for short arrays, else two 16-bit LSD
+ * radix passes through tmp (same length) */
+static void sort_u32(uint32_t* a, int64_t n, uint32_t* tmp) {
+    if (n <= 48) {
+        for (int64_t i = 1; i < n; i++) {
+            uint32_t x = a[i];
+            int64_t j = i - 1;
+            while (j >= 0 && a[j] > x) { a[j + 1] = a[j]; j--; }
+            a[j + 1] = x;
+        }
+        return;
+    }
+    static const int B = 1 << 16;
+    int64_t* cnt = (int64_t*)calloc((size_t)B + 1, sizeof(int64_t));
+    for (int pass = 0; pass < 2; pass++) {
+        int sh = 16 * pass;
+        uint32_t* src = pass == 0 ? a : tmp;
+        uint32_t* dst = pass == 0 ? tmp : a;
+        memset(cnt, 0, sizeof(int64_t) * (size_t)(B + 1));
+        for (int64_t i = 0; i < n; i++) cnt[((src[i] >> sh) & 0xFFFF) + 1]++;
+        for (int b = 0; b < B; b++) cnt[b + 1] += cnt[b];
+        for (int64_t i = 0; i < n; i++) dst[cnt[(src[i] >> sh) & 0xFFFF]++] = src[i];
+    }
+    free(cnt);
+}
+
+/* per-read generator, so that reads can be drawn in any order or in parallel */
+static rng_t rng_read(uint64_t seed, uint64_t stream, int64_t r) {
+    return rng_make(seed * 0x9E3779B97F4A7C15ULL + (uint64_t)r, stream);
 }
 
 /*
@@ -179,13 +205,13 @@ static int cmp_u32(const void* a, const void* b) {
  */
 void synth_cand_counts(uint64_t seed, int64_t n, int k_fixed, int k_max, int64_t n_bins,
                        int64_t* cand_offsets) {
-    rng_t g = rng_make(seed, 41);
     cand_offsets[0] = 0;
     double lk = log((double)(k_max > 1 ? k_max : 1));
     for (int64_t r = 0; r < n; r++) {
         int64_t k;
         if (k_fixed > 0) k = k_fixed;
         else {
+            rng_t g = rng_read(seed, 41, r);
             k = (int64_t)floor(exp(rng_unit(&g) * lk));
             if (k < 1) k = 1;
             if (k > k_max) k = k_max;
@@ -201,28 +227,38 @@ void synth_cand_counts(uint64_t seed, int64_t n, int k_fixed, int k_max, int64_t
  */
 int synth_cands_random(uint64_t seed, int64_t n, const int64_t* starts, int bin_len, int64_t n_bins,
                        const int64_t* cand_offsets, uint32_t* cand_bins) {
-    rng_t g = rng_make(seed, 43);
-    for (int64_t r = 0; r < n; r++) {
-        int64_t k = cand_offsets[r + 1] - cand_offsets[r];
-        if (k <= 0) continue;
-        uint32_t* c = cand_bins + cand_offsets[r];
-        int64_t tb = starts[r] / bin_len;
-        if (tb >= n_bins) tb = n_bins - 1;
-        c[0] = (uint32_t)tb;
-        int64_t have = 1;
-        while (have < k) {
-            int64_t need = k - have;
-            for (int64_t j = 0; j < need; j++) c[have + j] = (uint32_t)rng_below(&g, (uint64_t)n_bins);
-            int64_t m = have + need;
-            qsort(c, (size_t)m, sizeof(uint32_t), cmp_u32);
-            int64_t u = 0;
-            for (int64_t j = 0; j < m; j++)
-                if (u == 0 || c[j] != c[u - 1]) c[u++] = c[j];
-            have = u;
+    int64_t kmax = 1;
+    for (int64_t r = 0; r < n; r++)
+        if (cand_offsets[r + 1] - cand_offsets[r] > kmax) kmax = cand_offsets[r + 1] - cand_offsets[r];
+    int err = 0;
+#pragma omp parallel
+    {
+        uint32_t* tmp = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(2 * kmax + 2));
+        if (!tmp) err = 1;
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t r = 0; r < n; r++) {
+            int64_t k = cand_offsets[r + 1] - cand_offsets[r];
+            if (k <= 0 || !tmp) continue;
+            rng_t g = rng_read(seed, 43, r);
+            uint32_t* c = cand_bins + cand_offsets[r];
+            int64_t tb = starts[r] / bin_len;
+            if (tb >= n_bins) tb = n_bins - 1;
+            c[0] = (uint32_t)tb;
+            int64_t have = 1;
+            while (have < k) {
+                int64_t need = k - have;
+                for (int64_t j = 0; j < need; j++) c[have + j] = (uint32_t)rng_below(&g, (uint64_t)n_bins);
+                int64_t m = have + need;
+                sort_u32(c, m, tmp);
+                int64_t u = 0;
+                for (int64_t j = 0; j < m; j++)
+                    if (u == 0 || c[j] != c[u - 1]) c[u++] = c[j];
+                have = u;
+            }
         }
-        qsort(c, (size_t)k, sizeof(uint32_t), cmp_u32);
+        free(tmp);
     }
-    return 0;
+    return err ? -1 : 0;
 }
 
 /* ----------------------------------------------- exact k-mer seed index */
@@ -274,6 +310,46 @@ static int cmp_bin(const void* a, const void* b) {
     return (x->bin > y->bin) - (x->bin < y->bin);
 }
 
+/* distinct voted bins of one read (see synth_cands_seeds); returns the
+ * count, bins in (*hits)[0..count) ascending; -1 on allocation failure */
+static int64_t seed_bins_of_read(const uint32_t* idx_offsets, const uint32_t* idx_positions, int k,
+                                 const uint8_t* s, int64_t L, int bin_len, int64_t n_bins, int cap,
+                                 bin_support** hits, int64_t* hcap) {
+    int64_t nh = 0;
+    for (int64_t o = 0; o + k <= L; o += k) {
+        uint64_t key = kmer_key(s + o, k);
+        uint32_t a = idx_offsets[key], b = idx_offsets[key + 1];
+        if (nh + (int64_t)(b - a) > *hcap) {
+            while (nh + (int64_t)(b - a) > *hcap) *hcap *= 2;
+            bin_support* h2 = (bin_support*)realloc(*hits, sizeof(bin_support) * (size_t)*hcap);
+            if (!h2) return -1;
+            *hits = h2;
+        }
+        for (uint32_t j = a; j < b; j++) {
+            int64_t st = (int64_t)idx_positions[j] - o;
+            if (st < 0) st = 0;
+            int64_t bin = st / bin_len;
+            if (bin >= n_bins) bin = n_bins - 1;
+            (*hits)[nh].bin = (uint32_t)bin;
+            (*hits)[nh].support = 1;
+            nh++;
+        }
+    }
+    bin_support* h = *hits;
+    qsort(h, (size_t)nh, sizeof(bin_support), cmp_bin);
+    int64_t u = 0;
+    for (int64_t j = 0; j < nh; j++) {
+        if (u > 0 && h[u - 1].bin == h[j].bin) h[u - 1].support++;
+        else h[u++] = h[j];
+    }
+    if (u > cap) {
+        qsort(h, (size_t)u, sizeof(bin_support), cmp_support);
+        u = cap;
+        qsort(h, (size_t)u, sizeof(bin_support), cmp_bin);
+    }
+    return u;
+}
+
 /*
  * Seed-hit candidates, as a hash-table read mapper would produce them:
  * non-overlapping k-mers of the read at offsets 0, k, 2k, ...; every exact
@@ -287,53 +363,45 @@ int64_t synth_cands_seeds(const uint32_t* idx_offsets, const uint32_t* idx_posit
                           const uint8_t* bases, const int64_t* read_offsets, int64_t n, int bin_len,
                           int64_t n_bins, int cap, int64_t cap_total, uint32_t* cand_bins,
                           int64_t* cand_offsets) {
-    int64_t scratch_cap = 1 << 16;
-    bin_support* hits = (bin_support*)malloc(sizeof(bin_support) * (size_t)scratch_cap);
-    if (!hits) return -1;
-    int64_t total = 0;
-    cand_offsets[0] = 0;
-    for (int64_t r = 0; r < n; r++) {
-        const uint8_t* s = bases + read_offsets[r];
-        int64_t L = read_offsets[r + 1] - read_offsets[r];
-        int64_t nh = 0;
-        for (int64_t o = 0; o + k <= L; o += k) {
-            uint64_t key = kmer_key(s + o, k);
-            uint32_t a = idx_offsets[key], b = idx_offsets[key + 1];
-            if (nh + (int64_t)(b - a) > scratch_cap) {
-                while (nh + (int64_t)(b - a) > scratch_cap) scratch_cap *= 2;
-                bin_support* h2 = (bin_support*)realloc(hits, sizeof(bin_support) * (size_t)scratch_cap);
-                if (!h2) { free(hits); return -1; }
-                hits = h2;
-            }
-            for (uint32_t j = a; j < b; j++) {
-                int64_t st = (int64_t)idx_positions[j] - o;
-                if (st < 0) st = 0;
-                int64_t bin = st / bin_len;
-                if (bin >= n_bins) bin = n_bins - 1;
-                hits[nh].bin = (uint32_t)bin;
-                hits[nh].support = 1;
-                nh++;
-            }
+    int err = 0;
+    /* pass 1: counts */
+#pragma omp parallel
+    {
+        int64_t hcap = 1 << 12;
+        bin_support* hits = (bin_support*)malloc(sizeof(bin_support) * (size_t)hcap);
+        if (!hits) err = 1;
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t r = 0; r < n; r++) {
+            if (!hits) continue;
+            int64_t u = seed_bins_of_read(idx_offsets, idx_positions, k, bases + read_offsets[r],
+                                          read_offsets[r + 1] - read_offsets[r], bin_len, n_bins, cap, &hits, &hcap);
+            if (u < 0) { err = 1; u = 0; }
+            cand_offsets[r + 1] = u;
         }
-        qsort(hits, (size_t)nh, sizeof(bin_support), cmp_bin);
-        int64_t u = 0;
-        for (int64_t j = 0; j < nh; j++) {
-            if (u > 0 && hits[u - 1].bin == hits[j].bin) hits[u - 1].support++;
-            else hits[u++] = hits[j];
-        }
-        if (u > cap) {
-            qsort(hits, (size_t)u, sizeof(bin_support), cmp_support);
-            u = cap;
-            qsort(hits, (size_t)u, sizeof(bin_support), cmp_bin);
-        }
-        for (int64_t j = 0; j < u; j++) {
-            if (total + j < cap_total) cand_bins[total + j] = hits[j].bin;
-        }
-        total += u;
-        cand_offsets[r + 1] = total;
+        free(hits);
     }
-    free(hits);
-    return total;
+    if (err) return -1;
+    cand_offsets[0] = 0;
+    for (int64_t r = 0; r < n; r++) cand_offsets[r + 1] += cand_offsets[r];
+    int64_t total = cand_offsets[n];
+    if (total > cap_total) return total;
+    /* pass 2: bins */
+#pragma omp parallel
+    {
+        int64_t hcap = 1 << 12;
+        bin_support* hits = (bin_support*)malloc(sizeof(bin_support) * (size_t)hcap);
+        if (!hits) err = 1;
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t r = 0; r < n; r++) {
+            if (!hits) continue;
+            int64_t u = seed_bins_of_read(idx_offsets, idx_positions, k, bases + read_offsets[r],
+                                          read_offsets[r + 1] - read_offsets[r], bin_len, n_bins, cap, &hits, &hcap);
+            if (u < 0) { err = 1; continue; }
+            for (int64_t j = 0; j < u; j++) cand_bins[cand_offsets[r] + j] = hits[j].bin;
+        }
+        free(hits);
+    }
+    return err ? -1 : total;
 }
 
 /* per-read E = floor(num * L / den) (integer arithmetic) */
