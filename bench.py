@@ -1,13 +1,24 @@
 """Benchmark of the seed-location filter on GB300.
 
-Default workload (N=1): 100 Mbp repeat-rich synthetic reference (70% i.i.d.
-ACGT + 30% planted repeat families at 10-20% divergence), q=5, 256 bp bins +
-150 bp overlap; 1M reads of 150 bp (4% substitutions, 1% indels), E=7;
-candidates = bins of all exact 12-mer seed hits from a CPU index, capped at
-1,000 per read.  One step = one gather-form filter pass over the whole read
-batch (read tokenisation, every (read, candidate bin) check, pass mask out);
-the bank is built once beforehand, as in the paper (Sec. 6.1: bitvectors
-are generated once per reference) and reported on its own.
+Three forms of the hot path, each on its synthetic workload:
+  gather   (default line): 100 Mbp repeat-rich reference (70% i.i.d. ACGT +
+           30% planted repeat families at 10-20% divergence), q=5, 256 bp
+           bins + 150 bp overlap; 1M reads of 150 bp (4% substitutions, 1%
+           indels), E=7; candidates = bins of all exact 12-mer seed hits from
+           a CPU index, capped at 1,000 per read.  One step = one grim_filter
+           over the whole batch.
+  batched: 100 Mbp repeat-rich reference, q=6, 256 + 300 bp; 2M reads of
+           50-300 bp (3% + 1%), E = floor(0.05 L); true bin + log-uniform
+           1-5,000 candidates.  One step = one grim_filter_batched (one
+           persistent launch per 262,144 reads, replayed CUDA graph,
+           autotuned launch shape).
+  fullscan: 3.1 Gbp repeat-rich reference, q=5, 256 + 100 bp (12.1M bins);
+           a batch of 65,536 reads of 100 bp, E=5, every bin scored on the
+           tensor cores.  One step = one grim_scan.
+The bank is built once per reference beforehand (the paper also leaves
+bitvector generation out of its runtime, Sec. 6.1) and timed on its own.
+`--workload` picks the form of the JSON line; the other two are measured
+after it and reported as sub-objects unless disabled.
 
 Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -31,10 +42,10 @@ METRIC = "(read,bin) checks/s & reads/s at E=0.05·L; frac of HBM/INT8 roofline 
 UNIT = "checks/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one gather launch, from an
-# ncu capture, valid only for the kernel source it was taken on.
+# dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch, from
+# an ncu capture, valid only for the kernel source it was taken on.
 TRAFFIC_BY_SOURCE: dict[str, dict] = {
-    # full-size launch (1M reads, 74.8M checks): 650.67 MB read + 74.77 MB written
+    # gather, 1M reads, 74.8M checks: 650.67 MB read + 74.77 MB written
     "6adfb81d6d4f3ac4": {"bytes": 725_440_000},
 }
 
@@ -45,50 +56,23 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--reads", type=int, default=1_000_000, help="reads per GPU (weak scaling)")
-    ap.add_argument("--ref-bp", type=int, default=100_000_000)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--workload", default="gather", choices=["gather", "fullscan"],
-                    help="gather: 100 Mbp / 1M x 150 bp seed candidates; fullscan: 3.1 Gbp, 65,536 x 100 bp, all bins")
-    ap.add_argument("--no-full-scan", action="store_true", help="skip the full-scan sub-measurement")
-    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form sub-measurement")
+    ap.add_argument("--workload", default="gather", choices=["gather", "batched", "fullscan"])
+    ap.add_argument("--reads", type=int, default=1_000_000, help="gather: reads per GPU (weak scaling)")
+    ap.add_argument("--ref-bp", type=int, default=100_000_000, help="gather: reference length")
     ap.add_argument("--batched-reads", type=int, default=2_000_000)
     ap.add_argument("--scan-ref-bp", type=int, default=3_100_000_000)
     ap.add_argument("--scan-reads", type=int, default=65_536)
-    ap.add_argument("--scan-steps", type=int, default=3)
+    ap.add_argument("--sub-steps", type=int, default=3, help="timed steps of the sub-measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched sub-measurement")
+    ap.add_argument("--no-full-scan", action="store_true", help="skip the full-scan sub-measurement")
     return ap.parse_args()
 
 
 def dist_env():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
-
-
-def make_workload(args, rank):
-    import synth
-    # same reference on every rank; each rank its own read batch (weak scaling)
-    return synth.gather_seeds(ref_len=args.ref_bp, n_reads=args.reads, read_seed=synth.SEED_READS + 1000 * rank)
-
-
-def config_of(w, n_gpus):
-    c = np.diff(w.cand_offsets)
-    return {
-        "workload": f"gather, {w.ref_len / 1e6:g} Mbp repeat-rich reference "
-                    f"({int(w.meta['repeat_frac'] * 100)}% repeats), {w.n_reads} x {int(np.diff(w.read_offsets)[0])} bp "
-                    f"reads/GPU, 12-mer seed candidates (cap 1000)",
-        "ref_bp": w.ref_len, "q": w.q, "bin_len": w.bin_len, "overlap": w.overlap, "n_bins": w.n_bins,
-        "reads_per_gpu": w.n_reads, "read_len": int(np.diff(w.read_offsets)[0]), "E": int(w.E[0]),
-        "checks_per_gpu_step": w.n_checks, "cands_per_read_mean": round(float(c.mean()), 2),
-        "cands_per_read_max": int(c.max()), "sub": w.meta["sub"], "indel": w.meta["indel"],
-        "l2": "flushed between timed steps (256 MiB write, outside the events)",
-        "parallelism": f"replicas x{n_gpus} (read batches sharded, no collective)",
-    }
-
-
-def algorithmic_bytes(w, row_bytes):
-    """Bytes one gather launch must move: per check the bin row, the candidate
-    id and the pass byte; per read its bases, two offsets and E."""
-    return w.n_checks * (row_bytes + 4 + 1) + int(w.read_offsets[-1]) + (w.n_reads + 1) * 16 + w.n_reads * 2
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def load_peaks():
@@ -101,137 +85,24 @@ def load_peaks():
 
 def load_fp8_peak():
     """Dense e4m3 tensor peak: the measured bf16 cuBLAS peak x the nominal
-    fp8 / bf16 ratio (4.5 / 2.25 PFLOP/s)."""
+    fp8 / bf16 ratio (4.5 / 2.25 PFLOP/s); burst and sustained."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return float(d["bf16_tflops"]) * 2.0, float(d.get("bf16_tflops_sustained", d["bf16_tflops"])) * 2.0, "measured bf16 x 2"
+        return (float(d["bf16_tflops"]) * 2.0, float(d.get("bf16_tflops_sustained", d["bf16_tflops"])) * 2.0,
+                "measured bf16 x 2")
     return 1900.0 * 2.0, 1700.0 * 2.0, "fallback bf16 x 2"
 
 
-def measure_batched(args, rank, dev):
-    """Batched form: 100 Mbp repeat-rich reference, q=6, reads of 50-300 bp,
-    log-uniform candidate lists; one persistent launch per 262,144-read batch
-    in a captured CUDA graph with the autotuner's launch shape, timed beside
-    the plain gather kernel on the same inputs."""
-    import torch
-
-    import paper_1711_01177_gb300 as grim
-    import synth
-    w = synth.batched_varlen(n_reads=args.batched_reads, read_seed=synth.SEED_READS + 1000 * rank)
-    bank = grim.grim_build_bank(dev(w.ref2bit), w.ref_len, w.q, w.bin_len, w.overlap)
-    ins = [dev(w.bases), dev(w.read_offsets), dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)]
-    out = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
-    side = torch.cuda.Stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-    with torch.cuda.stream(side):
-        t = grim.grim_autotune(bank, *ins, pass_out=out, stream=side)
-    side.synchronize()
-
-    def timed(fn, steps):
-        ms = []
-        for i in range(steps + 2):
-            with torch.cuda.stream(side):
-                flush.fill_(i)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(side)
-                fn()
-                b.record(side)
-            side.synchronize()
-            if i >= 2:
-                ms.append(a.elapsed_time(b))
-        return float(np.mean(ms))
-
-    ms_b = timed(lambda: grim.grim_filter_batched(bank, *ins, pass_out=out, tune=t, stream=side), args.steps)
-    ms_p = timed(lambda: grim.grim_filter(bank, *ins, pass_out=out, stream=side), args.steps)
-    st, flags = grim.grim_bank_status(bank, side)
-    assert st == grim.GRIM_OK, (st, flags)
-    row = bank.row_words * 4
-    alg = w.n_checks * (row + 4 + 1) + int(w.read_offsets[-1]) + (w.n_reads + 1) * 16 + w.n_reads * 2
-    peak, kind = load_peaks()
-    n_batches = -(-w.n_reads // int(t.batch_reads))
-    res = {"workload": f"batched gather, {w.ref_len / 1e6:g} Mbp repeat-rich reference, q={w.q} "
-                       f"({row} B rows, {w.n_bins} bins), {w.n_reads} reads of 50-300 bp, E=floor(0.05 L), "
-                       f"log-uniform 1-5000 candidates (mean {w.n_checks / w.n_reads:.0f})",
-           "value": w.n_checks / (ms_b / 1e3), "unit": UNIT, "reads_per_s": w.n_reads / (ms_b / 1e3),
-           "ms_per_step": ms_b, "checks_per_step": w.n_checks, "launches_per_step": n_batches,
-           "tune": t.as_dict(),
-           "roofline": {"bound": "hbm", "achieved": alg / (ms_b / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                        "frac": alg / (ms_b / 1e3) / 1e9 / peak, "traffic": None,
-                        "peak_source": f"{kind} hbm_gbs", "kernel": f"gather_persistent_kernel<{w.q}>",
-                        "algorithmic_bytes_per_step": alg},
-           "plain_gather_same_workload": {"value": w.n_checks / (ms_p / 1e3), "ms_per_step": ms_p,
-                                          "frac": alg / (ms_p / 1e3) / 1e9 / peak}}
-    bank.free()
-    return res
-
-
-def measure_full_scan(args, rank, dev, stream, with_cpu):
-    """Full-scan form: one batch of reads against every bin of a genome-scale
-    reference on the tensor cores.  Returns a dict (one grim_scan per step)."""
-    import torch
-
-    import paper_1711_01177_gb300 as grim
-    import synth
-    w = synth.fullscan(ref_len=args.scan_ref_bp, n_reads=args.scan_reads)
-    bank = grim.grim_build_bank(dev(w.ref2bit), w.ref_len, w.q, w.bin_len, w.overlap)
-    st, flags = grim.grim_bank_status(bank)
-    assert st == grim.GRIM_OK, (st, flags)
-    reads_d, roff_d, E_d = dev(w.bases), dev(w.read_offsets), dev(w.E)
-    cap = 1 << 24
-    res = grim.grim_scan(bank, reads_d, roff_d, E_d, cap=cap)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-    for _ in range(1):
-        flush.fill_(1)
-        grim.grim_scan(bank, reads_d, roff_d, E_d, out=res)
-    torch.cuda.synchronize()
-    times = []
-    for i in range(args.scan_steps):
-        flush.fill_(i)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        grim.grim_scan(bank, reads_d, roff_d, E_d, out=res)
-        b.record(stream)
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
-    st, flags = grim.grim_bank_status(bank)
-    assert st == grim.GRIM_OK, (st, flags)
-    n_pairs = res.n_pairs
-    ms = float(np.mean(times))
-    checks = w.n_reads * w.n_bins
-    flops = 2.0 * checks * (4 ** w.q)
-    peak, peak_sust, src = load_fp8_peak()
-    achieved = flops / (ms / 1e3) / 1e12
-    out = {"workload": f"full scan, {w.ref_len / 1e9:g} Gbp repeat-rich reference "
-                       f"({int(w.meta['repeat_frac'] * 100)}% repeats), {w.n_bins} bins, batch of {w.n_reads} x "
-                       f"{int(np.diff(w.read_offsets)[0])} bp reads, E={int(w.E[0])}",
-           "value": checks / (ms / 1e3), "unit": UNIT, "reads_per_s": w.n_reads / (ms / 1e3), "ms_per_batch": ms,
-           "steps": args.scan_steps, "pairs_passing": n_pairs,
-           "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
-                        "peak_source": f"{src} (e4m3 dense), burst", "kernel": f"scan_kernel<{w.q}> (+ scan_prep)",
-                        "algorithmic_flops_per_launch": flops, "avg_launch_ms": ms,
-                        "frac_of_sustained": achieved / peak_sust},
-           "dtype": "e4m3 x e4m3 -> f32 (exact small integers)"}
-    if with_cpu:
-        import oracle
-        o = oracle.Oracle()
-        nb = 20_000
-        prefix = nb * w.bin_len + w.overlap
-        ob = o.build_bank(synth.pack2bit(w.codes[:prefix]), prefix, w.q, w.bin_len, w.overlap)[:nb]
-        nr = 64
-        t = time.perf_counter()
-        o.scan(ob, w.q, w.bases[:w.read_offsets[nr]], w.read_offsets[:nr + 1], w.E[:nr])
-        dt = time.perf_counter() - t
-        out["cpu_baseline"] = {"value": nr * nb / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"first {nr} reads x first {nb} bins of the same workload, single thread"}
-    bank.free()
-    del res
-    return out
+def source_sha(files=("gather.cu", "grim_internal.cuh", "tokens.cuh")):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1711_01177_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
-    """nvidia-smi clocks + throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks + throttle reasons sampled during a timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -239,6 +110,7 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.rows = []
 
     def __enter__(self):
         try:
@@ -250,7 +122,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
-        self.rows = []
         if self.proc is None:
             return
         time.sleep(0.25)
@@ -266,25 +137,278 @@ class ClockSampler:
                 self.rows.append(f)
 
     def summary(self):
-        if not getattr(self, "rows", None):
+        if not self.rows:
             return None
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        num = lambda x: x.replace(".", "", 1).isdigit()
+        sm = [float(r[1]) for r in self.rows if num(r[1])]
+        mx = [float(r[2]) for r in self.rows if num(r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def source_sha():
-    h = hashlib.sha256()
-    for f in ("gather.cu", "grim_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1711_01177_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:16]
+# --------------------------------------------------------------- workloads
+
+def make_gather(args, rank):
+    import synth
+    return synth.gather_seeds(ref_len=args.ref_bp, n_reads=args.reads, read_seed=synth.SEED_READS + 1000 * rank)
 
 
-def cpu_baseline(w, seconds):
-    """The oracle, single-threaded, on the first reads of the workload."""
+def make_batched(args, rank):
+    import synth
+    return synth.batched_varlen(n_reads=args.batched_reads, read_seed=synth.SEED_READS + 1000 * rank)
+
+
+def make_fullscan(args, rank):
+    import synth
+    return synth.fullscan(ref_len=args.scan_ref_bp, n_reads=args.scan_reads,
+                          read_seed=synth.SEED_READS + 1000 * rank)
+
+
+def describe(form, w):
+    L = np.diff(w.read_offsets)
+    base = {"ref_bp": w.ref_len, "q": w.q, "bin_len": w.bin_len, "overlap": w.overlap, "n_bins": w.n_bins,
+            "reads_per_gpu": w.n_reads, "read_len": [int(L.min()), int(L.max())],
+            "E": [int(w.E.min()), int(w.E.max())], "sub": w.meta["sub"], "indel": w.meta["indel"],
+            "repeat_frac": w.meta["repeat_frac"],
+            "l2": "flushed between timed steps (256 MiB write, outside the events)"}
+    rep = f"{int(w.meta['repeat_frac'] * 100)}% repeats"
+    if form == "gather":
+        c = np.diff(w.cand_offsets)
+        base.update(workload=f"gather, {w.ref_len / 1e6:g} Mbp repeat-rich reference ({rep}), q={w.q}, "
+                             f"{w.n_reads} x {int(L[0])} bp reads/GPU, 12-mer seed candidates (cap 1000)",
+                    checks_per_gpu_step=w.n_checks, cands_per_read_mean=round(float(c.mean()), 2),
+                    cands_per_read_max=int(c.max()))
+    elif form == "batched":
+        base.update(workload=f"batched gather, {w.ref_len / 1e6:g} Mbp repeat-rich reference ({rep}), q={w.q}, "
+                             f"{w.n_reads} reads of {int(L.min())}-{int(L.max())} bp/GPU, E=floor(0.05 L), "
+                             f"log-uniform 1-5000 candidates (mean {w.n_checks / w.n_reads:.0f})",
+                    checks_per_gpu_step=w.n_checks)
+    else:
+        base.update(workload=f"full scan, {w.ref_len / 1e9:g} Gbp repeat-rich reference ({rep}), q={w.q}, "
+                             f"{w.n_bins} bins, batch of {w.n_reads} x {int(L[0])} bp reads/GPU, every bin",
+                    checks_per_gpu_step=w.n_reads * w.n_bins)
+    return base
+
+
+def gather_bytes(w, row_bytes):
+    """Bytes one gather pass must move: per check the bin row, the candidate
+    id and the pass byte; per read its bases, two offsets and E."""
+    return w.n_checks * (row_bytes + 4 + 1) + int(w.read_offsets[-1]) + (w.n_reads + 1) * 16 + w.n_reads * 2
+
+
+# --------------------------------------------------------------- one form
+
+class Ctx:
+    def __init__(self, rank, world, local):
+        import torch
+        self.rank, self.world, self.local = rank, world, local
+        self.stream = torch.cuda.Stream()
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    @staticmethod
+    def dev(a):
+        import torch
+        a = np.ascontiguousarray(a)
+        view = {np.dtype(np.uint32): np.int32, np.dtype(np.uint16): np.int16}.get(a.dtype)
+        return torch.from_numpy(a.view(view) if view else a).cuda()
+
+    @staticmethod
+    def pin(a):
+        import torch
+        a = np.ascontiguousarray(a)
+        view = {np.dtype(np.uint32): np.int32, np.dtype(np.uint16): np.int16}.get(a.dtype)
+        return torch.from_numpy(a.view(view) if view else a).pin_memory()
+
+    def max_over_ranks(self, x):
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(self, fn, steps, warmup, clocks=False):
+        """Per-step CUDA-event times on the launching stream, L2 flushed
+        between steps outside the events; returns (list of ms, clock summary)."""
+        import torch
+        s = self.stream
+        for i in range(warmup):
+            with torch.cuda.stream(s):
+                self.flush.fill_(i)
+                fn()
+        s.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        self.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(self.local) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        for i in range(steps):
+            with torch.cuda.stream(s):
+                self.flush.fill_(i)
+                ev[i][0].record(s)
+                fn()
+                ev[i][1].record(s)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        self.barrier()
+        return [a.elapsed_time(b) for a, b in ev], (sampler.summary() if sampler else None)
+
+
+def run_form(form, args, ctx, primary):
+    """Measure one form; returns its JSON dict (contract keys if primary)."""
+    import torch
+
+    import paper_1711_01177_gb300 as grim
+    w = {"gather": make_gather, "batched": make_batched, "fullscan": make_fullscan}[form](args, ctx.rank)
+    dev, s = ctx.dev, ctx.stream
+    steps = args.steps if primary else args.sub_steps
+    warmup = args.warmup if primary else 2
+
+    ref_d = dev(w.ref2bit)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        e0.record(s)
+        bank = grim.grim_build_bank(ref_d, w.ref_len, w.q, w.bin_len, w.overlap, stream=s)
+        e1.record(s)
+    s.synchronize()
+    bank_ms = e0.elapsed_time(e1)
+    st, flags = grim.grim_bank_status(bank, s)
+    assert st == grim.GRIM_OK, (st, flags)
+    row = bank.row_words * 4
+    bank_info = {"ms": bank_ms, "mbp_per_s": w.ref_len / 1e6 / (bank_ms / 1e3),
+                 "gb_per_s": (bank.n_bins * row + len(w.ref2bit)) / 1e9 / (bank_ms / 1e3),
+                 "bank_bytes": bank.n_bins * row}
+    del ref_d
+
+    out = {"form": form}
+    if form in ("gather", "batched"):
+        ins = [dev(w.bases), dev(w.read_offsets), dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)]
+        pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
+        tune = None
+        if form == "batched":
+            with torch.cuda.stream(s):
+                tune = grim.grim_autotune(bank, *ins, pass_out=pass_d, stream=s)
+            s.synchronize()
+            call = lambda: grim.grim_filter_batched(bank, *ins, pass_out=pass_d, tune=tune, stream=s)
+            launches = -(-w.n_reads // int(tune.batch_reads))
+            kernel = f"gather_persistent_kernel<{w.q}>"
+        else:
+            call = lambda: grim.grim_filter(bank, *ins, pass_out=pass_d, stream=s)
+            launches = 1
+            kernel = f"gather_kernel<{w.q}>"
+        ms, clk = ctx.timed(call, steps, warmup, clocks=primary)
+        units = w.n_checks
+        alg = gather_bytes(w, row)
+        peak, peak_kind = load_peaks()
+        avg = float(np.mean(ms))
+        roof = {"bound": "hbm", "achieved": alg / (avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": alg / (avg / 1e3) / 1e9 / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                "kernel": kernel, "algorithmic_bytes_per_launch": alg // launches, "launches_per_step": launches,
+                "avg_step_ms": avg}
+        if form == "gather":
+            sha = source_sha()
+            roof["source_sha"] = sha
+            roof["traffic"] = TRAFFIC_BY_SOURCE.get(sha, {}).get("bytes")
+            if w.q == 5:
+                roof["note"] = ("the 50 MB bank stays in the 129 MB L2, so algorithmic bytes exceed DRAM "
+                                "traffic; frac counts algorithmic bytes")
+        if form == "batched":
+            out["tune"] = tune.as_dict()
+            ms_plain, _ = ctx.timed(lambda: grim.grim_filter(bank, *ins, pass_out=pass_d, stream=s),
+                                    args.sub_steps, 2)
+            ap = float(np.mean(ms_plain))
+            out["plain_gather_same_workload"] = {
+                "value": units * ctx.world * len(ms_plain) / (ctx.max_over_ranks(sum(ms_plain)) / 1e3),
+                "ms_per_step": ap, "frac": alg / (ap / 1e3) / 1e9 / peak}
+        st, flags = grim.grim_bank_status(bank, s)
+        assert st == grim.GRIM_OK, (st, flags)
+        out["pass_rate"] = float(pass_d.float().mean().item())
+        if primary:
+            h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.cand_bins), ctx.pin(w.cand_offsets),
+                    ctx.pin(w.E)]
+            h_out = torch.empty(w.n_checks, dtype=torch.uint8).pin_memory()
+
+            def e2e_step():
+                for h, d in zip(h_in, ins):
+                    d.copy_(h, non_blocking=True)
+                call()
+                h_out.copy_(pass_d, non_blocking=True)
+
+            e2e_ms, _ = ctx.timed(e2e_step, steps, warmup)
+            out["e2e"] = {"value": units * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3), "unit": UNIT,
+                          "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
+                          "d2h_bytes_per_step": h_out.numel()}
+            if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
+                out["cpu_baseline"] = cpu_baseline_filter(w, args.cpu_seconds)
+        del ins, pass_d
+    else:
+        ins = [dev(w.bases), dev(w.read_offsets), dev(w.E)]
+        cap = 1 << 24
+        res = grim.grim_scan(bank, *ins, cap=cap, stream=s)
+        call = lambda: grim.grim_scan(bank, *ins, out=res, stream=s)
+        ms, clk = ctx.timed(call, steps, warmup, clocks=primary)
+        st, flags = grim.grim_bank_status(bank, s)
+        assert st == grim.GRIM_OK, (st, flags)
+        n_pairs = res.n_pairs
+        units = w.n_reads * w.n_bins
+        launches = 2  # scan_prep_kernel + scan_kernel
+        avg = float(np.mean(ms))
+        flops = 2.0 * units * (4 ** w.q)
+        peak, peak_sust, src = load_fp8_peak()
+        roof = {"bound": "tensor", "achieved": flops / (avg / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / (avg / 1e3) / 1e12 / peak, "traffic": None,
+                "peak_source": f"{src} (e4m3 dense), burst", "kernel": f"scan_kernel<{w.q}> (+ scan_prep_kernel)",
+                "algorithmic_flops_per_launch": flops, "avg_step_ms": avg,
+                "frac_of_sustained": flops / (avg / 1e3) / 1e12 / peak_sust}
+        out["pairs_passing"] = n_pairs
+        if primary:
+            h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.E)]
+            h_read = torch.empty(n_pairs + 1, dtype=torch.int32).pin_memory()
+            h_bin = torch.empty(n_pairs + 1, dtype=torch.int32).pin_memory()
+            h_n = torch.empty(1, dtype=torch.int64).pin_memory()
+
+            def e2e_step():
+                for h, d in zip(h_in, ins):
+                    d.copy_(h, non_blocking=True)
+                call()
+                h_n.copy_(res.n_pairs_dev, non_blocking=True)
+                h_read.copy_(res.pair_read[:n_pairs + 1], non_blocking=True)
+                h_bin.copy_(res.pair_bin[:n_pairs + 1], non_blocking=True)
+
+            e2e_ms, _ = ctx.timed(e2e_step, steps, warmup)
+            out["e2e"] = {"value": units * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3), "unit": UNIT,
+                          "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
+                          "d2h_bytes_per_step": 8 + 8 * (n_pairs + 1)}
+        if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_scan(w)
+        del ins, res
+    total_ms = ctx.max_over_ranks(float(sum(ms)))
+    out.update({"value": units * ctx.world * steps / (total_ms / 1e3), "unit": UNIT,
+                "reads_per_s": w.n_reads * ctx.world * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
+                "steps": steps, "roofline": roof, "gpu_launches": launches * steps, "clocks": clk,
+                "bank_build": bank_info, "config": describe(form, w)})
+    bank.free()
+    del w
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def cpu_baseline_filter(w, seconds):
+    """The oracle, single-threaded, on the first reads of the same workload."""
     import oracle
     o = oracle.Oracle()
     t0 = time.perf_counter()
@@ -292,14 +416,13 @@ def cpu_baseline(w, seconds):
     t_bank = time.perf_counter() - t0
 
     def run(n):
-        co = w.cand_offsets[:n + 1]
-        ro = w.read_offsets[:n + 1]
+        co, ro = w.cand_offsets[:n + 1], w.read_offsets[:n + 1]
         t = time.perf_counter()
         o.filter(ob, w.q, w.bases[:ro[-1]], ro, w.cand_bins[:co[-1]], co, w.E[:n])
         return time.perf_counter() - t, int(co[-1])
 
-    dt, nc = run(min(2000, w.n_reads))
-    n = min(w.n_reads, max(2000, int(2000 * seconds / max(dt, 1e-6))))
+    dt, nc = run(min(500, w.n_reads))
+    n = min(w.n_reads, max(500, int(500 * seconds / max(dt, 1e-6))))
     dt, nc = run(n)
     return {"value": nc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n} reads ({nc} checks) of the same workload, oracle bank prebuilt "
@@ -307,40 +430,70 @@ def cpu_baseline(w, seconds):
             "reads_per_s": n / dt, "seconds": round(dt, 2)}
 
 
+def cpu_baseline_scan(w, n_reads=64, n_bins=20_000):
+    """The oracle's full scan, single-threaded, on the first reads x the first
+    bins of the same workload (the oracle bank of a reference prefix: its
+    first n_bins bins equal the full reference's)."""
+    import oracle
+    import synth
+    o = oracle.Oracle()
+    prefix = n_bins * w.bin_len + w.overlap
+    ob = o.build_bank(synth.pack2bit(w.codes[:prefix]), prefix, w.q, w.bin_len, w.overlap)[:n_bins]
+    t = time.perf_counter()
+    o.scan(ob, w.q, w.bases[:w.read_offsets[n_reads]], w.read_offsets[:n_reads + 1], w.E[:n_reads])
+    dt = time.perf_counter() - t
+    return {"value": n_reads * n_bins / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n_reads} reads x first {n_bins} bins of the same workload, single thread",
+            "seconds": round(dt, 2)}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
-    import synth
-    w = synth.gather_seeds(ref_len=args.ref_bp, n_reads=args.reads)
-    o = oracle.Oracle()
-    ob = o.build_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
-    # size one step at about (budget / steps) seconds of oracle work
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    o = oracle.Oracle()
+    if args.workload == "fullscan":
+        import synth
+        w = make_fullscan(args, 0)
+        nb = 20_000
+        prefix = nb * w.bin_len + w.overlap
+        ob = o.build_bank(synth.pack2bit(w.codes[:prefix]), prefix, w.q, w.bin_len, w.overlap)[:nb]
 
-    def step(n):
-        co, ro = w.cand_offsets[:n + 1], w.read_offsets[:n + 1]
-        t = time.perf_counter()
-        o.filter(ob, w.q, w.bases[:ro[-1]], ro, w.cand_bins[:co[-1]], co, w.E[:n])
-        return time.perf_counter() - t, int(co[-1])
+        def step(n):
+            t = time.perf_counter()
+            o.scan(ob, w.q, w.bases[:w.read_offsets[n]], w.read_offsets[:n + 1], w.E[:n])
+            return time.perf_counter() - t, n * nb
 
-    dt, _ = step(1000)
-    n = min(w.n_reads, max(1000, int(1000 * per_step / max(dt, 1e-6))))
+        sample = f"first n reads x first {nb} bins per step"
+    else:
+        w = make_gather(args, 0) if args.workload == "gather" else make_batched(args, 0)
+        ob = o.build_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
+
+        def step(n):
+            co, ro = w.cand_offsets[:n + 1], w.read_offsets[:n + 1]
+            t = time.perf_counter()
+            o.filter(ob, w.q, w.bases[:ro[-1]], ro, w.cand_bins[:co[-1]], co, w.E[:n])
+            return time.perf_counter() - t, int(co[-1])
+
+        sample = "first n reads per step"
+    dt, _ = step(16)
+    n = min(w.n_reads, max(16, int(16 * per_step / max(dt, 1e-6))))
     for _ in range(args.warmup):
         step(n)
-    times, checks = [], 0
+    times, units = [], 0
     for _ in range(args.steps):
-        dt, nc = step(n)
+        dt, u = step(n)
         times.append(dt)
-        checks += nc
-    value = checks / sum(times)
+        units += u
+    value = units / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": config_of(w, 1),
+            "config": describe(args.workload, w),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {n} reads ({checks // args.steps} checks) per step, single thread"},
+                             "sample": sample.replace("n reads", f"{n} reads") + ", single thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -359,145 +512,28 @@ def run_ours(args):
         torch.cuda.set_device(0)
     grim.build()
     grim.load()
-    w = make_workload(args, rank)
-
-    def dev(a):
-        a = np.ascontiguousarray(a)
-        if a.dtype == np.uint32:
-            a = a.view(np.int32)
-        elif a.dtype == np.uint16:
-            a = a.view(np.int16)
-        return torch.from_numpy(a).cuda()
-
-    stream = torch.cuda.current_stream()
-    # bank build, once per reference (timed on its own)
-    ref_d = dev(w.ref2bit)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    bank = grim.grim_build_bank(ref_d, w.ref_len, w.q, w.bin_len, w.overlap)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    bank_ms = e0.elapsed_time(e1)
-    st, flags = grim.grim_bank_status(bank)
-    assert st == grim.GRIM_OK, (st, flags)
-    bank_bytes = bank.n_bins * bank.row_words * 4 + len(w.ref2bit)
-
-    reads_d, roff_d = dev(w.bases), dev(w.read_offsets)
-    cb_d, co_d, E_d = dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)
-    pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-
-    def step():
-        grim.grim_filter(bank, reads_d, roff_d, cb_d, co_d, E_d, pass_out=pass_d)
-
-    for _ in range(args.warmup):
-        flush.fill_(1)
-        step()
-    torch.cuda.synchronize()
-    st, flags = grim.grim_bank_status(bank)
-    assert st == grim.GRIM_OK, (st, flags)
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(i)
-            starts[i].record(stream)
-            step()
-            ends[i].record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    launches = args.steps  # one gather kernel per step
-
-    # end to end through the public API: pinned host buffers in, pass mask out
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(
-        {np.dtype(np.uint32): np.int32, np.dtype(np.uint16): np.int16}.get(a.dtype, a.dtype))).pin_memory()
-    h_in = [pin(w.bases), pin(w.read_offsets), pin(w.cand_bins), pin(w.cand_offsets), pin(w.E)]
-    d_in = [reads_d, roff_d, cb_d, co_d, E_d]
-    h_out = torch.empty(w.n_checks, dtype=torch.uint8).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in h_in)
-    d2h = h_out.numel()
-    e2e_ms = []
-    for i in range(args.warmup + args.steps):
-        flush.fill_(i)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for h, d in zip(h_in, d_in):
-            d.copy_(h, non_blocking=True)
-        grim.grim_filter(bank, *d_in, pass_out=pass_d)
-        h_out.copy_(pass_d, non_blocking=True)
-        b.record(stream)
-        torch.cuda.synchronize()
-        if i >= args.warmup:
-            e2e_ms.append(a.elapsed_time(b))
-    e2e_total = float(sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    st, flags = grim.grim_bank_status(bank)
-    assert st == grim.GRIM_OK, (st, flags)
-    pass_rate = float(pass_d.float().mean().item())
-
-    checks_all = w.n_checks * world
-    value = checks_all * args.steps / (total_ms / 1e3)
-    avg_launch_ms = float(np.mean(step_ms))
-    row_bytes = bank.row_words * 4
-    alg = algorithmic_bytes(w, row_bytes)
-    peak, peak_kind = load_peaks()
-    achieved = alg / (avg_launch_ms / 1e3) / 1e9
-    sha = source_sha()
-    traffic = TRAFFIC_BY_SOURCE.get(sha, {}).get("bytes")
-
+    ctx = Ctx(rank, world, local)
+    main_form = run_form(args.workload, args, ctx, primary=True)
+    subs = {}
+    if args.workload != "batched" and not args.no_batched:
+        subs["batched"] = run_form("batched", args, ctx, primary=False)
+    if args.workload != "fullscan" and not args.no_full_scan:
+        subs["full_scan"] = run_form("fullscan", args, ctx, primary=False)
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": config_of(w, world),
-            "reads_per_s": w.n_reads * world * args.steps / (total_ms / 1e3),
-            "pass_rate": pass_rate,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
-                         "kernel": f"gather_kernel<{w.q}>", "algorithmic_bytes_per_launch": alg,
-                         "avg_launch_ms": avg_launch_ms, "source_sha": sha,
-                         "note": "bank (50 MB) fits the 129 MB L2 between candidate rows; frac counts "
-                                 "algorithmic bytes, not DRAM bytes"},
-            "e2e": {"value": checks_all * args.steps / (e2e_total / 1e3), "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "clocks": clk.summary(),
-            "bank_build": {"ms": bank_ms, "ref_bp": w.ref_len, "mbp_per_s": w.ref_len / 1e6 / (bank_ms / 1e3),
-                           "gb_per_s": bank_bytes / 1e9 / (bank_ms / 1e3), "bank_bytes": bank.n_bins * row_bytes},
-        }
-        if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
-        else:
-            line["cpu_baseline"] = None
-    bank.free()
-    del reads_d, roff_d, cb_d, co_d, E_d, pass_d, flush, h_in, h_out
-    torch.cuda.empty_cache()
-    if not args.no_batched:
-        bt = measure_batched(args, rank, dev)
-        if rank == 0:
-            line["batched"] = bt
-        torch.cuda.empty_cache()
-    if not args.no_full_scan:
-        fs = measure_full_scan(args, rank, dev, stream, with_cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
-        if rank == 0:
-            line["full_scan"] = fs
-    if rank == 0:
+        m = main_form
+        line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "e4m3" if args.workload == "fullscan" else "u32",
+                "data": "synthetic",
+                "config": dict(m["config"], parallelism=f"replicas x{world} (read batches per GPU, no collective)"),
+                "reads_per_s": m["reads_per_s"], "roofline": m["roofline"], "e2e": m["e2e"],
+                "gpu_launches": m["gpu_launches"], "clocks": m["clocks"], "cpu_baseline": m.get("cpu_baseline"),
+                "bank_build": m["bank_build"]}
+        for k in ("pass_rate", "tune", "plain_gather_same_workload", "pairs_passing"):
+            if k in m:
+                line[k] = m[k]
+        for k, v in subs.items():
+            line[k] = {kk: vv for kk, vv in v.items() if kk != "clocks"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

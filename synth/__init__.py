@@ -256,12 +256,12 @@ def batched_varlen(ref_len: int = 100_000_000, n_reads: int = 2_000_000, lmin: i
 
 def fullscan(ref_len: int = 3_100_000_000, n_reads: int = 65_536, L: int = 100, q: int = 5,
              bin_len: int = 256, overlap: int = 100, E: int = 5, repeat_frac: float = 0.30,
-             sub: float = 0.03, indel: float = 0.01) -> Workload:
+             sub: float = 0.03, indel: float = 0.01, read_seed: int = SEED_READS) -> Workload:
     """Genome-scale repeat-rich reference, one read batch, no candidate list
     (every bin is scored)."""
     codes = ref_with_repeats(ref_len, SEED_REF, repeat_frac)
-    off = read_offsets(n_reads, L, L, SEED_READS)
-    bases, starts = reads(codes, off, SEED_READS, sub, indel)
+    off = read_offsets(n_reads, L, L, read_seed)
+    bases, starts = reads(codes, off, read_seed, sub, indel)
     return Workload(f"fullscan_{ref_len}bp_q{q}_L{L}_batch{n_reads}", codes, pack2bit(codes), q, bin_len, overlap,
                     bases, off, starts, np.full(n_reads, E, dtype=np.uint16), None, None,
                     {"sub": sub, "indel": indel, "repeat_frac": repeat_frac})
