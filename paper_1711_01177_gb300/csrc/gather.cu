@@ -11,7 +11,8 @@
 //
 // One warp per read (grid-stride over reads):
 //   0. the first batch of candidate rows is requested before anything else,
-//      so its latency hides behind the token work;
+//      so its latency hides behind the token work (and every later batch's
+//      candidate ids are requested while the batch before it is scored);
 //   1. lanes load the read 32 bases at a time; two ballots per 32 bases give
 //      the low and high bits of every base code, and a funnel shift puts the
 //      q bases starting at the lane's position side by side; a per-CTA
@@ -70,34 +71,40 @@ struct Batch {
     int cnt;
 };
 
+// Requests the rows of one batch: cnt candidates starting at the read's
+// candidate c0; `id` is this lane's candidate id (lane < cnt), already loaded.
 template <int Q>
-__device__ __forceinline__ void load_batch(Batch<Q>& bt, const uint32_t* __restrict__ cand_bins, int64_t cb,
-                                           int64_t ce, const uint32_t* __restrict__ bank, int64_t n_bins,
-                                           int lane) {
+__device__ __forceinline__ void load_rows(Batch<Q>& bt, uint32_t id, int cnt, const uint32_t* __restrict__ bank,
+                                          uint32_t n_bins32, int lane) {
     using G = GatherGeo<Q>;
-    bt.cnt = (ce - cb) < G::kBatch ? (int)(ce - cb) : G::kBatch;
-    bt.id = (lane < bt.cnt) ? __ldg(cand_bins + cb + lane) : 0u;
+    bt.cnt = cnt;
+    bt.id = id;
     const int s = lane % G::kLPB;
 #pragma unroll
     for (int t = 0; t < G::kSteps; t++) {
-        if (t * G::kBPS >= bt.cnt) break;  // warp-uniform: the rest of the batch is empty
+        if (t * G::kBPS >= cnt) break;  // warp-uniform: the rest of the batch is empty
         const int j = t * G::kBPS + lane / G::kLPB;
-        const uint32_t b = __shfl_sync(kFull, bt.id, j & 31);
-        const bool ok = j < bt.cnt && (int64_t)b < n_bins;
+        const uint32_t b = __shfl_sync(kFull, id, j & 31);
+        const bool ok = j < cnt && b < n_bins32;
         const uint4* row = reinterpret_cast<const uint4*>(bank) + (size_t)b * G::kRowVecs + s;
 #pragma unroll
         for (int u = 0; u < G::kVPL; u++) bt.v[t][u] = ok ? __ldg(row + u * G::kLPB) : make_uint4(0, 0, 0, 0);
     }
 }
 
-// Score every batch of one read.  NP > 0: NP planes held in registers;
-// NP == 0: P planes read from shared memory.
+// This lane's candidate id of the batch starting at c (n candidates in all).
+__device__ __forceinline__ uint32_t batch_id(const uint32_t* __restrict__ cands, int c, int n, int batch, int lane) {
+    return (lane < batch && c + lane < n) ? __ldg(cands + c + lane) : 0u;
+}
+
+// Score every batch of one read; the first batch is already in bt.
+// NP > 0: NP planes held in registers; NP == 0: P planes read from shared
+// memory.  cands / pass / sums point at the read's first candidate.
 template <int Q, int NP>
-__device__ __forceinline__ void score_read(Batch<Q>& bt, const uint4* __restrict__ planes, int P, int T,
-                                           int64_t co, int64_t ce, const uint32_t* __restrict__ cand_bins,
-                                           const uint32_t* __restrict__ bank, int64_t n_bins,
-                                           uint8_t* __restrict__ pass, uint16_t* __restrict__ sums, int lane,
-                                           uint32_t& flags) {
+__device__ __forceinline__ void score_read(Batch<Q>& bt, const uint4* __restrict__ planes, int P, int T, int n,
+                                           const uint32_t* __restrict__ cands, const uint32_t* __restrict__ bank,
+                                           uint32_t n_bins32, uint8_t* __restrict__ pass,
+                                           uint16_t* __restrict__ sums, int lane, uint32_t& flags) {
     using G = GatherGeo<Q>;
     const int s = lane % G::kLPB;
     uint4 pl[NP > 0 ? NP : 1][G::kVPL];
@@ -107,7 +114,9 @@ __device__ __forceinline__ void score_read(Batch<Q>& bt, const uint4* __restrict
 #pragma unroll
             for (int u = 0; u < G::kVPL; u++) pl[p][u] = planes[p * G::kRowVecs + s + u * G::kLPB];
     }
-    for (int64_t cb = co; cb < ce; cb += G::kBatch) {
+    for (int c = 0; c < n; c += G::kBatch) {
+        // the next batch's ids travel while this batch is scored
+        const uint32_t next_id = batch_id(cands, c + G::kBatch, n, G::kBatch, lane);
         uint32_t mine = 0;
 #pragma unroll
         for (int t = 0; t < G::kSteps; t++) {
@@ -136,13 +145,14 @@ __device__ __forceinline__ void score_read(Batch<Q>& bt, const uint4* __restrict
             if (lane / G::kBPS == t) mine = got;
         }
         if (lane < bt.cnt) {
-            const bool in_range = (int64_t)bt.id < n_bins;
+            const bool in_range = bt.id < n_bins32;
             if (!in_range) flags |= GRIM_FLAG_BAD_BIN;
             const uint32_t sum = in_range ? mine : 0u;
-            pass[cb + lane] = (in_range && (int)sum >= T) ? 1 : 0;
-            if (sums) sums[cb + lane] = (uint16_t)sum;
+            pass[c + lane] = (in_range && (int)sum >= T) ? 1 : 0;
+            if (sums) sums[c + lane] = (uint16_t)sum;
         }
-        if (cb + G::kBatch < ce) load_batch<Q>(bt, cand_bins, cb + G::kBatch, ce, bank, n_bins, lane);
+        const int rest = n - (c + G::kBatch);
+        if (rest > 0) load_rows<Q>(bt, next_id, rest < G::kBatch ? rest : G::kBatch, bank, n_bins32, lane);
     }
 }
 
@@ -190,8 +200,14 @@ __device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restric
         return;
     }
     // 0. first candidate batch in flight while the tokens are built
+    const uint32_t n_bins32 = (uint32_t)n_bins;  // n_bins < 2^32 (checked when the bank is built)
+    const int n_c = (int)(ce - co);
+    const uint32_t* cands = cand_bins + co;
     Batch<Q> bt;
-    if (co < ce) load_batch<Q>(bt, cand_bins, co, ce, bank, n_bins, lane);
+    if (n_c > 0) {
+        const int cnt = n_c < GatherGeo<Q>::kBatch ? n_c : GatherGeo<Q>::kBatch;
+        load_rows<Q>(bt, batch_id(cands, 0, n_c, GatherGeo<Q>::kBatch, lane), cnt, bank, n_bins32, lane);
+    }
 
     bool bad_read = false;
     int L = 0;
@@ -233,11 +249,14 @@ __device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restric
         if (bad_read || used == 0)
             write_constant(co, ce, cand_bins, n_bins, !bad_read && T <= 0, pass, sums, lane, flags);
         else if (used == 1)
-            score_read<Q, 1>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
+            score_read<Q, 1>(bt, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+                             lane, flags);
         else if (used == 2)
-            score_read<Q, 2>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
+            score_read<Q, 2>(bt, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+                             lane, flags);
         else
-            score_read<Q, 0>(bt, planes4, used, T, co, ce, cand_bins, bank, n_bins, pass, sums, lane, flags);
+            score_read<Q, 0>(bt, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+                             lane, flags);
     }
 
     // leave the planes zeroed for the warp's next read
