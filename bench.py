@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gather", choices=["gather", "batched", "fullscan"])
+    ap.add_argument("--workload", default="gather", choices=["gather", "batched", "fullscan", "mixed"])
     ap.add_argument("--reads", type=int, default=1_000_000, help="gather: reads per GPU (weak scaling)")
     ap.add_argument("--ref-bp", type=int, default=100_000_000, help="gather: reference length")
     ap.add_argument("--batched-reads", type=int, default=2_000_000)
@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched sub-measurement")
     ap.add_argument("--no-full-scan", action="store_true", help="skip the full-scan sub-measurement")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the dispatcher (mixed) sub-measurement")
+    ap.add_argument("--mixed-reads", type=int, default=65_536)
     return ap.parse_args()
 
 
@@ -166,6 +168,12 @@ def make_fullscan(args, rank):
                           read_seed=synth.SEED_READS + 1000 * rank)
 
 
+def make_mixed(args, rank):
+    import synth
+    return synth.mixed_seeds(ref_len=args.scan_ref_bp, n_reads=args.mixed_reads,
+                             read_seed=synth.SEED_READS + 1000 * rank)
+
+
 def describe(form, w):
     L = np.diff(w.read_offsets)
     base = {"ref_bp": w.ref_len, "q": w.q, "bin_len": w.bin_len, "overlap": w.overlap, "n_bins": w.n_bins,
@@ -185,6 +193,13 @@ def describe(form, w):
                              f"{w.n_reads} reads of {int(L.min())}-{int(L.max())} bp/GPU, E=floor(0.05 L), "
                              f"log-uniform 1-5000 candidates (mean {w.n_checks / w.n_reads:.0f})",
                     checks_per_gpu_step=w.n_checks)
+    elif form == "mixed":
+        c = np.diff(w.cand_offsets)
+        base.update(workload=f"dispatcher, {w.ref_len / 1e9:g} Gbp reference ({rep} at 5-20% divergence), q={w.q}, "
+                             f"{w.n_reads} x {int(L[0])} bp reads/GPU, 12-mer seed candidates (cap 10000), "
+                             f"gather vs full scan chosen per batch",
+                    checks_per_gpu_step=w.n_checks, cands_per_read_mean=round(float(c.mean()), 2),
+                    cands_per_read_max=int(c.max()))
     else:
         base.update(workload=f"full scan, {w.ref_len / 1e9:g} Gbp repeat-rich reference ({rep}), q={w.q}, "
                              f"{w.n_bins} bins, batch of {w.n_reads} x {int(L[0])} bp reads/GPU, every bin",
@@ -199,6 +214,18 @@ def gather_bytes(w, row_bytes):
 
 
 # --------------------------------------------------------------- one form
+
+def max_over_ranks(x, world):
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
 
 class Ctx:
     def __init__(self, rank, world, local):
@@ -222,13 +249,7 @@ class Ctx:
         return torch.from_numpy(a.view(view) if view else a).pin_memory()
 
     def max_over_ranks(self, x):
-        if self.world == 1:
-            return x
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(x, self.world)
 
     def barrier(self):
         if self.world > 1:
@@ -269,7 +290,8 @@ def run_form(form, args, ctx, primary):
     import torch
 
     import paper_1711_01177_gb300 as grim
-    w = {"gather": make_gather, "batched": make_batched, "fullscan": make_fullscan}[form](args, ctx.rank)
+    w = {"gather": make_gather, "batched": make_batched, "fullscan": make_fullscan,
+         "mixed": make_mixed}[form](args, ctx.rank)
     dev, s = ctx.dev, ctx.stream
     steps = args.steps if primary else args.sub_steps
     warmup = args.warmup if primary else 2
@@ -292,7 +314,60 @@ def run_form(form, args, ctx, primary):
     del ref_d
 
     out = {"form": form}
-    if form in ("gather", "batched"):
+    if form == "mixed":
+        ins = [dev(w.bases), dev(w.read_offsets), dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)]
+        pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(s):
+            tune = grim.grim_autotune(bank, *ins, pass_out=pass_d, stream=s)
+        s.synchronize()
+        choice = grim.grim_choose_form(bank, w.n_reads, w.n_checks)
+        scanned = []
+
+        def call():
+            _, n_sc = grim.grim_filter_auto(bank, *ins, pass_out=pass_d, stream=s)
+            scanned.append(n_sc)
+
+        ms, clk = ctx.timed(call, steps, warmup, clocks=primary)
+        ms_g, _ = ctx.timed(lambda: grim.grim_filter_batched(bank, *ins, pass_out=pass_d, tune=tune, stream=s),
+                            args.sub_steps, 1)
+        res = grim.grim_scan(bank, ins[0], ins[1], ins[4], cap=1 << 24, stream=s)
+        ms_s, _ = ctx.timed(lambda: grim.grim_scan(bank, ins[0], ins[1], ins[4], out=res, stream=s), 1, 1)
+        st, flags = grim.grim_bank_status(bank, s)
+        assert st == grim.GRIM_OK, (st, flags)
+        units = w.n_checks
+        launches = -(-w.n_reads // 262144)
+        alg = gather_bytes(w, row)
+        peak, peak_kind = load_peaks()
+        avg = float(np.mean(ms))
+        g, sc = float(np.mean(ms_g)), float(np.mean(ms_s))
+        roof = {"bound": "hbm", "achieved": alg / (avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": alg / (avg / 1e3) / 1e9 / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                "kernel": "dispatcher -> gather_persistent_kernel<5>", "avg_step_ms": avg}
+        out["dispatch"] = {"choice": "scan" if choice == grim.GRIM_FORM_SCAN else "gather",
+                           "reads_scanned_per_step": scanned[-1] if scanned else 0}
+        out["gather_form"] = {"ms_per_step": g, "checks_per_s": units / (g / 1e3), "reads_per_s": w.n_reads / (g / 1e3)}
+        out["scan_form"] = {"ms_per_step": sc, "checks_per_s_all_bins": w.n_reads * w.n_bins / (sc / 1e3),
+                            "reads_per_s": w.n_reads / (sc / 1e3), "pairs_passing": res.n_pairs}
+        out["pass_rate"] = float(pass_d.float().mean().item())
+        if primary:
+            h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.cand_bins), ctx.pin(w.cand_offsets),
+                    ctx.pin(w.E)]
+            h_out = torch.empty(w.n_checks, dtype=torch.uint8).pin_memory()
+
+            def e2e_step():
+                for h, d in zip(h_in, ins):
+                    d.copy_(h, non_blocking=True)
+                call()
+                h_out.copy_(pass_d, non_blocking=True)
+
+            e2e_ms, _ = ctx.timed(e2e_step, steps, warmup)
+            out["e2e"] = {"value": units * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3), "unit": UNIT,
+                          "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
+                          "d2h_bytes_per_step": h_out.numel()}
+            if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
+                out["cpu_baseline"] = cpu_baseline_rows(w, args.cpu_seconds)
+        del ins, pass_d, res
+    elif form in ("gather", "batched"):
         ins = [dev(w.bases), dev(w.read_offsets), dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)]
         pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
         tune = None
@@ -430,6 +505,29 @@ def cpu_baseline_filter(w, seconds):
             "reads_per_s": n / dt, "seconds": round(dt, 2)}
 
 
+def cpu_baseline_rows(w, seconds):
+    """The oracle on a genome-scale candidate list: each candidate's bitvector
+    built straight from the reference (oracle_bin_row), then summed
+    (oracle_sum_one); single-threaded, on the first candidates of the same
+    workload (a byte-per-bit oracle bank of 12.1M bins would not fit)."""
+    import oracle
+    o = oracle.Oracle()
+    t0 = time.perf_counter()
+    done = 0
+    r = 0
+    while time.perf_counter() - t0 < seconds and r < w.n_reads:
+        read = w.bases[w.read_offsets[r]:w.read_offsets[r + 1]]
+        for c in range(w.cand_offsets[r], w.cand_offsets[r + 1]):
+            row = o.bin_row(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap, int(w.cand_bins[c]))
+            o.sum_one(row, w.q, read)
+            done += 1
+        r += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {r} reads ({done} checks) of the same workload, rows built per check, single thread",
+            "seconds": round(dt, 2)}
+
+
 def cpu_baseline_scan(w, n_reads=64, n_bins=20_000):
     """The oracle's full scan, single-threaded, on the first reads x the first
     bins of the same workload (the oracle bank of a reference prefix: its
@@ -467,6 +565,21 @@ def run_reference(args):
             return time.perf_counter() - t, n * nb
 
         sample = f"first n reads x first {nb} bins per step"
+    elif args.workload == "mixed":
+        w = make_mixed(args, 0)
+
+        def step(n):
+            t = time.perf_counter()
+            done = 0
+            for r in range(n):
+                read = w.bases[w.read_offsets[r]:w.read_offsets[r + 1]]
+                for c in range(w.cand_offsets[r], w.cand_offsets[r + 1]):
+                    o.sum_one(o.bin_row(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap, int(w.cand_bins[c])),
+                              w.q, read)
+                    done += 1
+            return time.perf_counter() - t, done
+
+        sample = "first n reads per step, rows built per check"
     else:
         w = make_gather(args, 0) if args.workload == "gather" else make_batched(args, 0)
         ob = o.build_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
@@ -519,6 +632,8 @@ def run_ours(args):
         subs["batched"] = run_form("batched", args, ctx, primary=False)
     if args.workload != "fullscan" and not args.no_full_scan:
         subs["full_scan"] = run_form("fullscan", args, ctx, primary=False)
+    if args.workload != "mixed" and not args.no_mixed:
+        subs["mixed"] = run_form("mixed", args, ctx, primary=False)
     if rank == 0:
         m = main_form
         line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -529,7 +644,8 @@ def run_ours(args):
                 "reads_per_s": m["reads_per_s"], "roofline": m["roofline"], "e2e": m["e2e"],
                 "gpu_launches": m["gpu_launches"], "clocks": m["clocks"], "cpu_baseline": m.get("cpu_baseline"),
                 "bank_build": m["bank_build"]}
-        for k in ("pass_rate", "tune", "plain_gather_same_workload", "pairs_passing"):
+        for k in ("pass_rate", "tune", "plain_gather_same_workload", "pairs_passing", "dispatch", "gather_form",
+                  "scan_form"):
             if k in m:
                 line[k] = m[k]
         for k, v in subs.items():

@@ -164,6 +164,35 @@ int grim_autotune(const grim_bank* bank, const uint8_t* reads, const int64_t* re
                   grim_tune* out, void* stream);
 
 /*
+ * Per-batch choice between the two forms (candidate density).  The gather
+ * form costs about one bank row per candidate; the full scan costs
+ * n_reads x n_bins small contractions whatever the candidates, so it only
+ * pays off when candidate lists cover a large share of the bins.
+ * grim_choose_form writes GRIM_FORM_GATHER or GRIM_FORM_SCAN to *form
+ * (host) for a batch of n_reads reads with n_checks candidates, from a cost
+ * model that uses the gather rate last measured by grim_autotune for this
+ * bank's q on this device (a default otherwise) and the full scan's
+ * tensor-core rate.
+ */
+#define GRIM_FORM_GATHER 0
+#define GRIM_FORM_SCAN 1
+int grim_choose_form(const grim_bank* bank, int64_t n_reads, int64_t n_checks, int* form);
+
+/*
+ * Dispatching filter: grim_filter's pass bytes (no sums), computed batch by
+ * batch (batch_reads reads, <= 0: 262,144) with the form grim_choose_form
+ * picks.  A scanned batch's passing pairs are joined back onto its
+ * candidates on the device, so both forms give the same bytes.  Reads each
+ * batch's candidate count from the device (synchronising `stream` once per
+ * batch) and allocates the scan's working memory with cudaMallocAsync.
+ * *n_scanned (host, nullable) receives the number of reads that went
+ * through the full scan.
+ */
+int grim_filter_auto(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                     const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
+                     int64_t batch_reads, int64_t* n_scanned, void* stream);
+
+/*
  * Full-scan form: the filter of Sec. 3.2 for every read against every bin
  * of the window [bin_begin, bin_end) (the paper's bin window, Sec. 6.1,
  * with every bin checked), computed as the contraction

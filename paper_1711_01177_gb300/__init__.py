@@ -43,7 +43,10 @@ SIGNATURES = {
     "grim_scan_noalloc": (_I32, [_P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P]),
     "grim_filter_batched": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "grim_autotune": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
+    "grim_choose_form": (_I32, [_P, _I64, _I64, ctypes.POINTER(_I32)]),
+    "grim_filter_auto": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
 }
+GRIM_FORM_GATHER, GRIM_FORM_SCAN = 0, 1
 
 
 class GrimTune(ctypes.Structure):
@@ -282,3 +285,29 @@ def grim_autotune(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, c
                                 _dev_ptr(cand_offsets, "cand_offsets", 8), _dev_ptr(E, "E", 2),
                                 _dev_ptr(pass_out, "pass", 1), ctypes.byref(t), _stream_ptr(stream)), "grim_autotune")
     return t
+
+
+def grim_choose_form(bank: Bank, n_reads: int, n_checks: int) -> int:
+    """GRIM_FORM_GATHER or GRIM_FORM_SCAN for a batch (cost model)."""
+    f = ctypes.c_int()
+    _check(load().grim_choose_form(bank.handle, n_reads, n_checks, ctypes.byref(f)), "grim_choose_form")
+    return f.value
+
+
+def grim_filter_auto(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, cand_bins: torch.Tensor,
+                     cand_offsets: torch.Tensor, E: torch.Tensor, pass_out: torch.Tensor | None = None,
+                     batch_reads: int = 262144, stream=None):
+    """grim_filter's pass bytes, each batch by the cheaper form; returns
+    (pass_out, reads that went through the full scan)."""
+    n_reads = read_offsets.numel() - 1
+    if n_reads < 0 or cand_offsets.numel() != n_reads + 1 or E.numel() != n_reads:
+        raise ValueError("read_offsets / cand_offsets / E sizes do not match")
+    if pass_out is None:
+        pass_out = torch.empty(cand_bins.numel(), dtype=torch.uint8, device=cand_bins.device)
+    scanned = ctypes.c_int64()
+    _check(load().grim_filter_auto(bank.handle, _dev_ptr(reads, "reads", 1), _dev_ptr(read_offsets, "read_offsets", 8),
+                                   n_reads, _dev_ptr(cand_bins, "cand_bins", 4),
+                                   _dev_ptr(cand_offsets, "cand_offsets", 8), _dev_ptr(E, "E", 2),
+                                   _dev_ptr(pass_out, "pass", 1), batch_reads, ctypes.byref(scanned),
+                                   _stream_ptr(stream)), "grim_filter_auto")
+    return pass_out, scanned.value

@@ -181,6 +181,11 @@ int grim_autotune(const grim_bank* bank, const uint8_t* reads, const int64_t* re
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != GRIM_OK) return rc;
+    int64_t bounds[2] = {0, 0};
+    GRIM_CUDA_TRY(cudaMemcpyAsync(&bounds[0], cand_offsets, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GRIM_CUDA_TRY(cudaMemcpyAsync(&bounds[1], cand_offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GRIM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (best_ms > 0 && bounds[1] > bounds[0]) grim::record_gather_rate(bank, (bounds[1] - bounds[0]) / (best_ms * 1e-3));
     best.use_graph = 1;
     *out = best;
     std::lock_guard<std::mutex> lock(g_tune_mu);

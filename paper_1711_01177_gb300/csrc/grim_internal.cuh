@@ -76,6 +76,9 @@ int launch_gather_persistent(const grim_bank* bank, const GatherArgs& a, const g
                              unsigned long long* counter, cudaStream_t stream);
 
 size_t scan_scratch_bytes(int q, int64_t n_reads);
+
+// Gather rate (checks/s) measured by the autotuner, used by the dispatcher.
+void record_gather_rate(const grim_bank* bank, double checks_per_s);
 int launch_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                 const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,
                 uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* scratch,

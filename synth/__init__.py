@@ -56,6 +56,7 @@ def _load():
             "synth_cand_counts": (None, [U64, I64, I32, I32, I64, P]),
             "synth_cands_random": (I32, [U64, I64, P, I32, I64, P, P]),
             "synth_seed_index": (I32, [P, I64, I32, P, P]),
+            "synth_seed_index_needed": (I64, [P, I64, I32, P, P, P]),
             "synth_cands_seeds": (I64, [P, P, I32, P, P, I64, I32, I64, I32, I64, P, P]),
             "synth_E_rate": (None, [P, I64, I32, I32, P]),
         }
@@ -136,6 +137,30 @@ def seed_index(codes: np.ndarray, k: int = 12):
     if _load().synth_seed_index(_p(codes), len(codes), k, _p(offsets), _p(positions)) != 0:
         raise ValueError("synth_seed_index failed")
     return offsets, positions
+
+
+def seed_index_for_reads(codes: np.ndarray, bases: np.ndarray, offsets: np.ndarray, k: int = 12):
+    """The seed index restricted to the k-mers the reads' non-overlapping
+    seeds ask for (same hits for those seeds as the full index)."""
+    lib = _load()
+    needed = np.zeros((1 << (2 * k)) // 64, dtype=np.uint64)
+    L = np.diff(offsets)
+    starts = offsets[:-1]
+    for o in range(0, int(L.max()) - k + 1, k):
+        sel = L >= o + k
+        pos = starts[sel] + o
+        key = np.zeros(len(pos), dtype=np.uint64)
+        for j in range(k):
+            key = (key << np.uint64(2)) | bases[pos + j].astype(np.uint64)
+        np.bitwise_or.at(needed, key >> np.uint64(6), np.uint64(1) << (key & np.uint64(63)))
+    idx_off = np.empty((1 << (2 * k)) + 1, dtype=np.uint32)
+    n = lib.synth_seed_index_needed(_p(codes), len(codes), k, _p(needed), _p(idx_off), None)
+    if n < 0:
+        raise ValueError("synth_seed_index_needed failed")
+    positions = np.empty(max(int(n), 1), dtype=np.uint32)
+    if lib.synth_seed_index_needed(_p(codes), len(codes), k, _p(needed), _p(idx_off), _p(positions)) < 0:
+        raise ValueError("synth_seed_index_needed failed")
+    return idx_off, positions
 
 
 def cands_seeds(index, bases: np.ndarray, offsets: np.ndarray, bin_len: int, n_bins: int, cap: int,
@@ -230,7 +255,7 @@ def gather_seeds(ref_len: int = 100_000_000, n_reads: int = 1_000_000, L: int = 
     off = read_offsets(n_reads, L, L, read_seed)
     bases, starts = reads(codes, off, read_seed, sub, indel)
     n_bins = -(-ref_len // bin_len)
-    idx = seed_index(codes, seed_k)
+    idx = seed_index_for_reads(codes, bases, off, seed_k)
     cb, co = cands_seeds(idx, bases, off, bin_len, n_bins, cap, seed_k)
     del idx
     return Workload(f"gather_seeds_{ref_len}bp_q{q}_L{L}_cap{cap}", codes, pack2bit(codes), q, bin_len, overlap,
@@ -252,6 +277,26 @@ def batched_varlen(ref_len: int = 100_000_000, n_reads: int = 2_000_000, lmin: i
     return Workload(f"batched_varlen_{ref_len}bp_q{q}_L{lmin}-{lmax}", codes, pack2bit(codes), q, bin_len,
                     overlap, bases, off, starts, E_rate(off), cb, co,
                     {"sub": sub, "indel": indel, "repeat_frac": repeat_frac})
+
+
+def mixed_seeds(ref_len: int = 3_100_000_000, n_reads: int = 65_536, L: int = 100, q: int = 5,
+                bin_len: int = 256, overlap: int = 100, E: int = 5, cap: int = 10_000, repeat_frac: float = 0.40,
+                div_lo: float = 0.05, div_hi: float = 0.20, sub: float = 0.03, indel: float = 0.01, seed_k: int = 12,
+                read_seed: int = SEED_READS) -> Workload:
+    """Genome-scale reference with 40% repeats at 5-20% divergence; 100 bp
+    reads; candidates = bins of all exact 12-mer seed hits, capped at
+    10,000 per read (dense for reads from repeat families)."""
+    codes = ref_with_repeats(ref_len, SEED_REF + 100, repeat_frac, div_lo=div_lo, div_hi=div_hi)
+    off = read_offsets(n_reads, L, L, read_seed)
+    bases, starts = reads(codes, off, read_seed, sub, indel)
+    n_bins = -(-ref_len // bin_len)
+    idx = seed_index_for_reads(codes, bases, off, seed_k)
+    cb, co = cands_seeds(idx, bases, off, bin_len, n_bins, cap, seed_k)
+    del idx
+    return Workload(f"mixed_seeds_{ref_len}bp_q{q}_L{L}_cap{cap}", codes, pack2bit(codes), q, bin_len, overlap,
+                    bases, off, starts, np.full(n_reads, E, dtype=np.uint16), cb, co,
+                    {"sub": sub, "indel": indel, "repeat_frac": repeat_frac, "seed_k": seed_k,
+                     "div": [div_lo, div_hi]})
 
 
 def fullscan(ref_len: int = 3_100_000_000, n_reads: int = 65_536, L: int = 100, q: int = 5,

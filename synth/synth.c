@@ -17,6 +17,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -167,7 +170,7 @@ int synth_reads(uint64_t seed, const uint8_t* codes, int64_t len, int64_t n, con
 
 /* ---------------------------------------------------------- candidates */
 
-/* sort u32 ascending: insertion sort for short arrays, else two 16-bit LSD
+/* sort u32 ascending: insertion sort for short arrays, else four 8-bit LSD
  * radix passes through tmp (same length) */
 static void sort_u32(uint32_t* a, int64_t n, uint32_t* tmp) {
     if (n <= 48) {
@@ -179,18 +182,18 @@ static void sort_u32(uint32_t* a, int64_t n, uint32_t* tmp) {
         }
         return;
     }
-    static const int B = 1 << 16;
-    int64_t* cnt = (int64_t*)calloc((size_t)B + 1, sizeof(int64_t));
-    for (int pass = 0; pass < 2; pass++) {
-        int sh = 16 * pass;
-        uint32_t* src = pass == 0 ? a : tmp;
-        uint32_t* dst = pass == 0 ? tmp : a;
-        memset(cnt, 0, sizeof(int64_t) * (size_t)(B + 1));
-        for (int64_t i = 0; i < n; i++) cnt[((src[i] >> sh) & 0xFFFF) + 1]++;
-        for (int b = 0; b < B; b++) cnt[b + 1] += cnt[b];
-        for (int64_t i = 0; i < n; i++) dst[cnt[(src[i] >> sh) & 0xFFFF]++] = src[i];
+    int64_t cnt[257];
+    uint32_t* src = a;
+    uint32_t* dst = tmp;
+    for (int pass = 0; pass < 4; pass++) {
+        int sh = 8 * pass;
+        memset(cnt, 0, sizeof(cnt));
+        for (int64_t i = 0; i < n; i++) cnt[((src[i] >> sh) & 0xFF) + 1]++;
+        for (int b = 0; b < 256; b++) cnt[b + 1] += cnt[b];
+        for (int64_t i = 0; i < n; i++) dst[cnt[(src[i] >> sh) & 0xFF]++] = src[i];
+        uint32_t* t = src; src = dst; dst = t;
     }
-    free(cnt);
+    /* four passes: the result is back in a */
 }
 
 /* per-read generator, so that reads can be drawn in any order or in parallel */
@@ -271,7 +274,9 @@ static uint64_t kmer_key(const uint8_t* s, int k) {
 
 /*
  * CSR index of every k-mer start position: offsets[4^k + 1] (uint32),
- * positions[len-k+1] (uint32) grouped by key, ascending within a key.
+ * positions[len-k+1] (uint32) grouped by key.  Built in parallel; the order
+ * of positions within a key is unspecified (the candidate lists drawn from
+ * the index do not depend on it: hits are deduplicated and sorted by bin).
  */
 int synth_seed_index(const uint8_t* codes, int64_t len, int k, uint32_t* offsets, uint32_t* positions) {
     if (k < 1 || k > 15 || len < k || len > 0xFFFFFFFFLL) return -1;
@@ -279,22 +284,112 @@ int synth_seed_index(const uint8_t* codes, int64_t len, int k, uint32_t* offsets
     memset(offsets, 0, sizeof(uint32_t) * (size_t)(nk + 1));
     int64_t npos = len - k + 1;
     uint64_t mask = nk - 1;
-    uint64_t v = kmer_key(codes, k - 1);
-    for (int64_t p = 0; p < npos; p++) {
-        v = ((v << 2) | codes[p + k - 1]) & mask;
-        offsets[v + 1]++;
+#pragma omp parallel
+    {
+#ifdef _OPENMP
+        int nt = omp_get_num_threads(), t = omp_get_thread_num();
+#else
+        int nt = 1, t = 0;
+#endif
+        int64_t a = npos * t / nt, b = npos * (t + 1) / nt;
+        if (a < b) {
+            uint64_t v = kmer_key(codes + a, k - 1);
+            for (int64_t p = a; p < b; p++) {
+                v = ((v << 2) | codes[p + k - 1]) & mask;
+#pragma omp atomic
+                offsets[v + 1]++;
+            }
+        }
     }
     for (uint64_t x = 0; x < nk; x++) offsets[x + 1] += offsets[x];
     uint32_t* fill = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nk);
     if (!fill) return -1;
     memcpy(fill, offsets, sizeof(uint32_t) * (size_t)nk);
-    v = kmer_key(codes, k - 1);
-    for (int64_t p = 0; p < npos; p++) {
-        v = ((v << 2) | codes[p + k - 1]) & mask;
-        positions[fill[v]++] = (uint32_t)p;
+#pragma omp parallel
+    {
+#ifdef _OPENMP
+        int nt = omp_get_num_threads(), t = omp_get_thread_num();
+#else
+        int nt = 1, t = 0;
+#endif
+        int64_t a = npos * t / nt, b = npos * (t + 1) / nt;
+        if (a < b) {
+            uint64_t v = kmer_key(codes + a, k - 1);
+            for (int64_t p = a; p < b; p++) {
+                v = ((v << 2) | codes[p + k - 1]) & mask;
+                uint32_t slot;
+#pragma omp atomic capture
+                slot = fill[v]++;
+                positions[slot] = (uint32_t)p;
+            }
+        }
     }
     free(fill);
     return 0;
+}
+
+/*
+ * The same CSR index restricted to the k-mers set in `needed` (a bitmap of
+ * 4^k bits): offsets[4^k + 1] count only needed keys.  Call with
+ * positions == NULL to count (returns the number of positions), then with
+ * a buffer of that size to fill.  Other keys have empty ranges.
+ */
+int64_t synth_seed_index_needed(const uint8_t* codes, int64_t len, int k, const uint64_t* needed,
+                                uint32_t* offsets, uint32_t* positions) {
+    if (k < 1 || k > 15 || len < k || len > 0xFFFFFFFFLL) return -1;
+    uint64_t nk = 1ULL << (2 * k);
+    int64_t npos = len - k + 1;
+    uint64_t mask = nk - 1;
+    if (!positions) {
+        memset(offsets, 0, sizeof(uint32_t) * (size_t)(nk + 1));
+#pragma omp parallel
+        {
+#ifdef _OPENMP
+            int nt = omp_get_num_threads(), t = omp_get_thread_num();
+#else
+            int nt = 1, t = 0;
+#endif
+            int64_t a = npos * t / nt, b = npos * (t + 1) / nt;
+            if (a < b) {
+                uint64_t v = kmer_key(codes + a, k - 1);
+                for (int64_t p = a; p < b; p++) {
+                    v = ((v << 2) | codes[p + k - 1]) & mask;
+                    if ((needed[v >> 6] >> (v & 63)) & 1) {
+#pragma omp atomic
+                        offsets[v + 1]++;
+                    }
+                }
+            }
+        }
+        for (uint64_t x = 0; x < nk; x++) offsets[x + 1] += offsets[x];
+        return (int64_t)offsets[nk];
+    }
+    uint32_t* fill = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nk);
+    if (!fill) return -1;
+    memcpy(fill, offsets, sizeof(uint32_t) * (size_t)nk);
+#pragma omp parallel
+    {
+#ifdef _OPENMP
+        int nt = omp_get_num_threads(), t = omp_get_thread_num();
+#else
+        int nt = 1, t = 0;
+#endif
+        int64_t a = npos * t / nt, b = npos * (t + 1) / nt;
+        if (a < b) {
+            uint64_t v = kmer_key(codes + a, k - 1);
+            for (int64_t p = a; p < b; p++) {
+                v = ((v << 2) | codes[p + k - 1]) & mask;
+                if ((needed[v >> 6] >> (v & 63)) & 1) {
+                    uint32_t slot;
+#pragma omp atomic capture
+                    slot = fill[v]++;
+                    positions[slot] = (uint32_t)p;
+                }
+            }
+        }
+    }
+    free(fill);
+    return (int64_t)offsets[nk];
 }
 
 typedef struct { uint32_t bin, support; } bin_support;
@@ -311,10 +406,11 @@ static int cmp_bin(const void* a, const void* b) {
 }
 
 /* distinct voted bins of one read (see synth_cands_seeds); returns the
- * count, bins in (*hits)[0..count) ascending; -1 on allocation failure */
+ * count, bins in (*hits)[0..count) ascending; -1 on allocation failure.
+ * bins/tmp: u32 scratch of *hcap entries each (grown with hits). */
 static int64_t seed_bins_of_read(const uint32_t* idx_offsets, const uint32_t* idx_positions, int k,
                                  const uint8_t* s, int64_t L, int bin_len, int64_t n_bins, int cap,
-                                 bin_support** hits, int64_t* hcap) {
+                                 bin_support** hits, uint32_t** bins, uint32_t** tmp, int64_t* hcap) {
     int64_t nh = 0;
     for (int64_t o = 0; o + k <= L; o += k) {
         uint64_t key = kmer_key(s + o, k);
@@ -322,25 +418,27 @@ static int64_t seed_bins_of_read(const uint32_t* idx_offsets, const uint32_t* id
         if (nh + (int64_t)(b - a) > *hcap) {
             while (nh + (int64_t)(b - a) > *hcap) *hcap *= 2;
             bin_support* h2 = (bin_support*)realloc(*hits, sizeof(bin_support) * (size_t)*hcap);
-            if (!h2) return -1;
-            *hits = h2;
+            uint32_t* b2 = (uint32_t*)realloc(*bins, sizeof(uint32_t) * (size_t)*hcap);
+            uint32_t* t2 = (uint32_t*)realloc(*tmp, sizeof(uint32_t) * (size_t)*hcap);
+            if (h2) *hits = h2;
+            if (b2) *bins = b2;
+            if (t2) *tmp = t2;
+            if (!h2 || !b2 || !t2) return -1;
         }
         for (uint32_t j = a; j < b; j++) {
             int64_t st = (int64_t)idx_positions[j] - o;
             if (st < 0) st = 0;
             int64_t bin = st / bin_len;
             if (bin >= n_bins) bin = n_bins - 1;
-            (*hits)[nh].bin = (uint32_t)bin;
-            (*hits)[nh].support = 1;
-            nh++;
+            (*bins)[nh++] = (uint32_t)bin;
         }
     }
+    sort_u32(*bins, nh, *tmp);
     bin_support* h = *hits;
-    qsort(h, (size_t)nh, sizeof(bin_support), cmp_bin);
     int64_t u = 0;
     for (int64_t j = 0; j < nh; j++) {
-        if (u > 0 && h[u - 1].bin == h[j].bin) h[u - 1].support++;
-        else h[u++] = h[j];
+        if (u > 0 && h[u - 1].bin == (*bins)[j]) h[u - 1].support++;
+        else { h[u].bin = (*bins)[j]; h[u].support = 1; u++; }
     }
     if (u > cap) {
         qsort(h, (size_t)u, sizeof(bin_support), cmp_support);
@@ -369,16 +467,19 @@ int64_t synth_cands_seeds(const uint32_t* idx_offsets, const uint32_t* idx_posit
     {
         int64_t hcap = 1 << 12;
         bin_support* hits = (bin_support*)malloc(sizeof(bin_support) * (size_t)hcap);
-        if (!hits) err = 1;
-#pragma omp for schedule(dynamic, 1024)
+        uint32_t* bins = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)hcap);
+        uint32_t* tmp = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)hcap);
+        if (!hits || !bins || !tmp) err = 1;
+#pragma omp for schedule(dynamic, 256)
         for (int64_t r = 0; r < n; r++) {
-            if (!hits) continue;
+            if (!hits || !bins || !tmp) continue;
             int64_t u = seed_bins_of_read(idx_offsets, idx_positions, k, bases + read_offsets[r],
-                                          read_offsets[r + 1] - read_offsets[r], bin_len, n_bins, cap, &hits, &hcap);
+                                          read_offsets[r + 1] - read_offsets[r], bin_len, n_bins, cap, &hits, &bins,
+                                          &tmp, &hcap);
             if (u < 0) { err = 1; u = 0; }
             cand_offsets[r + 1] = u;
         }
-        free(hits);
+        free(hits); free(bins); free(tmp);
     }
     if (err) return -1;
     cand_offsets[0] = 0;
@@ -390,16 +491,19 @@ int64_t synth_cands_seeds(const uint32_t* idx_offsets, const uint32_t* idx_posit
     {
         int64_t hcap = 1 << 12;
         bin_support* hits = (bin_support*)malloc(sizeof(bin_support) * (size_t)hcap);
-        if (!hits) err = 1;
-#pragma omp for schedule(dynamic, 1024)
+        uint32_t* bins = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)hcap);
+        uint32_t* tmp = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)hcap);
+        if (!hits || !bins || !tmp) err = 1;
+#pragma omp for schedule(dynamic, 256)
         for (int64_t r = 0; r < n; r++) {
-            if (!hits) continue;
+            if (!hits || !bins || !tmp) continue;
             int64_t u = seed_bins_of_read(idx_offsets, idx_positions, k, bases + read_offsets[r],
-                                          read_offsets[r + 1] - read_offsets[r], bin_len, n_bins, cap, &hits, &hcap);
+                                          read_offsets[r + 1] - read_offsets[r], bin_len, n_bins, cap, &hits, &bins,
+                                          &tmp, &hcap);
             if (u < 0) { err = 1; continue; }
             for (int64_t j = 0; j < u; j++) cand_bins[cand_offsets[r] + j] = hits[j].bin;
         }
-        free(hits);
+        free(hits); free(bins); free(tmp);
     }
     return err ? -1 : total;
 }

@@ -158,3 +158,45 @@ def test_scan_bad_reads_never_pass(oracle):
     rp = host(res.read_pass[:64], np.uint32)
     assert rp[5] == 0 and rp.sum() > 0
     bank.free()
+
+
+def test_scan_3gbp_batch_sampled(oracle):
+    """3.1 Gbp repeat-rich reference (12.1M bins), one batch of 65,536 x 100 bp
+    reads: the launch bench.py times, checked on sampled pairs, sampled
+    reads x bins, and per-read counts."""
+    w = synth.fullscan()
+    bank = grim.grim_build_bank(dev(w.ref2bit), w.ref_len, w.q, w.bin_len, w.overlap)
+    res = grim.grim_scan(bank, dev(w.bases), dev(w.read_offsets), dev(w.E), cap=1 << 24, with_read_pass=True)
+    assert grim.grim_bank_status(bank) == (grim.GRIM_OK, 0)
+    n = res.n_pairs
+    assert 0 < n <= 1 << 24
+    pr = host(res.pair_read[:n], np.uint32)
+    pb = host(res.pair_bin[:n], np.uint32)
+    ps = host(res.pair_sum[:n], np.uint16)
+    rp = host(res.read_pass[:w.n_reads], np.uint32)
+    assert np.array_equal(np.bincount(pr, minlength=w.n_reads).astype(np.uint32), rp)
+    key = pr.astype(np.int64) * w.n_bins + pb
+    assert len(np.unique(key)) == n  # each pair once
+    T = (100 - w.q + 1) - w.q * int(w.E[0])
+    rng = np.random.default_rng(9)
+    row_cache = {}
+
+    def row(b):
+        if b not in row_cache:
+            row_cache[b] = oracle.bin_row(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap, int(b))
+        return row_cache[b]
+
+    for i in rng.integers(0, n, 300):  # every reported pair is a pass with the oracle's sum
+        read = w.bases[w.read_offsets[pr[i]]:w.read_offsets[pr[i] + 1]]
+        s = oracle.sum_one(row(pb[i]), w.q, read)
+        assert s == ps[i] and s >= T
+    got = set(key.tolist())
+    for r in rng.integers(0, w.n_reads, 4):  # sampled bins of sampled reads: nothing missed, nothing extra
+        read = w.bases[w.read_offsets[r]:w.read_offsets[r + 1]]
+        true_bin = int(w.starts[r] // w.bin_len)
+        bins = set(range(max(0, true_bin - 20), min(w.n_bins, true_bin + 21)))
+        bins |= set(rng.integers(0, w.n_bins, 1500).tolist())
+        for b in bins:
+            passes = oracle.sum_one(row(b), w.q, read) >= T
+            assert passes == ((int(r) * w.n_bins + b) in got), (r, b)
+    bank.free()
