@@ -7,11 +7,11 @@
 //
 // Exactness.  sm_103a has no integer tcgen05 kind, so the contraction runs
 // on kind::f8f6f4 with e4m3 operands and f32 accumulation.  A = bank bits as
-// e4m3 0.0 / 1.0.  B = the read's token counts split in base-16 digits
+// e4m3 0 / 2^-6.  B = the read's token counts split in base-16 digits
 // (count = sum_d 16^d * digit_d, digit_d in [0, 15], each digit exact in
 // e4m3); every digit of every read is its own B row, so one MMA yields
 // sum_t bit * digit_d for all (read, digit) rows at once, and the epilogue
-// recombines Sum = sum_d 16^d * acc_d.  Every product is 0 or a small
+// recombines Sum = 64 * sum_d 16^d * acc_d.  Every product is 0 or a small
 // integer and every partial sum is below 2^24, so f32 accumulation is exact
 // and the pass decision is bit-identical to counting tokens one by one.
 // Reads whose counts stay below 16 (nearly all) take one row; reads with
@@ -24,14 +24,15 @@
 //         in shared memory in the 128-byte-swizzled K-major layout;
 //   bank: tiles of 128 bin rows stream through a 4-deep shared-memory ring
 //         by 1-D TMA bulk copies (warp 0);
-//   A   : warps 2-5 (one thread per bin = per TMEM lane) expand 128 bits of
-//         their bin's row into 128 e4m3 bytes and store them straight into
-//         tensor memory (4 stages of 32 columns) - the expanded operand never
-//         touches shared memory;
+//   A   : warps 2-9 (one thread per bin = per TMEM lane; two groups of four
+//         warps taking alternate K chunks) expand 128 bits of their bin's row
+//         into 128 e4m3 bytes and store them straight into tensor memory (2
+//         stages of 128 columns = 512 tokens, 16 MMAs per stage) - the
+//         expanded operand never touches shared memory;
 //   MMA : warp 1 issues M=128 (bins) x N=128 (rows) x K=32 tcgen05.mma with A
 //         from TMEM, B from shared memory, accumulating in TMEM (two 128-column
 //         accumulators);
-//   out : warps 6-9 read the accumulators with tcgen05.ld, recombine digits,
+//   out : warps 10-13 read the accumulators with tcgen05.ld, recombine digits,
 //         compare with each read's threshold and append the rare passing
 //         (read, bin, sum) triples with warp-aggregated atomics.
 // Every wait is an mbarrier try_wait bounded by a time limit; on expiry the
@@ -51,14 +52,16 @@ static __device__ __align__(256) uint8_t g_scan_scratch[GRIM_SCAN_NOALLOC_SCRATC
 
 // ------------------------------------------------------------ constants
 
-constexpr int kScanThreads = 320;   // 10 warps: TMA, MMA, 4 expand, 4 epilogue
+constexpr int kScanThreads = 448;   // 14 warps: TMA, MMA, 2 x 4 expand, 4 epilogue
+constexpr int kExpandWarp0 = 2;     // expander warps 2..9: group (warp-2)/4 takes every other K chunk
+constexpr int kEpilogueWarp0 = 10;  // epilogue warps 10..13
 constexpr int kBinTile = 128;       // bins per MMA tile (M, TMEM lanes)
 constexpr int kRowsTile = 128;      // B rows per read tile (N)
 constexpr int kBankStages = 4;
-constexpr int kAStages = 4;
-constexpr int kACols = 32;          // TMEM columns per A stage (128 K bytes)
+constexpr int kAStages = 2;          // one per expander group
+constexpr int kACols = 128;         // TMEM columns per A stage (up to 512 K bytes)
 constexpr int kAccCol = 0;          // two accumulators: columns [0, 256)
-constexpr int kACol = 256;          // A stages: columns [256, 384)
+constexpr int kACol = 256;          // A stages: columns [256, 512)
 constexpr int kTmemCols = 512;
 constexpr int kPrepWarps = 8;
 constexpr int kNumClasses = 3;      // digit classes: 1, 2, 4 digits
@@ -72,7 +75,10 @@ struct ScanGeo {
     static constexpr int kRowWords = Geo<Q>::kRowWords;
     static constexpr int kRowBytes = kRowWords * 4;
     static constexpr int kK = (1 << (2 * Q)) < 128 ? 128 : (1 << (2 * Q));  // padded token count
-    static constexpr int kChunks = kK / 128;                                  // 128-token K chunks
+    static constexpr int kChunkTok = kK >= 512 ? 512 : kK;                   // tokens per A stage
+    static constexpr int kVecPerChunk = kChunkTok / 128;                      // 16-byte row slices per stage
+    static constexpr int kMmaPerChunk = kChunkTok / 32;                       // K=32 MMAs per stage
+    static constexpr int kChunks = kK / kChunkTok;
     static constexpr int kBBytes = kRowsTile * kK;                            // staged B tile
     static constexpr int kBankTileBytes = kBinTile * kRowBytes;
     static_assert(kRowBytes * 8 == kK, "a bank row holds exactly the padded K bits");
@@ -232,7 +238,7 @@ __host__ __device__ constexpr uint32_t idesc_f8(int M, int N) {
     return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// e4m3 bit pattern of an integer 0..15
+// e4m3 bit pattern of an integer 0..15 (B digits)
 __device__ __forceinline__ uint32_t e4m3_small_int(uint32_t k) {
     if (k == 0) return 0;
     const uint32_t e = 31 - __clz(k);
@@ -240,9 +246,21 @@ __device__ __forceinline__ uint32_t e4m3_small_int(uint32_t k) {
     return ((e + 7u) << 3) | m;
 }
 
-// four bits -> four bytes, 0x00 or 0x38 (e4m3 1.0), bit i in byte i
-__device__ __forceinline__ uint32_t expand_nibble(uint32_t n) {
-    return ((n * 0x00204081u) & 0x01010101u) * 0x38u;
+// A operand: a set bit is e4m3 0x08 = 2^-6 (the smallest normal), a clear bit
+// 0.  Products with the B digits (0..15) and all partial sums (multiples of
+// 2^-6 below 2^8) are exact in f32; the epilogue scales back by 64.
+// Four bits n (bit i -> byte i): n * 0x01020408 puts bit i at bit 8i + 3 with
+// no overlapping copies, the mask keeps exactly those bits.
+__device__ __forceinline__ uint32_t expand_nibble(uint32_t n) { return (n * 0x01020408u) & 0x08080808u; }
+
+// 32 bits of a row -> 8 columns of A (4 tokens per column, token t in byte t%4).
+__device__ __forceinline__ void expand_word(uint32_t w, uint32_t* v) {
+    const uint32_t lo = w & 0x0F0F0F0Fu, hi = (w >> 4) & 0x0F0F0F0Fu;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        v[2 * k] = expand_nibble(__byte_perm(lo, 0u, 0x4440u | k));
+        v[2 * k + 1] = expand_nibble(__byte_perm(hi, 0u, 0x4440u | k));
+    }
 }
 
 // ------------------------------------------------------------ prep kernel
@@ -343,7 +361,8 @@ struct ScanSmem {
     static constexpr size_t kB = 0;                                     // 1024-aligned
     static constexpr size_t kBank = kB + G::kBBytes;                    // 1024-aligned
     static constexpr size_t kT = kBank + (size_t)kBankStages * G::kBankTileBytes;
-    static constexpr size_t kRid = kT + 4 * kRowsTile;
+    static constexpr size_t kTf = kT + 4 * kRowsTile;
+    static constexpr size_t kRid = kTf + 4 * kRowsTile;
     static constexpr size_t kBars = kRid + 4 * kRowsTile;
     static constexpr size_t kMisc = kBars + 8 * (2 * kBankStages + 2 * kAStages + 5);
     static constexpr size_t kTotal = kMisc + 64;
@@ -360,13 +379,48 @@ struct ScanParams {
     uint32_t* status;
 };
 
+// Appends the passing (read, bin) pairs of one group of reads: sums[i] is
+// the sum of read n0 + i for this thread's bin.  Rare path.
+template <int NG>
+__device__ __forceinline__ void scan_emit(const ScanParams& P, const int* sums, int n0, int valid_reads,
+                                          const int32_t* __restrict__ sT, const uint32_t* __restrict__ sRid,
+                                          int64_t b, bool bin_ok, int lane) {
+    for (int i = 0; i < NG && n0 + i < valid_reads; i++) {
+        const int n = n0 + i;
+        const int sum = sums[i];
+        const bool p = bin_ok && sum >= sT[n];
+        const uint32_t bal = __ballot_sync(kFull, p);
+        if (!bal) continue;
+        const int leader = __ffs(bal) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) {
+            base = atomicAdd(P.out.n_pairs, (unsigned long long)__popc(bal));
+            if (P.out.read_pass) atomicAdd(&P.out.read_pass[sRid[n]], (uint32_t)__popc(bal));
+        }
+        base = __shfl_sync(kFull, base, leader);
+        if (p) {
+            const unsigned long long idx = base + __popc(bal & ((1u << lane) - 1u));
+            if ((long long)idx < P.out.cap) {
+                P.out.pair_read[idx] = sRid[n];
+                P.out.pair_bin[idx] = (uint32_t)b;
+                if (P.out.pair_sum) P.out.pair_sum[idx] = (uint16_t)sum;
+            } else {
+                atomicOr(P.status, GRIM_FLAG_OVERFLOW);
+            }
+        }
+    }
+}
+
 // Epilogue of one work item for reads with D base-16 digits (N = 128 / D
 // reads per tile): thread = bin row = TMEM lane of its warp's quadrant.
+// Accumulator column d*N + n holds 2^-6 * (digit-d sum of read n); the
+// columns are read 64 at a time.
 template <int D>
 __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem, uint64_t* acc_full,
                                               uint64_t* acc_empty, volatile int* abort_flag,
-                                              const int32_t* __restrict__ sT, const uint32_t* __restrict__ sRid,
-                                              int valid_reads, int64_t bt0, int64_t bt1, uint32_t& acc_cnt) {
+                                              const int32_t* __restrict__ sT, const float* __restrict__ sTf,
+                                              const uint32_t* __restrict__ sRid, int valid_reads, int64_t bt0,
+                                              int64_t bt1, uint32_t& acc_cnt) {
     constexpr int N = kRowsTile / D;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quad = warp & 3;
@@ -376,56 +430,63 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
         const uint32_t buf = acc_cnt & 1, phb = (acc_cnt >> 1) & 1;
         if (!__all_sync(kFull, mbar_wait(&acc_full[buf], phb, abort_flag))) break;
         tc_fence_after();
-        uint32_t v[kRowsTile];
-#pragma unroll
-        for (int cb = 0; cb < kRowsTile / 32; cb++)
-            tmem_ld32(tmem + lane_base + kAccCol + buf * kRowsTile + cb * 32, v + cb * 32);
-        tmem_wait_ld();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[buf]);
-        acc_cnt++;
-
+        const uint32_t col0 = tmem + lane_base + kAccCol + buf * kRowsTile;
         const int64_t b = P.bin_begin + bt * kBinTile + m;
         const bool bin_ok = b < P.bin_end;
-        // Sum(read n) = sum_d 16^d * acc[d*N + n]; partial sums are exact in f32
-        uint32_t any = 0;
+        if (D == 1) {
+            // one digit: compare 2^-6 * Sum with T / 64 in f32 (both exact)
 #pragma unroll
-        for (int n = 0; n < N; n++) {
-            int sum = 0;
+            for (int h = 0; h < 2; h++) {
+                uint32_t v[64];
+                tmem_ld32(col0 + 64 * h, v);
+                tmem_ld32(col0 + 64 * h + 32, v + 32);
+                tmem_wait_ld();
+                if (h == 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                }
+                uint32_t any = 0;
 #pragma unroll
-            for (int d = 0; d < D; d++) sum += (int)__uint_as_float(v[d * N + n]) << (4 * d);
-            v[n] = (uint32_t)sum;
-            any |= (uint32_t)(sum >= sT[n]);
-        }
-        if (!__any_sync(kFull, bin_ok && any)) continue;
-        // rare: some (read, bin) passes; walk the reads with warp-aggregated appends
-        uint32_t loc[N];
+                for (int i = 0; i < 64; i++) any |= (uint32_t)(__uint_as_float(v[i]) >= sTf[64 * h + i]);
+                if (__any_sync(kFull, bin_ok && any)) {
+                    int sums[64];
 #pragma unroll
-        for (int n = 0; n < N; n++) loc[n] = v[n];
-        for (int n = 0; n < valid_reads; n++) {
-            const int sum = (int)loc[n];
-            const bool p = bin_ok && sum >= sT[n];
-            const uint32_t bal = __ballot_sync(kFull, p);
-            if (!bal) continue;
-            const int leader = __ffs(bal) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) {
-                base = atomicAdd(P.out.n_pairs, (unsigned long long)__popc(bal));
-                if (P.out.read_pass) atomicAdd(&P.out.read_pass[sRid[n]], (uint32_t)__popc(bal));
-            }
-            base = __shfl_sync(kFull, base, leader);
-            if (p) {
-                const unsigned long long idx = base + __popc(bal & ((1u << lane) - 1u));
-                if ((long long)idx < P.out.cap) {
-                    P.out.pair_read[idx] = sRid[n];
-                    P.out.pair_bin[idx] = (uint32_t)b;
-                    if (P.out.pair_sum) P.out.pair_sum[idx] = (uint16_t)sum;
-                } else {
-                    atomicOr(P.status, GRIM_FLAG_OVERFLOW);
+                    for (int i = 0; i < 64; i++) sums[i] = (int)(__uint_as_float(v[i]) * 64.0f);
+                    scan_emit<64>(P, sums, 64 * h, valid_reads, sT, sRid, b, bin_ok, lane);
                 }
             }
+        } else {
+            // D digits: groups of 32 reads, two digit columns per load round
+#pragma unroll
+            for (int g = 0; g < N / 32; g++) {
+                int acc[32];
+#pragma unroll
+                for (int i = 0; i < 32; i++) acc[i] = 0;
+#pragma unroll
+                for (int d = 0; d < D; d += 2) {
+                    uint32_t v[64];
+                    tmem_ld32(col0 + d * N + 32 * g, v);
+                    tmem_ld32(col0 + (d + 1) * N + 32 * g, v + 32);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 32; i++)
+                        acc[i] += ((int)(__uint_as_float(v[i]) * 64.0f) << (4 * d)) +
+                                  ((int)(__uint_as_float(v[32 + i]) * 64.0f) << (4 * (d + 1)));
+                }
+                if (g == N / 32 - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                }
+                uint32_t any = 0;
+#pragma unroll
+                for (int i = 0; i < 32; i++) any |= (uint32_t)(acc[i] >= sT[32 * g + i]);
+                if (__any_sync(kFull, bin_ok && any))
+                    scan_emit<32>(P, acc, 32 * g, valid_reads, sT, sRid, b, bin_ok, lane);
+            }
         }
+        acc_cnt++;
     }
 }
 
@@ -438,6 +499,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
     uint8_t* sB = smem + S::kB;
     uint8_t* sBank = smem + S::kBank;
     int32_t* sT = reinterpret_cast<int32_t*>(smem + S::kT);
+    float* sTf = reinterpret_cast<float*>(smem + S::kTf);
     uint32_t* sRid = reinterpret_cast<uint32_t*>(smem + S::kRid);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kBars);
     uint64_t* bank_full = bars;
@@ -458,7 +520,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
     if (threadIdx.x == 0) {
         for (int i = 0; i < kBankStages; i++) {
             mbar_init(&bank_full[i], 1);
-            mbar_init(&bank_empty[i], 4);
+            mbar_init(&bank_empty[i], 8);
         }
         for (int i = 0; i < kAStages; i++) {
             mbar_init(&a_full[i], 4);
@@ -520,6 +582,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
             }
             for (int n = threadIdx.x; n < kRowsTile; n += kScanThreads) {
                 sT[n] = n < valid_reads ? P.sc.T[cls][tile * nR + n] : 0x7fffffff;
+                // T / 64 exactly (|T| < 2^24); "never passes" is +inf
+                sTf[n] = sT[n] == 0x7fffffff ? __int_as_float(0x7f800000) : (float)sT[n] * (1.0f / 64.0f);
                 sRid[n] = n < valid_reads ? P.sc.rid[cls][tile * nR + n] : 0u;
             }
             if (threadIdx.x == 0) {
@@ -562,9 +626,11 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
                         }
                         tc_fence_after();
 #pragma unroll
-                        for (int kk = 0; kk < 4; kk++) {
+                        for (int kk = 0; kk < G::kMmaPerChunk; kk++) {
                             const uint32_t a_tmem = tmem + kACol + sa * kACols + kk * 8;
-                            const uint64_t bdesc = smem_desc_sw128(smem_addr(sB) + c * (kRowsTile * 128) + kk * 32);
+                            const int kb = c * G::kVecPerChunk + (kk >> 2);  // 128-byte K block of B
+                            const uint64_t bdesc =
+                                smem_desc_sw128(smem_addr(sB) + kb * (kRowsTile * 128) + (kk & 3) * 32);
                             mma_f8f6f4_tmemA(d_tmem, a_tmem, bdesc, kIdesc, (c | kk) != 0);
                         }
                         mma_commit(&a_empty[sa]);
@@ -575,9 +641,11 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
                     acc_cnt++;
                 }
             }
-        } else if (warp < 6) {
-            // ---- expanders: thread = bin row = TMEM lane
+        } else if (warp < kEpilogueWarp0) {
+            // ---- expanders: thread = bin row = TMEM lane; group g takes the
+            // K chunks whose running index has parity g (alternate A stages)
             const int quad = warp & 3;
+            const uint32_t group = (uint32_t)((warp - kExpandWarp0) >> 2);
             const int m = quad * 32 + lane;
             const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
             for (int64_t bt = bt0; bt < bt1; bt++) {
@@ -588,26 +656,31 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
                 const uint4* myrow = reinterpret_cast<const uint4*>(sBank + (size_t)s * G::kBankTileBytes +
                                                                     (size_t)m * G::kRowBytes);
                 bool ok = true;
-                for (int c = 0; c < G::kChunks; c++) {
-                    const uint4 bits = (m < rows) ? myrow[c] : make_uint4(0, 0, 0, 0);
+                for (int c = 0; c < G::kChunks; c++, a_cnt++) {
+                    if ((a_cnt & 1u) != group) continue;
                     const uint32_t sa = a_cnt % kAStages, pha = (a_cnt / kAStages) & 1;
+                    uint4 bits[G::kVecPerChunk];
+#pragma unroll
+                    for (int u = 0; u < G::kVecPerChunk; u++)
+                        bits[u] = (m < rows) ? myrow[c * G::kVecPerChunk + u] : make_uint4(0, 0, 0, 0);
                     if (!__all_sync(kFull, mbar_wait(&a_empty[sa], pha ^ 1, abort_flag))) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    uint32_t v[32];
-                    const uint32_t w[4] = {bits.x, bits.y, bits.z, bits.w};
 #pragma unroll
-                    for (int j = 0; j < 4; j++)
-#pragma unroll
-                        for (int i = 0; i < 8; i++) v[j * 8 + i] = expand_nibble((w[j] >> (4 * i)) & 0xFu);
-                    tmem_st32(tmem + lane_base + kACol + sa * kACols, v);
+                    for (int u = 0; u < G::kVecPerChunk; u++) {
+                        uint32_t v[32];
+                        expand_word(bits[u].x, v);
+                        expand_word(bits[u].y, v + 8);
+                        expand_word(bits[u].z, v + 16);
+                        expand_word(bits[u].w, v + 24);
+                        tmem_st32(tmem + lane_base + kACol + sa * kACols + u * 32, v);
+                    }
                     tmem_wait_st();
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&a_full[sa]);
-                    a_cnt++;
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bank_empty[s]);
@@ -618,11 +691,14 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
             // ---- epilogue: thread = bin row = TMEM lane
             const int cls_now = *s_cls;
             if (cls_now == 0)
-                scan_epilogue<1>(P, tmem, acc_full, acc_empty, abort_flag, sT, sRid, *s_valid, bt0, bt1, acc_cnt);
+                scan_epilogue<1>(P, tmem, acc_full, acc_empty, abort_flag, sT, sTf, sRid, *s_valid, bt0, bt1,
+                                 acc_cnt);
             else if (cls_now == 1)
-                scan_epilogue<2>(P, tmem, acc_full, acc_empty, abort_flag, sT, sRid, *s_valid, bt0, bt1, acc_cnt);
+                scan_epilogue<2>(P, tmem, acc_full, acc_empty, abort_flag, sT, sTf, sRid, *s_valid, bt0, bt1,
+                                 acc_cnt);
             else
-                scan_epilogue<4>(P, tmem, acc_full, acc_empty, abort_flag, sT, sRid, *s_valid, bt0, bt1, acc_cnt);
+                scan_epilogue<4>(P, tmem, acc_full, acc_empty, abort_flag, sT, sTf, sRid, *s_valid, bt0, bt1,
+                                 acc_cnt);
         }
         __syncthreads();  // the item is drained before B is overwritten
     }
