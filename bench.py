@@ -45,8 +45,8 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch, from
 # an ncu capture, valid only for the kernel source it was taken on.
 TRAFFIC_BY_SOURCE: dict[str, dict] = {
-    # gather, 1M reads, 74.8M checks: 650.67 MB read + 74.77 MB written
-    "6adfb81d6d4f3ac4": {"bytes": 725_440_000},
+    # gather, 1M reads, 74.8M checks: 670.37 MB read + 77.11 MB written
+    "b975ee0a825bbbdd": {"bytes": 747_480_000},
 }
 
 
