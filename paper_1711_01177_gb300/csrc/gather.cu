@@ -10,9 +10,8 @@
 // per token.  Reads of 100-150 bases need two or three planes.
 //
 // One warp per read (grid-stride over reads):
-//   0. the first batch of candidate rows is requested before anything else,
-//      so its latency hides behind the token work (and every later batch's
-//      candidate ids are requested while the batch before it is scored);
+//   0. the first candidate rows are requested before anything else, so
+//      their latency hides behind the token work;
 //   1. lanes load the read 32 bases at a time; two ballots per 32 bases give
 //      the low and high bits of every base code, and a funnel shift puts the
 //      q bases starting at the lane's position side by side; a per-CTA
@@ -23,12 +22,14 @@
 //      set carries into plane p+1);
 //   3. every lane keeps its slice of the planes in registers (reads with up
 //      to two planes) or reads it from shared memory (more planes);
-//   4. candidate rows are fetched as 16-byte vectors, lanes_per_row lanes per
-//      row (4 lanes x 32 bytes for q=5: 8 rows per warp step, 32 rows in
-//      flight per warp), ANDed with the planes, popcounted and reduced with
-//      xor-shuffles, then compared with the threshold (steps 3-5);
-//   5. the results of a batch are gathered into lane order and stored as one
-//      coalesced run of pass bytes (and sums).
+//   4. candidate rows stream through the warp as 16-byte vectors,
+//      lanes_per_row lanes per row (4 lanes x 32 bytes for q=5: 8 rows per
+//      warp step); each row is requested three steps before it is scored,
+//      its id taken from a prefetched window of 32 candidate ids; rows are
+//      ANDed with the planes, popcounted, reduced with xor-shuffles and
+//      compared with the threshold (steps 3-5);
+//   5. the first lane of each row stores its pass byte (and sum); the eight
+//      rows of a step land in eight consecutive bytes.
 #include "grim_internal.cuh"
 #include "tokens.cuh"
 
@@ -44,13 +45,9 @@ struct GatherGeo {
     static constexpr int kVPL = kRowWords >= 32 ? 2 : 1;        // vectors per lane per row
     static constexpr int kLPB = kRowVecs / kVPL;               // lanes per row
     static constexpr int kBPS = 32 / kLPB;                     // rows per warp step
-    static constexpr int kStepsA = 32 / kBPS;
-    static constexpr int kStepsB = 8 / kVPL;
-    static constexpr int kSteps = kStepsA < kStepsB ? kStepsA : kStepsB;
-    static constexpr int kBatch = kSteps * kBPS;               // candidates per batch (<= 32)
     static constexpr int kTabWords = TokenTable<Q>::kWords;
     static constexpr int kPlaneWords = kPlanes * kRowWords;    // per warp
-    static_assert(kLPB >= 1 && kLPB <= 32 && kBatch <= 32, "bad gather geometry");
+    static_assert(kLPB >= 1 && kLPB <= 32 && 32 % kBPS == 0, "bad gather geometry");
 };
 
 template <int Q>
@@ -62,51 +59,65 @@ __device__ __forceinline__ uint32_t and_popc(const uint4& a, const uint4& b) {
     return __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
 }
 
-// One batch of candidate rows held in registers.
+// The candidate stream of one read.  Step k scores rows k*BPS .. k*BPS+BPS-1
+// (lane group g = lane / LPB takes row k*BPS + g).  Candidate ids arrive in
+// windows of 32 (one per lane, the next window prefetched); rows are
+// requested kAhead steps before they are scored, into kBufs rotating
+// register buffers.  A past-the-end or out-of-range id fetches row 0, which
+// is scored but never stored.
 template <int Q>
-struct Batch {
+struct Stream {
     using G = GatherGeo<Q>;
-    uint4 v[G::kSteps][G::kVPL];
-    uint32_t id;  // this lane's candidate id (lane < cnt)
-    int cnt;
+    static constexpr int kWinSteps = 32 / G::kBPS;       // steps per id window
+    static constexpr int kBufs = kWinSteps >= 4 ? 4 : kWinSteps;  // row buffers; divides kWinSteps
+    static constexpr int kAhead = kBufs - 1;                      // steps a row is requested early
+    static_assert(kWinSteps % kBufs == 0, "buffer rotation must repeat every window");
+    uint32_t win_cur, win_next;  // candidate ids c = base + lane, base + 32 + lane
+    uint4 r[kBufs][G::kVPL];
 };
 
-// Requests the rows of one batch: cnt candidates starting at the read's
-// candidate c0; `id` is this lane's candidate id (lane < cnt), already loaded.
+__device__ __forceinline__ uint32_t window_id(const uint32_t* __restrict__ cands, int c, int n) {
+    return c < n ? __ldg(cands + c) : 0xFFFFFFFFu;
+}
+
 template <int Q>
-__device__ __forceinline__ void load_rows(Batch<Q>& bt, uint32_t id, int cnt, const uint32_t* __restrict__ bank,
-                                          uint32_t n_bins32, int lane) {
+__device__ __forceinline__ void fetch_row(uint4 (&r)[GatherGeo<Q>::kVPL], uint32_t id,
+                                          const uint32_t* __restrict__ bank, uint32_t n_bins32, int s) {
     using G = GatherGeo<Q>;
-    bt.cnt = cnt;
-    bt.id = id;
-    const int s = lane % G::kLPB;
+    const uint32_t b = id < n_bins32 ? id : 0u;
+    const uint4* row = reinterpret_cast<const uint4*>(bank) + (size_t)b * G::kRowVecs + s;
 #pragma unroll
-    for (int t = 0; t < G::kSteps; t++) {
-        if (t * G::kBPS >= cnt) break;  // warp-uniform: the rest of the batch is empty
-        const int j = t * G::kBPS + lane / G::kLPB;
-        const uint32_t b = __shfl_sync(kFull, id, j & 31);
-        const bool ok = j < cnt && b < n_bins32;
-        const uint4* row = reinterpret_cast<const uint4*>(bank) + (size_t)b * G::kRowVecs + s;
+    for (int u = 0; u < G::kVPL; u++) r[u] = __ldg(row + u * G::kLPB);
+}
+
+// Before the token work: the first two id windows and the first kAhead steps' rows.
+template <int Q>
+__device__ __forceinline__ void stream_start(Stream<Q>& st, const uint32_t* __restrict__ cands, int n,
+                                             const uint32_t* __restrict__ bank, uint32_t n_bins32, int lane) {
+    using G = GatherGeo<Q>;
+    using S = Stream<Q>;
+    st.win_cur = window_id(cands, lane, n);
+    st.win_next = window_id(cands, 32 + lane, n);
+    const int s = lane % G::kLPB, g = lane / G::kLPB;
 #pragma unroll
-        for (int u = 0; u < G::kVPL; u++) bt.v[t][u] = ok ? __ldg(row + u * G::kLPB) : make_uint4(0, 0, 0, 0);
+    for (int k = 0; k < S::kAhead; k++) {
+        const int idx = k * G::kBPS + g;  // < 64: within the two windows
+        const uint32_t id = __shfl_sync(kFull, idx < 32 ? st.win_cur : st.win_next, idx & 31);
+        fetch_row<Q>(st.r[k], id, bank, n_bins32, s);
     }
 }
 
-// This lane's candidate id of the batch starting at c (n candidates in all).
-__device__ __forceinline__ uint32_t batch_id(const uint32_t* __restrict__ cands, int c, int n, int batch, int lane) {
-    return (lane < batch && c + lane < n) ? __ldg(cands + c + lane) : 0u;
-}
-
-// Score every batch of one read; the first batch is already in bt.
-// NP > 0: NP planes held in registers; NP == 0: P planes read from shared
-// memory.  cands / pass / sums point at the read's first candidate.
+// Score the read's candidates.  NP > 0: NP planes held in registers;
+// NP == 0: P planes read from shared memory.  cands / pass / sums point at
+// the read's first candidate.
 template <int Q, int NP>
-__device__ __forceinline__ void score_read(Batch<Q>& bt, const uint4* __restrict__ planes, int P, int T, int n,
+__device__ __forceinline__ void score_read(Stream<Q>& st, const uint4* __restrict__ planes, int P, int T, int n,
                                            const uint32_t* __restrict__ cands, const uint32_t* __restrict__ bank,
                                            uint32_t n_bins32, uint8_t* __restrict__ pass,
                                            uint16_t* __restrict__ sums, int lane, uint32_t& flags) {
     using G = GatherGeo<Q>;
-    const int s = lane % G::kLPB;
+    using S = Stream<Q>;
+    const int s = lane % G::kLPB, g = lane / G::kLPB;
     uint4 pl[NP > 0 ? NP : 1][G::kVPL];
     if (NP > 0) {
 #pragma unroll
@@ -114,20 +125,29 @@ __device__ __forceinline__ void score_read(Batch<Q>& bt, const uint4* __restrict
 #pragma unroll
             for (int u = 0; u < G::kVPL; u++) pl[p][u] = planes[p * G::kRowVecs + s + u * G::kLPB];
     }
-    for (int c = 0; c < n; c += G::kBatch) {
-        // the next batch's ids travel while this batch is scored
-        const uint32_t next_id = batch_id(cands, c + G::kBatch, n, G::kBatch, lane);
-        uint32_t mine = 0;
+    for (int w0 = 0; w0 < n; w0 += 32) {
+        const uint32_t win_after = window_id(cands, w0 + 64 + lane, n);  // two windows ahead
 #pragma unroll
-        for (int t = 0; t < G::kSteps; t++) {
-            if (t * G::kBPS >= bt.cnt) break;  // warp-uniform
+        for (int t = 0; t < S::kWinSteps; t++) {
+            const int c0 = w0 + t * G::kBPS;
+            if (c0 >= n) break;  // warp-uniform
+            // request the rows kAhead steps ahead (window position t + kAhead)
+            {
+                const int ahead = t + S::kAhead;
+                const int idx = (ahead % S::kWinSteps) * G::kBPS + g;
+                const uint32_t src = ahead < S::kWinSteps ? st.win_cur : st.win_next;
+                const uint32_t id = __shfl_sync(kFull, src, idx);
+                fetch_row<Q>(st.r[(t + S::kAhead) % S::kBufs], id, bank, n_bins32, s);
+            }
+            // score this step's rows
+            const uint4 (&v)[G::kVPL] = st.r[t % S::kBufs];
             uint32_t part = 0;
             if (NP > 0) {
 #pragma unroll
                 for (int p = 0; p < (NP > 0 ? NP : 1); p++) {
                     uint32_t q = 0;
 #pragma unroll
-                    for (int u = 0; u < G::kVPL; u++) q += and_popc(bt.v[t][u], pl[p][u]);
+                    for (int u = 0; u < G::kVPL; u++) q += and_popc(v[u], pl[p][u]);
                     part += q << p;
                 }
             } else {
@@ -135,24 +155,24 @@ __device__ __forceinline__ void score_read(Batch<Q>& bt, const uint4* __restrict
                     uint32_t q = 0;
 #pragma unroll
                     for (int u = 0; u < G::kVPL; u++)
-                        q += and_popc(bt.v[t][u], planes[p * G::kRowVecs + s + u * G::kLPB]);
+                        q += and_popc(v[u], planes[p * G::kRowVecs + s + u * G::kLPB]);
                     part += q << p;
                 }
             }
 #pragma unroll
             for (int o = G::kLPB / 2; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-            const uint32_t got = __shfl_sync(kFull, part, (lane % G::kBPS) * G::kLPB);
-            if (lane / G::kBPS == t) mine = got;
+            const int c = c0 + g;
+            const uint32_t id = __shfl_sync(kFull, st.win_cur, (t * G::kBPS + g) & 31);
+            if (s == 0 && c < n) {
+                const bool in_range = id < n_bins32;
+                if (!in_range) flags |= GRIM_FLAG_BAD_BIN;
+                const uint32_t sum = in_range ? part : 0u;
+                pass[c] = (in_range && (int)sum >= T) ? 1 : 0;
+                if (sums) sums[c] = (uint16_t)sum;
+            }
         }
-        if (lane < bt.cnt) {
-            const bool in_range = bt.id < n_bins32;
-            if (!in_range) flags |= GRIM_FLAG_BAD_BIN;
-            const uint32_t sum = in_range ? mine : 0u;
-            pass[c + lane] = (in_range && (int)sum >= T) ? 1 : 0;
-            if (sums) sums[c + lane] = (uint16_t)sum;
-        }
-        const int rest = n - (c + G::kBatch);
-        if (rest > 0) load_rows<Q>(bt, next_id, rest < G::kBatch ? rest : G::kBatch, bank, n_bins32, lane);
+        st.win_cur = st.win_next;
+        st.win_next = win_after;
     }
 }
 
@@ -199,15 +219,12 @@ __device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restric
         flags |= GRIM_FLAG_BAD_OFFSETS;
         return;
     }
-    // 0. first candidate batch in flight while the tokens are built
+    // 0. the first candidate rows in flight while the tokens are built
     const uint32_t n_bins32 = (uint32_t)n_bins;  // n_bins < 2^32 (checked when the bank is built)
     const int n_c = (int)(ce - co);
     const uint32_t* cands = cand_bins + co;
-    Batch<Q> bt;
-    if (n_c > 0) {
-        const int cnt = n_c < GatherGeo<Q>::kBatch ? n_c : GatherGeo<Q>::kBatch;
-        load_rows<Q>(bt, batch_id(cands, 0, n_c, GatherGeo<Q>::kBatch, lane), cnt, bank, n_bins32, lane);
-    }
+    Stream<Q> st;
+    if (n_c > 0) stream_start<Q>(st, cands, n_c, bank, n_bins32, lane);
 
     bool bad_read = false;
     int L = 0;
@@ -249,13 +266,13 @@ __device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restric
         if (bad_read || used == 0)
             write_constant(co, ce, cand_bins, n_bins, !bad_read && T <= 0, pass, sums, lane, flags);
         else if (used == 1)
-            score_read<Q, 1>(bt, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+            score_read<Q, 1>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
                              lane, flags);
         else if (used == 2)
-            score_read<Q, 2>(bt, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+            score_read<Q, 2>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
                              lane, flags);
         else
-            score_read<Q, 0>(bt, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+            score_read<Q, 0>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
                              lane, flags);
     }
 
