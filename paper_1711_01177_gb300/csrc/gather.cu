@@ -282,7 +282,49 @@ __device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restric
     __syncwarp();
 }
 
-// Plain gather: warps walk the reads grid-stride.
+// Modelled cost of the reads before r: 8 per candidate, 1 per base, 64 per
+// read.  Strictly increasing in r for valid offsets, so equal cost shares
+// are contiguous, disjoint read ranges that cover every read.
+__device__ __forceinline__ int64_t cost_before(const int64_t* __restrict__ read_offsets,
+                                               const int64_t* __restrict__ cand_offsets, int64_t r) {
+    return 8 * (__ldg(cand_offsets + r) - __ldg(cand_offsets)) + (__ldg(read_offsets + r) - __ldg(read_offsets)) +
+           64 * r;
+}
+
+// Smallest r in [0, n] with cost_before(r) >= target, found by a half-warp
+// 16-ary search: lanes 0-15 search target0, lanes 16-31 target1.  Every
+// lane returns its own half's answer.
+__device__ int64_t split_search(const int64_t* __restrict__ read_offsets, const int64_t* __restrict__ cand_offsets,
+                                int64_t n, int64_t target0, int64_t target1, int lane) {
+    const int j = lane & 15;
+    const int64_t target = lane < 16 ? target0 : target1;
+    int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+    while (__any_sync(kFull, hi - lo > 16)) {
+        const int64_t p = lo + (hi - lo) * (j + 1) / 17;  // sorted samples inside [lo, hi)
+        const unsigned below = __ballot_sync(kFull, cost_before(read_offsets, cand_offsets, p) < target);
+        const unsigned half = lane < 16 ? below & 0xFFFFu : below >> 16;
+        const int k = __popc(half);  // the samples below target are a prefix
+        const int64_t p_last = __shfl_sync(kFull, p, (lane & 16) + (k > 0 ? k - 1 : 0));
+        const int64_t p_next = __shfl_sync(kFull, p, (lane & 16) + (k < 16 ? k : 15));
+        if (k > 0) lo = p_last + 1;
+        if (k < 16) hi = p_next;
+        if (lo > hi) lo = hi;  // only with a non-monotone cost (invalid offsets)
+    }
+    const int64_t p = lo + j;
+    const bool below = p < hi && cost_before(read_offsets, cand_offsets, p) < target;
+    const unsigned b = __ballot_sync(kFull, below);
+    return lo + __popc(lane < 16 ? b & 0xFFFFu : b >> 16);
+}
+
+// floor(total * i / n) without overflow, for 0 <= i <= n.
+__device__ __forceinline__ int64_t cost_share(int64_t total, int64_t i, int64_t n) {
+    return total / n * i + total % n * i / n;
+}
+
+// Plain gather: one launch of one wave.  Each CTA owns the contiguous read
+// range of an equal share of the modelled cost, and its warps claim reads
+// one at a time from a shared-memory counter, so uneven candidate lists and
+// read lengths balance without any global work counter.
 template <int Q>
 __global__ void __launch_bounds__(kGatherWarps * 32, 3)
 gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* __restrict__ reads,
@@ -291,17 +333,39 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
               uint8_t* __restrict__ pass, uint16_t* __restrict__ sums, uint32_t* __restrict__ status) {
     using G = GatherGeo<Q>;
     extern __shared__ uint4 gather_smem[];
-    gather_cta_setup<Q>(gather_smem, kGatherWarps);
-    const uint16_t* tab = reinterpret_cast<const uint16_t*>(gather_smem);
+    __shared__ unsigned long long next_read;
+    __shared__ long long end_read;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    if (warp == 0) {
+        const int64_t n_ctas = gridDim.x, b = blockIdx.x;
+        const int64_t total = cost_before(read_offsets, cand_offsets, n_reads);
+        const int64_t split = split_search(read_offsets, cand_offsets, n_reads, cost_share(total, b, n_ctas),
+                                           cost_share(total, b + 1, n_ctas), lane);
+        const int64_t r_begin = __shfl_sync(kFull, split, 0);
+        const int64_t r_end = __shfl_sync(kFull, split, 16);
+        // The ends are pinned so that every read lies in some CTA's range even
+        // when decreasing (invalid) offsets break the monotone cost; such
+        // reads are then flagged by whichever warp visits them.
+        if (lane == 0) {
+            next_read = b == 0 ? 0 : (unsigned long long)r_begin;
+            end_read = b == n_ctas - 1 ? n_reads : r_end;
+        }
+    }
+    gather_cta_setup<Q>(gather_smem, kGatherWarps);  // ends with a CTA barrier
+    const uint16_t* tab = reinterpret_cast<const uint16_t*>(gather_smem);
     uint32_t* planes = reinterpret_cast<uint32_t*>(gather_smem) + G::kTabWords + warp * G::kPlaneWords;
+    const int64_t r_end = end_read;
 
     uint32_t flags = 0;
-    const int64_t warp_stride = (int64_t)gridDim.x * kGatherWarps;
-    for (int64_t r = (int64_t)blockIdx.x * kGatherWarps + warp; r < n_reads; r += warp_stride)
-        gather_read<Q>(r, bank, n_bins, reads, read_offsets, cand_bins, cand_offsets, E, pass, sums, tab, planes,
-                       lane, flags);
+    while (true) {
+        unsigned long long r = 0;
+        if (lane == 0) r = atomicAdd(&next_read, 1ull);
+        r = __shfl_sync(kFull, r, 0);
+        if ((int64_t)r >= r_end) break;
+        gather_read<Q>((int64_t)r, bank, n_bins, reads, read_offsets, cand_bins, cand_offsets, E, pass, sums, tab,
+                       planes, lane, flags);
+    }
     flags = __reduce_or_sync(kFull, flags);
     if (lane == 0 && flags) atomicOr(status, flags);
 }
@@ -354,9 +418,9 @@ static int launch_q(const grim_bank* bank, const uint8_t* reads, const int64_t* 
         GRIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gather_kernel<Q>, kGatherWarps * 32, smem));
         blocks_per_sm = b > 0 ? b : 1;
     }
-    const int64_t need = (n_reads + kGatherWarps - 1) / kGatherWarps;
-    const int64_t cap = (int64_t)sm_count() * blocks_per_sm * 8;
-    const int64_t blocks = need < cap ? need : cap;
+    const int64_t need = (n_reads + kGatherWarps - 1) / kGatherWarps;  // at least a read per warp
+    const int64_t wave = (int64_t)sm_count() * blocks_per_sm;
+    const int64_t blocks = need < wave ? need : wave;
     gather_kernel<Q><<<(unsigned)blocks, kGatherWarps * 32, smem, s>>>(bank->bits, bank->n_bins, reads, read_offsets,
                                                                        n_reads, cand_bins, cand_offsets, E, pass,
                                                                        sums, bank->status);

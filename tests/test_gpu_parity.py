@@ -180,6 +180,34 @@ def test_filter_bad_data_is_flagged_not_faulted(oracle):
     bank.free()
 
 
+@pytest.mark.parametrize("entry", ["grim_filter", "grim_filter_batched"])
+def test_decreasing_offsets_spare_every_other_read(oracle, entry):
+    """Decreasing read and candidate offsets in a 20,000-read launch: both
+    reads are flagged and every read whose own offsets are intact, on any warp
+    of the launch, still gets the oracle's bytes."""
+    w = synth.gather_iid(ref_len=400_000, n_reads=20_000, k=16)
+    bank = gpu_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
+    ob = oracle.build_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
+    op, os_ = oracle.filter(ob, w.q, w.bases, w.read_offsets, w.cand_bins, w.cand_offsets, w.E)
+    offs = w.read_offsets.copy()
+    offs[5000] = offs[5001] + 2000  # read 4999 grows into later bases, read 5000 decreases
+    co = w.cand_offsets.copy()
+    co[1000] = co[1001] + 40  # read 999 spills over reads 1000-1003's slots, read 1000 decreases
+    spoiled = np.zeros(len(w.cand_bins), bool)
+    spoiled[w.cand_offsets[999]:w.cand_offsets[1004]] = True
+    spoiled[w.cand_offsets[4999]:w.cand_offsets[5001]] = True
+    pass_out = torch.full((len(w.cand_bins),), 0xAA, dtype=torch.uint8, device="cuda")
+    sums = torch.full((len(w.cand_bins),), 0x5A5A, dtype=torch.int16, device="cuda")
+    getattr(grim, entry)(bank, dev(w.bases), dev(offs), dev(w.cand_bins), dev(co), dev(w.E), pass_out=pass_out,
+                         sums=sums)
+    st, flags = grim.grim_bank_status(bank)
+    assert st == grim.GRIM_EDATA and flags == grim.GRIM_FLAG_BAD_OFFSETS
+    p, s = host(pass_out, np.uint8), host(sums, np.uint16)
+    assert np.array_equal(p[~spoiled], op[~spoiled])
+    assert np.array_equal(s[~spoiled], os_[~spoiled].astype(np.uint16))
+    bank.free()
+
+
 def test_host_errors():
     r2 = dev(synth.pack2bit(synth.ref_iid(1000, 1)))
     with pytest.raises(grim.GrimError) as e:
