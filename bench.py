@@ -10,7 +10,7 @@ Three forms of the hot path, each on its synthetic workload:
   batched: 100 Mbp repeat-rich reference, q=6, 256 + 300 bp; 2M reads of
            50-300 bp (3% + 1%), E = floor(0.05 L); true bin + log-uniform
            1-5,000 candidates.  One step = one grim_filter_batched (one
-           persistent launch per 262,144 reads, replayed CUDA graph,
+           cost-balanced launch per 262,144 reads, replayed CUDA graph,
            autotuned launch shape).
   fullscan: 3.1 Gbp repeat-rich reference, q=5, 256 + 100 bp (12.1M bins);
            a batch of 65,536 reads of 100 bp, E=5, every bin scored on the
@@ -45,8 +45,8 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch, from
 # an ncu capture, valid only for the kernel source it was taken on.
 TRAFFIC_BY_SOURCE: dict[str, dict] = {
-    # gather, 1M reads, 74.8M checks: 670.37 MB read + 77.11 MB written
-    "b975ee0a825bbbdd": {"bytes": 747_480_000},
+    # gather_kernel<5,8>, 1M reads, 74.8M checks: 636.08 MB read + 74.59 MB written
+    "0f3c17eb9b000ee9": {"bytes": 710_667_776, "reads": 1_000_000},
 }
 
 
@@ -342,7 +342,7 @@ def run_form(form, args, ctx, primary):
         g, sc = float(np.mean(ms_g)), float(np.mean(ms_s))
         roof = {"bound": "hbm", "achieved": alg / (avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                 "frac": alg / (avg / 1e3) / 1e9 / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
-                "kernel": "dispatcher -> gather_persistent_kernel<5>", "avg_step_ms": avg}
+                "kernel": "dispatcher -> gather_kernel<5,8>", "avg_step_ms": avg}
         out["dispatch"] = {"choice": "scan" if choice == grim.GRIM_FORM_SCAN else "gather",
                            "reads_scanned_per_step": scanned[-1] if scanned else 0}
         out["gather_form"] = {"ms_per_step": g, "checks_per_s": units / (g / 1e3), "reads_per_s": w.n_reads / (g / 1e3)}
@@ -377,11 +377,11 @@ def run_form(form, args, ctx, primary):
             s.synchronize()
             call = lambda: grim.grim_filter_batched(bank, *ins, pass_out=pass_d, tune=tune, stream=s)
             launches = -(-w.n_reads // int(tune.batch_reads))
-            kernel = f"gather_persistent_kernel<{w.q}>"
+            kernel = f"gather_kernel<{w.q},{int(tune.warps_per_cta)}>"
         else:
             call = lambda: grim.grim_filter(bank, *ins, pass_out=pass_d, stream=s)
             launches = 1
-            kernel = f"gather_kernel<{w.q}>"
+            kernel = f"gather_kernel<{w.q},8>"
         ms, clk = ctx.timed(call, steps, warmup, clocks=primary)
         units = w.n_checks
         alg = gather_bytes(w, row)
@@ -394,7 +394,8 @@ def run_form(form, args, ctx, primary):
         if form == "gather":
             sha = source_sha()
             roof["source_sha"] = sha
-            roof["traffic"] = TRAFFIC_BY_SOURCE.get(sha, {}).get("bytes")
+            rec = TRAFFIC_BY_SOURCE.get(sha, {})
+            roof["traffic"] = rec.get("bytes") if rec.get("reads") == w.n_reads else None
             if w.q == 5:
                 roof["note"] = ("the 50 MB bank stays in the 129 MB L2, so algorithmic bytes exceed DRAM "
                                 "traffic; frac counts algorithmic bytes")

@@ -118,7 +118,10 @@ int grim_bank_free(grim_bank* bank);
  *                 one byte per location).
  *   sums          device u16 output aligned with cand_bins, or NULL.
  * Duplicate candidates are checked independently; a read shorter than q
- * has sum 0 and passes iff its threshold is <= 0.
+ * has sum 0 and passes iff its threshold is <= 0.  One launch, in which
+ * each CTA works through the reads holding an equal share of the work; it
+ * keeps no device state besides the bank's status word, so calls that
+ * overlap on the GPU (other streams) are independent.
  */
 int grim_filter(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                 const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
@@ -132,21 +135,22 @@ typedef struct grim_tune {
     int32_t reads_per_claim; /* reads a warp claims from the work counter at a time (default 1) */
     int32_t ctas_per_sm;     /* resident CTAs per SM, up to the occupancy limit (default: the limit) */
     int32_t use_graph;       /* 1: capture the launches in a CUDA graph, replayed by identical calls */
-    int64_t batch_reads;     /* reads per persistent launch (default 262,144) */
+    int64_t batch_reads;     /* reads per launch (default 262,144) */
 } grim_tune;
 
 /*
  * Batched gather filter: the same outputs as grim_filter, computed by one
- * persistent launch per batch of `batch_reads` reads in which every warp
- * claims reads from a device work counter, so reads of uneven length and
- * uneven candidate lists balance across the GPU.  With use_graph, the
- * call's launches are captured once into a CUDA graph and an identical
- * later call (same pointers, sizes, tune and stream) replays it; a stream
- * that is already capturing simply records the launches.  tune == NULL
- * uses the last grim_autotune result for this bank's q on this device,
- * else the defaults with use_graph = 1.  The work counters live in the
- * bank: batched calls on one bank that overlap on the GPU without a graph
- * of their own must be serialised.
+ * launch per batch of `batch_reads` reads in which every warp claims reads
+ * from a device work counter, so reads of uneven length and uneven
+ * candidate lists balance across the GPU.  With use_graph, the call's
+ * launches are captured once into a CUDA graph and an identical later call
+ * (same pointers, sizes, tune and stream) replays it; a stream that is
+ * already capturing simply records the launches.  tune == NULL uses the
+ * last grim_autotune result for this bank's q on this device, else the
+ * defaults with use_graph = 1.  The graph cache is host state of the bank:
+ * calls on one bank from several host threads must be serialised.  The
+ * work counters live in the bank: batched calls on one bank that overlap
+ * on the GPU without a graph of their own must be serialised.
  */
 int grim_filter_batched(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                         const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,

@@ -1,4 +1,4 @@
-// Batched gather filter (persistent launches under a CUDA graph) and its
+// Batched gather filter (one launch per batch, under a CUDA graph) and its
 // autotuner.  The kernels are in gather.cu; this file decides launch
 // shapes, captures and caches graphs, and times candidate shapes.
 #include <mutex>
@@ -71,7 +71,7 @@ int grim_filter_batched(const grim_bank* bank, const uint8_t* reads, const int64
     const bool real_stream = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
     if (real_stream) GRIM_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
     if (!t.use_graph || !real_stream || cs != cudaStreamCaptureStatusNone)
-        return grim::launch_gather_persistent(bank, a, t, &mb->counters[0], s);
+        return grim::launch_gather_batches(bank, a, t, &mb->counters[0], s);
 
     const void* key[8] = {reads, read_offsets, cand_bins, cand_offsets, E, pass, sums, nullptr};
     std::vector<grim::GraphEntry>& cache = *mb->graphs;
@@ -94,7 +94,7 @@ int grim_filter_batched(const grim_bank* bank, const uint8_t* reads, const int64
         slot = cache[victim].slot;
     }
     GRIM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    rc = grim::launch_gather_persistent(bank, a, t, &mb->counters[slot], s);
+    rc = grim::launch_gather_batches(bank, a, t, &mb->counters[slot], s);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &graph);
     if (rc != GRIM_OK) {
@@ -160,12 +160,12 @@ int grim_autotune(const grim_bank* bank, const uint8_t* reads, const int64_t* re
                 t.reads_per_claim = c;
                 t.ctas_per_sm = p;
                 t.use_graph = 0;
-                rc = grim::launch_gather_persistent(bank, a, t, &mb->counters[0], s);  // warm-up
+                rc = grim::launch_gather_batches(bank, a, t, &mb->counters[0], s);  // warm-up
                 if (rc != GRIM_OK) break;
                 float ms = 1e30f;
                 for (int rep = 0; rep < 3 && rc == GRIM_OK; rep++) {
                     cudaEventRecord(e0, s);
-                    rc = grim::launch_gather_persistent(bank, a, t, &mb->counters[0], s);
+                    rc = grim::launch_gather_batches(bank, a, t, &mb->counters[0], s);
                     cudaEventRecord(e1, s);
                     if (cudaEventSynchronize(e1) != cudaSuccess) rc = GRIM_ECUDA;
                     float x = 0;

@@ -321,23 +321,29 @@ __device__ __forceinline__ int64_t cost_share(int64_t total, int64_t i, int64_t 
     return total / n * i + total % n * i / n;
 }
 
-// Plain gather: one launch of one wave.  Each CTA owns the contiguous read
-// range of an equal share of the modelled cost, and its warps claim reads
-// one at a time from a shared-memory counter, so uneven candidate lists and
-// read lengths balance without any global work counter.
-template <int Q>
-__global__ void __launch_bounds__(kGatherWarps * 32, 3)
+// The gather launch: one wave of CTAs of WARPS warps whose warps claim
+// `claim` reads at a time, in one of two ways.
+//  - counter == nullptr: each CTA owns the contiguous read range of an equal
+//    share of the modelled cost and claims from a shared-memory counter.  No
+//    device state, so concurrent launches on different streams stay
+//    independent (the one-launch filter).
+//  - counter != nullptr: every warp claims from that zeroed device counter,
+//    which also absorbs speed differences between SMs; the batched filter
+//    resets it before each launch of its graph.
+template <int Q, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 24 / WARPS)
 gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* __restrict__ reads,
               const int64_t* __restrict__ read_offsets, int64_t n_reads, const uint32_t* __restrict__ cand_bins,
               const int64_t* __restrict__ cand_offsets, const uint16_t* __restrict__ E,
-              uint8_t* __restrict__ pass, uint16_t* __restrict__ sums, uint32_t* __restrict__ status) {
+              uint8_t* __restrict__ pass, uint16_t* __restrict__ sums, uint32_t* __restrict__ status, int claim,
+              unsigned long long* __restrict__ counter) {
     using G = GatherGeo<Q>;
     extern __shared__ uint4 gather_smem[];
     __shared__ unsigned long long next_read;
     __shared__ long long end_read;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp == 0) {
+    if (counter == nullptr && warp == 0) {
         const int64_t n_ctas = gridDim.x, b = blockIdx.x;
         const int64_t total = cost_before(read_offsets, cand_offsets, n_reads);
         const int64_t split = split_search(read_offsets, cand_offsets, n_reads, cost_share(total, b, n_ctas),
@@ -352,51 +358,20 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
             end_read = b == n_ctas - 1 ? n_reads : r_end;
         }
     }
-    gather_cta_setup<Q>(gather_smem, kGatherWarps);  // ends with a CTA barrier
+    gather_cta_setup<Q>(gather_smem, WARPS);  // ends with a CTA barrier
     const uint16_t* tab = reinterpret_cast<const uint16_t*>(gather_smem);
     uint32_t* planes = reinterpret_cast<uint32_t*>(gather_smem) + G::kTabWords + warp * G::kPlaneWords;
-    const int64_t r_end = end_read;
+    const int64_t r_end = counter ? n_reads : end_read;
+    unsigned long long* next = counter ? counter : &next_read;
 
     uint32_t flags = 0;
     while (true) {
-        unsigned long long r = 0;
-        if (lane == 0) r = atomicAdd(&next_read, 1ull);
-        r = __shfl_sync(kFull, r, 0);
-        if ((int64_t)r >= r_end) break;
-        gather_read<Q>((int64_t)r, bank, n_bins, reads, read_offsets, cand_bins, cand_offsets, E, pass, sums, tab,
-                       planes, lane, flags);
-    }
-    flags = __reduce_or_sync(kFull, flags);
-    if (lane == 0 && flags) atomicOr(status, flags);
-}
-
-// Persistent gather: a grid sized to fill the GPU once; every warp claims
-// `claim` consecutive reads at a time from a device counter until the batch
-// is exhausted, so uneven read lengths and candidate lists balance across
-// the GPU.  No warp ever waits for another.
-template <int Q, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 24 / WARPS)
-gather_persistent_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* __restrict__ reads,
-                         const int64_t* __restrict__ read_offsets, int64_t n_reads,
-                         const uint32_t* __restrict__ cand_bins, const int64_t* __restrict__ cand_offsets,
-                         const uint16_t* __restrict__ E, uint8_t* __restrict__ pass, uint16_t* __restrict__ sums,
-                         uint32_t* __restrict__ status, unsigned long long* __restrict__ counter, int claim) {
-    using G = GatherGeo<Q>;
-    extern __shared__ uint4 gather_smem[];
-    gather_cta_setup<Q>(gather_smem, WARPS);
-    const uint16_t* tab = reinterpret_cast<const uint16_t*>(gather_smem);
-    const int warp = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    uint32_t* planes = reinterpret_cast<uint32_t*>(gather_smem) + G::kTabWords + warp * G::kPlaneWords;
-
-    uint32_t flags = 0;
-    while (true) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(counter, (unsigned long long)claim);
-        base = __shfl_sync(kFull, base, 0);
-        if ((int64_t)base >= n_reads) break;
-        const int64_t end = (int64_t)base + claim < n_reads ? (int64_t)base + claim : n_reads;
-        for (int64_t r = (int64_t)base; r < end; r++)
+        unsigned long long r0 = 0;
+        if (lane == 0) r0 = atomicAdd(next, (unsigned long long)claim);
+        r0 = __shfl_sync(kFull, r0, 0);
+        if ((int64_t)r0 >= r_end) break;
+        const int64_t r1 = (int64_t)r0 + claim < r_end ? (int64_t)r0 + claim : r_end;
+        for (int64_t r = (int64_t)r0; r < r1; r++)
             gather_read<Q>(r, bank, n_bins, reads, read_offsets, cand_bins, cand_offsets, E, pass, sums, tab, planes,
                            lane, flags);
     }
@@ -404,77 +379,57 @@ gather_persistent_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, cons
     if (lane == 0 && flags) atomicOr(status, flags);
 }
 
-template <int Q>
-static int launch_q(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
-                    const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
-                    uint16_t* sums, cudaStream_t s) {
-    constexpr size_t smem = gather_smem_bytes<Q>();
-    static int blocks_per_sm = 0;
-    if (blocks_per_sm == 0) {
-        if (smem > 48 * 1024)
-            GRIM_CUDA_TRY(cudaFuncSetAttribute(gather_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem));
-        int b = 0;
-        GRIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gather_kernel<Q>, kGatherWarps * 32, smem));
-        blocks_per_sm = b > 0 ? b : 1;
-    }
-    const int64_t need = (n_reads + kGatherWarps - 1) / kGatherWarps;  // at least a read per warp
-    const int64_t wave = (int64_t)sm_count() * blocks_per_sm;
-    const int64_t blocks = need < wave ? need : wave;
-    gather_kernel<Q><<<(unsigned)blocks, kGatherWarps * 32, smem, s>>>(bank->bits, bank->n_bins, reads, read_offsets,
-                                                                       n_reads, cand_bins, cand_offsets, E, pass,
-                                                                       sums, bank->status);
-    GRIM_CUDA_TRY(cudaGetLastError());
-    return GRIM_OK;
-}
-
+// One launch over reads [r0, r0 + n) with `per_sm` CTAs per SM (0 = as many
+// as fit).
 template <int Q, int WARPS>
-static int launch_persistent_qw(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
-                                unsigned long long* counter, cudaStream_t s) {
+static int launch_range(const grim_bank* bank, const GatherArgs& a, int64_t r0, int64_t n, int per_sm, int claim,
+                        unsigned long long* counter, cudaStream_t s) {
     constexpr size_t smem = gather_smem_bytes<Q>(WARPS);
     static int max_blocks = 0;
     if (max_blocks == 0) {
         if (smem > 48 * 1024)
-            GRIM_CUDA_TRY(cudaFuncSetAttribute(gather_persistent_kernel<Q, WARPS>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            GRIM_CUDA_TRY(
+                cudaFuncSetAttribute(gather_kernel<Q, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int b = 0;
-        GRIM_CUDA_TRY(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gather_persistent_kernel<Q, WARPS>, WARPS * 32, smem));
+        GRIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gather_kernel<Q, WARPS>, WARPS * 32, smem));
         max_blocks = b > 0 ? b : 1;
     }
-    const int per_sm = (t.ctas_per_sm > 0 && t.ctas_per_sm < max_blocks) ? t.ctas_per_sm : max_blocks;
-    const int claim = t.reads_per_claim > 0 ? t.reads_per_claim : 1;
-    const int64_t batch = t.batch_reads > 0 ? t.batch_reads : (int64_t)262144;
-    for (int64_t r0 = 0; r0 < a.n_reads; r0 += batch) {
-        const int64_t n = (a.n_reads - r0) < batch ? (a.n_reads - r0) : batch;
-        int64_t blocks = (int64_t)sm_count() * per_sm;
-        const int64_t need = (n + (int64_t)WARPS * claim - 1) / ((int64_t)WARPS * claim);
-        if (need < blocks) blocks = need;
-        GRIM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
-        gather_persistent_kernel<Q, WARPS><<<(unsigned)blocks, WARPS * 32, smem, s>>>(
-            bank->bits, bank->n_bins, a.reads, a.read_offsets + r0, n, a.cand_bins, a.cand_offsets + r0, a.E + r0,
-            a.pass, a.sums, bank->status, counter, claim);
-        GRIM_CUDA_TRY(cudaGetLastError());
-    }
+    if (per_sm <= 0 || per_sm > max_blocks) per_sm = max_blocks;
+    if (claim <= 0) claim = 1;
+    int64_t blocks = (int64_t)sm_count() * per_sm;
+    const int64_t need = (n + (int64_t)WARPS * claim - 1) / ((int64_t)WARPS * claim);  // a claim per warp at least
+    if (need < blocks) blocks = need;
+    if (counter) GRIM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    gather_kernel<Q, WARPS><<<(unsigned)blocks, WARPS * 32, smem, s>>>(
+        bank->bits, bank->n_bins, a.reads, a.read_offsets + r0, n, a.cand_bins, a.cand_offsets + r0, a.E + r0,
+        a.pass, a.sums, bank->status, claim, counter);
+    GRIM_CUDA_TRY(cudaGetLastError());
     return GRIM_OK;
 }
 
 template <int Q>
-static int launch_persistent_q(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
-                               unsigned long long* counter, cudaStream_t s) {
-    if (t.warps_per_cta == 4) return launch_persistent_qw<Q, 4>(bank, a, t, counter, s);
-    return launch_persistent_qw<Q, 8>(bank, a, t, counter, s);
+static int launch_batches(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
+                          unsigned long long* counter, cudaStream_t s) {
+    const int64_t batch = t.batch_reads > 0 ? t.batch_reads : a.n_reads;
+    for (int64_t r0 = 0; r0 < a.n_reads; r0 += batch) {
+        const int64_t n = (a.n_reads - r0) < batch ? (a.n_reads - r0) : batch;
+        const int rc = t.warps_per_cta == 4
+                           ? launch_range<Q, 4>(bank, a, r0, n, t.ctas_per_sm, t.reads_per_claim, counter, s)
+                           : launch_range<Q, 8>(bank, a, r0, n, t.ctas_per_sm, t.reads_per_claim, counter, s);
+        if (rc != GRIM_OK) return rc;
+    }
+    return GRIM_OK;
 }
 
-int launch_gather_persistent(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
-                             unsigned long long* counter, cudaStream_t s) {
+int launch_gather_batches(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
+                          unsigned long long* counter, cudaStream_t s) {
     switch (bank->q) {
-        case 1: return launch_persistent_q<1>(bank, a, t, counter, s);
-        case 2: return launch_persistent_q<2>(bank, a, t, counter, s);
-        case 3: return launch_persistent_q<3>(bank, a, t, counter, s);
-        case 4: return launch_persistent_q<4>(bank, a, t, counter, s);
-        case 5: return launch_persistent_q<5>(bank, a, t, counter, s);
-        case 6: return launch_persistent_q<6>(bank, a, t, counter, s);
+        case 1: return launch_batches<1>(bank, a, t, counter, s);
+        case 2: return launch_batches<2>(bank, a, t, counter, s);
+        case 3: return launch_batches<3>(bank, a, t, counter, s);
+        case 4: return launch_batches<4>(bank, a, t, counter, s);
+        case 5: return launch_batches<5>(bank, a, t, counter, s);
+        case 6: return launch_batches<6>(bank, a, t, counter, s);
         default: return GRIM_ENOTSUP;
     }
 }
@@ -482,15 +437,9 @@ int launch_gather_persistent(const grim_bank* bank, const GatherArgs& a, const g
 int launch_gather(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                   const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
                   uint16_t* sums, cudaStream_t s) {
-    switch (bank->q) {
-        case 1: return launch_q<1>(bank, reads, read_offsets, n_reads, cand_bins, cand_offsets, E, pass, sums, s);
-        case 2: return launch_q<2>(bank, reads, read_offsets, n_reads, cand_bins, cand_offsets, E, pass, sums, s);
-        case 3: return launch_q<3>(bank, reads, read_offsets, n_reads, cand_bins, cand_offsets, E, pass, sums, s);
-        case 4: return launch_q<4>(bank, reads, read_offsets, n_reads, cand_bins, cand_offsets, E, pass, sums, s);
-        case 5: return launch_q<5>(bank, reads, read_offsets, n_reads, cand_bins, cand_offsets, E, pass, sums, s);
-        case 6: return launch_q<6>(bank, reads, read_offsets, n_reads, cand_bins, cand_offsets, E, pass, sums, s);
-        default: return GRIM_ENOTSUP;
-    }
+    const GatherArgs a{reads, read_offsets, n_reads, cand_bins, cand_offsets, E, pass, sums};
+    const grim_tune t = {kGatherWarps, 1, 0, 0, 0};  // one launch over every read
+    return launch_gather_batches(bank, a, t, nullptr, s);
 }
 
 }  // namespace grim

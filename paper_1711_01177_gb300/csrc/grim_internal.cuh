@@ -72,8 +72,12 @@ struct GatherArgs {
     uint8_t* pass;
     uint16_t* sums;
 };
-int launch_gather_persistent(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
-                             unsigned long long* counter, cudaStream_t stream);
+// Gather launches over a.n_reads reads in batches of t.batch_reads (0 = one
+// launch), shaped by t.warps_per_cta, t.ctas_per_sm and t.reads_per_claim.
+// counter == nullptr: each CTA takes a cost-balanced read range; else the
+// warps claim reads from *counter, zeroed before every launch.
+int launch_gather_batches(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
+                          unsigned long long* counter, cudaStream_t stream);
 
 size_t scan_scratch_bytes(int q, int64_t n_reads);
 
