@@ -44,6 +44,8 @@ def _bind(lib):
         "oracle_scan": (I64, [P, I64, I32, P, P, I64, P, I64, I64, I64, P, P, P]),
         "oracle_bin_row": (I32, [P, I64, I32, I32, I32, I64, P]),
         "oracle_sellers": (I64, [P, I64, P, I64]),
+        "oracle_seed_candidates": (I64, [P, I64, I32, P, P, I64, I32, I64, I32, I64, P, P]),
+        "oracle_locate": (I64, [P, P, P, I64, P, I64, I32, I32, I64, P, P, P, P, P, I64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -161,3 +163,40 @@ class Oracle:
         r = np.ascontiguousarray(read, dtype=np.uint8)
         t = np.ascontiguousarray(text, dtype=np.uint8)
         return int(self.lib.oracle_sellers(_p(r), len(r), _p(t), len(t)))
+
+    def seed_candidates(self, ref_codes: np.ndarray, k: int, reads: np.ndarray, read_offsets: np.ndarray,
+                        bin_len: int, n_bins: int, cap: int):
+        """Candidate bins from exact seed locations (Sec. 1 Fig. 1, Sec. 3.3).
+        Returns (cand_bins u32, cand_offsets i64)."""
+        ref = np.ascontiguousarray(ref_codes, dtype=np.uint8)
+        rd = np.ascontiguousarray(reads, dtype=np.uint8)
+        off = np.ascontiguousarray(read_offsets, dtype=np.int64)
+        n = len(off) - 1
+        co = np.empty(n + 1, dtype=np.int64)
+        args = [_p(ref), len(ref), k, _p(rd), _p(off), n, bin_len, n_bins, cap]
+        total = self.lib.oracle_seed_candidates(*args, 0, None, _p(co))
+        if total < 0:
+            raise ValueError(f"oracle_seed_candidates: {total}")
+        cb = np.empty(max(int(total), 1), dtype=np.uint32)
+        total2 = self.lib.oracle_seed_candidates(*args, int(total), _p(cb), _p(co))
+        assert total2 == total
+        return cb[:total], co
+
+    def locate(self, pass_: np.ndarray, cand_bins: np.ndarray, cand_offsets: np.ndarray, ref_codes: np.ndarray,
+               bin_len: int, overlap: int, seg_stride: int = 0):
+        """Seed Location Checker (Sec. 3.3, Fig. 4): passing candidates with
+        their reference segments.  Returns (read, bin, begin, end, segments)."""
+        ps = np.ascontiguousarray(pass_, dtype=np.uint8)
+        cb = np.ascontiguousarray(cand_bins, dtype=np.uint32)
+        co = np.ascontiguousarray(cand_offsets, dtype=np.int64)
+        ref = np.ascontiguousarray(ref_codes, dtype=np.uint8)
+        n = len(co) - 1
+        m = int(np.count_nonzero(ps))
+        rd, bn = np.empty(m, np.uint32), np.empty(m, np.uint32)
+        be, en = np.empty(m, np.int64), np.empty(m, np.int64)
+        seg = np.empty((m, seg_stride), np.uint8) if seg_stride > 0 else None
+        got = self.lib.oracle_locate(_p(ps), _p(cb), _p(co), n, _p(ref), len(ref), bin_len, overlap, m, _p(rd),
+                                     _p(bn), _p(be), _p(en), _p(seg), seg_stride)
+        if got != m:
+            raise ValueError(f"oracle_locate: {got}")
+        return rd, bn, be, en, seg

@@ -245,3 +245,207 @@ int64_t oracle_sellers(const uint8_t* read, int64_t L, const uint8_t* text, int6
     free(cur);
     return best;
 }
+
+/* ------------------------------------------------ seed locations (Sec. 1, 3.3) */
+
+typedef struct { uint32_t bin; int64_t votes; } oracle_vote;
+
+static int oracle_cmp_u64(const void* a, const void* b) {
+    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return (x > y) - (x < y);
+}
+
+static int oracle_cmp_u32(const void* a, const void* b) {
+    uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+    return (x > y) - (x < y);
+}
+
+static int oracle_cmp_votes_desc(const void* a, const void* b) {
+    const oracle_vote *x = (const oracle_vote*)a, *y = (const oracle_vote*)b;
+    if (x->votes != y->votes) return x->votes > y->votes ? -1 : 1;
+    return (x->bin > y->bin) - (x->bin < y->bin);
+}
+
+static int oracle_cmp_vote_bin(const void* a, const void* b) {
+    const oracle_vote *x = (const oracle_vote*)a, *y = (const oracle_vote*)b;
+    return (x->bin > y->bin) - (x->bin < y->bin);
+}
+
+/* key of the k bases at s (first base most significant), or -1 if one of
+ * them is not a base code 0..3 */
+static int64_t oracle_seed_key(const uint8_t* s, int k) {
+    int64_t v = 0;
+    for (int j = 0; j < k; j++) {
+        if (s[j] > 3) return -1;
+        v = v * 4 + s[j];
+    }
+    return v;
+}
+
+/* index of key in the sorted array keys[0..n), or -1 */
+static int64_t oracle_find_key(const uint64_t* keys, int64_t n, uint64_t key) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (keys[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < n && keys[lo] == key) ? lo : -1;
+}
+
+/*
+ * Candidate bins of every read from its exact seed locations, the way a
+ * seed-and-extend mapper would hand them to the filter (Sec. 1 / Fig. 1:
+ * seeds are looked up in a hash table of reference locations; Sec. 3.3:
+ * only the bins that hold a potential seed location are checked).
+ * Readings:
+ *  - the seeds are the read's non-overlapping k-mers at offsets 0, k, 2k,
+ *    ... (o + k <= L); a seed holding a code > 3 has no locations;
+ *  - an exact occurrence of the seed at offset o at reference position p
+ *    puts the read's start at p - o: it votes for the bin whose core holds
+ *    max(0, p - o), clamped to the last bin;
+ *  - the distinct voted bins are the candidates; when there are more than
+ *    cap, the cap bins with the most votes are kept, equal votes going to
+ *    the lower bin id; each read's list is ascending.
+ * ref: codes 0..3 (len bases).  Writes cand_offsets[n + 1] always and
+ * cand_bins only when the total fits in out_cap; returns the total, or a
+ * negative error.
+ */
+int64_t oracle_seed_candidates(const uint8_t* ref, int64_t len, int k, const uint8_t* reads,
+                               const int64_t* read_offsets, int64_t n, int bin_len, int64_t n_bins, int cap,
+                               int64_t out_cap, uint32_t* cand_bins, int64_t* cand_offsets) {
+    if (k < 1 || k > 15 || bin_len < 1 || n_bins < 1 || cap < 1 || n < 0) return ORACLE_EINVAL;
+    /* 1. the seed keys the reads ask for, sorted, without repeats */
+    int64_t n_keys = 0;
+    for (int64_t r = 0; r < n; r++)
+        for (int64_t o = 0; o + k <= read_offsets[r + 1] - read_offsets[r]; o += k) n_keys++;
+    uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n_keys + 1));
+    if (!keys) return ORACLE_ENOMEM;
+    int64_t m = 0;
+    for (int64_t r = 0; r < n; r++)
+        for (int64_t o = 0; o + k <= read_offsets[r + 1] - read_offsets[r]; o += k) {
+            int64_t key = oracle_seed_key(reads + read_offsets[r] + o, k);
+            if (key >= 0) keys[m++] = (uint64_t)key;
+        }
+    qsort(keys, (size_t)m, sizeof(uint64_t), oracle_cmp_u64);
+    int64_t u = 0;
+    for (int64_t i = 0; i < m; i++)
+        if (u == 0 || keys[u - 1] != keys[i]) keys[u++] = keys[i];
+    /* 2. every reference position of each of those keys: one pass over the
+     *    reference, recomputing each k-mer from its bases */
+    int64_t* count = (int64_t*)calloc((size_t)(u + 1), sizeof(int64_t));
+    if (!count) { free(keys); return ORACLE_ENOMEM; }
+    for (int64_t p = 0; p + k <= len; p++) {
+        int64_t key = oracle_seed_key(ref + p, k);
+        int64_t i = key >= 0 ? oracle_find_key(keys, u, (uint64_t)key) : -1;
+        if (i >= 0) count[i + 1]++;
+    }
+    for (int64_t i = 0; i < u; i++) count[i + 1] += count[i];
+    int64_t* where = (int64_t*)malloc(sizeof(int64_t) * (size_t)(count[u] + 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(u + 1));
+    if (!where || !fill) { free(keys); free(count); free(where); free(fill); return ORACLE_ENOMEM; }
+    memcpy(fill, count, sizeof(int64_t) * (size_t)(u + 1));
+    for (int64_t p = 0; p + k <= len; p++) {
+        int64_t key = oracle_seed_key(ref + p, k);
+        int64_t i = key >= 0 ? oracle_find_key(keys, u, (uint64_t)key) : -1;
+        if (i >= 0) where[fill[i]++] = p;
+    }
+    free(fill);
+    /* 3. per read: votes, distinct bins with their vote counts, the cap */
+    int64_t total = 0;
+    cand_offsets[0] = 0;
+    for (int64_t r = 0; r < n; r++) {
+        const int64_t L = read_offsets[r + 1] - read_offsets[r];
+        int64_t* seed_at = (int64_t*)malloc(sizeof(int64_t) * (size_t)(L + 1));  /* seed offsets */
+        if (!seed_at) { free(keys); free(count); free(where); return ORACLE_ENOMEM; }
+        int64_t n_seeds = 0;
+        for (int64_t o = 0; o + k <= L; o += k) seed_at[n_seeds++] = o;
+        int64_t n_votes = 0;
+        for (int64_t s = 0; s < n_seeds; s++) {
+            int64_t key = oracle_seed_key(reads + read_offsets[r] + seed_at[s], k);
+            int64_t i = key >= 0 ? oracle_find_key(keys, u, (uint64_t)key) : -1;
+            if (i >= 0) n_votes += count[i + 1] - count[i];
+        }
+        uint32_t* votes = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n_votes + 1));
+        oracle_vote* bins = (oracle_vote*)malloc(sizeof(oracle_vote) * (size_t)(n_votes + 1));
+        if (!votes || !bins) {
+            free(seed_at); free(votes); free(bins); free(keys); free(count); free(where);
+            return ORACLE_ENOMEM;
+        }
+        int64_t v = 0;
+        for (int64_t s = 0; s < n_seeds; s++) {
+            const int64_t o = seed_at[s];
+            int64_t key = oracle_seed_key(reads + read_offsets[r] + o, k);
+            int64_t i = key >= 0 ? oracle_find_key(keys, u, (uint64_t)key) : -1;
+            if (i < 0) continue;
+            for (int64_t j = count[i]; j < count[i + 1]; j++) {
+                int64_t start = where[j] - o;
+                if (start < 0) start = 0;
+                int64_t b = start / bin_len;
+                if (b > n_bins - 1) b = n_bins - 1;
+                votes[v++] = (uint32_t)b;
+            }
+        }
+        free(seed_at);
+        qsort(votes, (size_t)v, sizeof(uint32_t), oracle_cmp_u32);
+        int64_t d = 0;
+        for (int64_t j = 0; j < v; j++) {
+            if (d > 0 && bins[d - 1].bin == votes[j]) {
+                bins[d - 1].votes++;
+            } else {
+                bins[d].bin = votes[j];
+                bins[d].votes = 1;
+                d++;
+            }
+        }
+        if (d > cap) {
+            qsort(bins, (size_t)d, sizeof(oracle_vote), oracle_cmp_votes_desc);
+            d = cap;
+            qsort(bins, (size_t)d, sizeof(oracle_vote), oracle_cmp_vote_bin);
+        }
+        for (int64_t j = 0; j < d; j++)
+            if (total + j < out_cap && cand_bins) cand_bins[total + j] = bins[j].bin;
+        total += d;
+        cand_offsets[r + 1] = total;
+        free(votes);
+        free(bins);
+    }
+    free(keys);
+    free(count);
+    free(where);
+    return total;
+}
+
+/*
+ * Seed Location Checker (Sec. 3.3, Fig. 4 steps 2-3): for every candidate
+ * whose filter bit is 1, in candidate order, the read, the bin and the
+ * reference segment the read mapper would align against: the bin's span
+ * [b*bin_len, min(len, b*bin_len + bin_len + overlap)).  When seg is not
+ * NULL, the segment's base codes are copied to seg + i*seg_stride (the rest
+ * of the row is filled with 4).  Returns the number of passing candidates
+ * (outputs written only while below out_cap), or a negative error.
+ */
+int64_t oracle_locate(const uint8_t* pass, const uint32_t* cand_bins, const int64_t* cand_offsets, int64_t n,
+                      const uint8_t* ref, int64_t len, int bin_len, int overlap, int64_t out_cap, uint32_t* out_read,
+                      uint32_t* out_bin, int64_t* out_begin, int64_t* out_end, uint8_t* seg, int64_t seg_stride) {
+    if (bin_len < 1 || overlap < 0 || n < 0) return ORACLE_EINVAL;
+    int64_t m = 0;
+    for (int64_t r = 0; r < n; r++)
+        for (int64_t c = cand_offsets[r]; c < cand_offsets[r + 1]; c++) {
+            if (!pass[c]) continue;
+            if (m < out_cap) {
+                int64_t b = cand_bins[c], begin, end;
+                oracle_bin_span(b, len, bin_len, overlap, &begin, &end);
+                out_read[m] = (uint32_t)r;
+                out_bin[m] = (uint32_t)b;
+                out_begin[m] = begin;
+                out_end[m] = end;
+                if (seg) {
+                    for (int64_t j = 0; j < seg_stride; j++)
+                        seg[m * seg_stride + j] = (begin + j < end) ? ref[begin + j] : 4;
+                }
+            }
+            m++;
+        }
+    return m;
+}

@@ -13,6 +13,7 @@ import pytest
 
 import oracle as oracle_pkg
 import test_oracle_pins as pins
+import test_oracle_seeds as seed_pins
 
 MUTANTS = {
     "unpack_msb_first": ("codes[k] = (uint8_t)((byte >> (2 * (k % 4))) & 3);",
@@ -30,6 +31,19 @@ MUTANTS = {
                               "for (int64_t i = 0; i + q < L; i++) {\n        int64_t t = oracle_token(read + i, q);"),
     "no_multiplicity": ("sum += bank_row[t];",
                         "sum += bank_row[t] && (i == 0 || oracle_token(read + i - 1, q) != t);"),
+    # seed locations and the Seed Location Checker
+    "seeds_overlapping": ("for (int64_t o = 0; o + k <= L; o += k) seed_at[n_seeds++] = o;",
+                          "for (int64_t o = 0; o + k <= L; o += 1) seed_at[n_seeds++] = o;"),
+    "seed_vote_no_offset": ("int64_t start = where[j] - o;", "int64_t start = where[j];"),
+    "seed_no_clamp_at_zero": ("if (start < 0) start = 0;", "if (start < 0) start = -start;"),
+    "seed_ties_to_higher_bin": ("    return (x->bin > y->bin) - (x->bin < y->bin);\n}\n\nstatic int oracle_cmp_vote_bin",
+                                "    return (x->bin < y->bin) - (x->bin > y->bin);\n}\n\nstatic int oracle_cmp_vote_bin"),
+    "seed_keeps_fewest_votes": ("if (x->votes != y->votes) return x->votes > y->votes ? -1 : 1;",
+                                "if (x->votes != y->votes) return x->votes < y->votes ? -1 : 1;"),
+    "seed_misses_last_position": ("    for (int64_t p = 0; p + k <= len; p++) {\n        int64_t key = oracle_seed_key(ref + p, k);\n        int64_t i = key >= 0 ? oracle_find_key(keys, u, (uint64_t)key) : -1;\n        if (i >= 0) count[i + 1]++;",
+                                  "    for (int64_t p = 0; p + k < len; p++) {\n        int64_t key = oracle_seed_key(ref + p, k);\n        int64_t i = key >= 0 ? oracle_find_key(keys, u, (uint64_t)key) : -1;\n        if (i >= 0) count[i + 1]++;"),
+    "locate_segment_off_by_one": ("seg[m * seg_stride + j] = (begin + j < end) ? ref[begin + j] : 4;",
+                                  "seg[m * seg_stride + j] = (begin + j <= end) ? ref[begin + j] : 4;"),
 }
 
 
@@ -47,6 +61,9 @@ def _pin_suite(o):
     pins.test_no_miss_within_edit_distance(o, 4, 4, 1)
     pins.test_invariants_sum_bound_monotone_scan(o)
     pins.test_short_reads(o)
+    seed_pins.test_hand_example_votes_cap_and_ties(o)
+    seed_pins.test_brute_force_string_search(o, 1)
+    seed_pins.test_locate_hand_example(o)
 
 
 def test_unmodified_oracle_passes_suite():
