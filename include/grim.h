@@ -247,6 +247,88 @@ int grim_scan_noalloc(const grim_bank* bank, const uint8_t* reads, const int64_t
                       const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,
                       uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* stream);
 
+/* ---- seed locations: the mapper's steps either side of the filter ------ */
+
+/*
+ * Seed location table of a reference (the hash table a seed-and-extend
+ * mapper indexes with each seed, Sec. 1 / Fig. 1 step 3): the start
+ * position of every k-mer, grouped by k-mer value in CSR form.
+ *   ref2bit  device, 2-bit packed reference (base i in bits 2*(i%4) of
+ *            byte i/4), as for grim_build_bank.
+ *   len      bases, k <= len <= 2^32 - 1 (positions are u32).
+ *   k        1..15 (keys index 4^k + 1 u32 offsets: 67 MB for k = 12).
+ *   *out     receives the table (library-owned until grim_seed_index_free).
+ * Device memory: 4 * (4^k + 1) + 4 * (len - k + 1) bytes, plus 4 * 4^k
+ * bytes of stream-ordered scratch during the build.  The order of the
+ * positions of one k-mer is not specified.  Enqueues on `stream`.
+ */
+typedef struct grim_seed_index grim_seed_index;
+int grim_seed_index_build(const uint8_t* ref2bit, int64_t len, int k, void* stream, grim_seed_index** out);
+
+/* Table metadata and zero-copy device views (offsets: 4^k + 1 u32,
+ * positions: len - k + 1 u32).  Any output pointer may be NULL. */
+int grim_seed_index_info(const grim_seed_index* idx, int64_t* len, int* k, const uint32_t** offsets,
+                         const uint32_t** positions);
+
+/* Free the table (synchronises the device first).  NULL is a no-op. */
+int grim_seed_index_free(grim_seed_index* idx);
+
+/*
+ * Candidate bins of every read from its exact seed locations: what the
+ * mapper sends to the filter with each read (Sec. 3.3: only the bins that
+ * hold a potential seed location are checked).
+ *   Seeds: the read's non-overlapping k-mers at offsets 0, k, 2k, ...
+ *   (o + k <= L); a seed holding a code > 3 has no locations.  A location p
+ *   of the seed at offset o puts the read's start at p - o and votes for
+ *   the bin whose core holds max(0, p - o) (at most n_bins - 1).  The
+ *   distinct voted bins are the read's candidates; when there are more
+ *   than `cap`, the cap bins with the most votes are kept, equal votes
+ *   going to the lower bin id.  Each read's list is ascending.
+ *   reads, read_offsets, n_reads  as for grim_filter.
+ *   bin_len, n_bins   the bank's geometry (n_bins < 2^32).
+ *   cap               >= 1.
+ *   cand_bins         device u32 output, `capacity` entries (may be NULL
+ *                     when capacity is 0).
+ *   cand_offsets      device int64 output, n_reads + 1 entries (CSR,
+ *                     cand_offsets[0] = 0); always written in full.
+ *   *n_cands          host: the total number of candidates.
+ * Returns GRIM_EOVERFLOW when the total exceeds `capacity` (then only the
+ * first `capacity` bins are written; call again with a larger buffer).
+ * Unlike the filter entry points this call SYNCHRONISES `stream`: reads are
+ * processed in batches whose vote scratch (12 bytes per seed location,
+ * cudaMallocAsync) is sized from per-read location counts read back to
+ * the host.
+ */
+int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const int64_t* read_offsets,
+                         int64_t n_reads, int bin_len, int64_t n_bins, int cap, uint32_t* cand_bins,
+                         int64_t capacity, int64_t* cand_offsets, int64_t* n_cands, void* stream);
+
+/*
+ * Seed Location Checker (Sec. 3.3, Fig. 4 steps 2-3): the locations whose
+ * filter bit is 1, in candidate order, with the reference segment the
+ * aligner receives for each - the bin's span [b * bin_len,
+ * min(len, b * bin_len + bin_len + overlap)).
+ *   bank              the bank the mask was computed with (geometry).
+ *   cand_bins, cand_offsets, n_reads   the candidate lists (CSR,
+ *                     cand_offsets[0] = 0, cand_offsets[n_reads] = n_cands).
+ *   pass              device u8 [n_cands]: the filter bitmask.
+ *   loc_read, loc_bin device u32 outputs, loc_begin, loc_end device int64
+ *                     outputs, `capacity` entries each.
+ *   segments          device u8 [capacity * seg_stride] or NULL: row i holds
+ *                     the base codes of location i's span, then code 4 up
+ *                     to seg_stride (a span longer than seg_stride is cut);
+ *                     needs ref2bit (device, 2-bit packed reference).
+ *   *n_loc            device int64: the number of passing locations (which
+ *                     may exceed capacity; outputs beyond it are not written).
+ * A passing candidate whose bin id is >= n_bins gets the empty span [0, 0)
+ * and raises GRIM_FLAG_BAD_BIN; cand_offsets[n_reads] != n_cands raises
+ * GRIM_FLAG_BAD_OFFSETS.  Enqueues on `stream` (stream-ordered scratch).
+ */
+int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* cand_bins,
+                const int64_t* cand_offsets, int64_t n_reads, int64_t n_cands, const uint8_t* pass,
+                uint32_t* loc_read, uint32_t* loc_bin, int64_t* loc_begin, int64_t* loc_end, uint8_t* segments,
+                int64_t seg_stride, int64_t capacity, int64_t* n_loc, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

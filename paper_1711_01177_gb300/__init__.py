@@ -45,6 +45,11 @@ SIGNATURES = {
     "grim_autotune": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
     "grim_choose_form": (_I32, [_P, _I64, _I64, ctypes.POINTER(_I32)]),
     "grim_filter_auto": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
+    "grim_seed_index_build": (_I32, [_P, _I64, _I32, _P, ctypes.POINTER(_P)]),
+    "grim_seed_index_info": (_I32, [_P, _P, _P, _P, _P]),
+    "grim_seed_index_free": (_I32, [_P]),
+    "grim_seed_candidates": (_I32, [_P, _P, _P, _I64, _I32, _I64, _I32, _P, _I64, _P, ctypes.POINTER(_I64), _P]),
+    "grim_locate": (_I32, [_P, _P, _P, _P, _I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _I64, _P, _P]),
 }
 GRIM_FORM_GATHER, GRIM_FORM_SCAN = 0, 1
 
@@ -311,3 +316,108 @@ def grim_filter_auto(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor
                                    _dev_ptr(pass_out, "pass", 1), batch_reads, ctypes.byref(scanned),
                                    _stream_ptr(stream)), "grim_filter_auto")
     return pass_out, scanned.value
+
+
+class SeedIndex:
+    """A seed location table (every k-mer's reference positions), owned by libgrim."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        L, k = ctypes.c_int64(), ctypes.c_int()
+        off, pos = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(load().grim_seed_index_info(handle, ctypes.byref(L), ctypes.byref(k), ctypes.byref(off),
+                                           ctypes.byref(pos)), "grim_seed_index_info")
+        self.len, self.k = L.value, k.value
+        self._off, self._pos = off.value, pos.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def offsets(self) -> torch.Tensor:
+        """Zero-copy int32 view of the 4^k + 1 CSR offsets (u32 values)."""
+        return torch.as_tensor(_CudaArray(self._off, ((1 << (2 * self.k)) + 1,), "<i4"), device="cuda")
+
+    def positions(self) -> torch.Tensor:
+        """Zero-copy int32 view of the len - k + 1 positions (u32 values)."""
+        return torch.as_tensor(_CudaArray(self._pos, (self.len - self.k + 1,), "<i4"), device="cuda")
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            _check(load().grim_seed_index_free(self._h), "grim_seed_index_free")
+        self._h = None
+
+    def __del__(self):
+        try:
+            if self._h is not None and self._h.value and _lib is not None:
+                _lib.grim_seed_index_free(self._h)
+        except Exception:
+            pass
+
+
+def grim_seed_index_build(ref2bit: torch.Tensor, length: int, k: int = 12, stream=None) -> SeedIndex:
+    """Reference positions of every k-mer (the mapper's seed table, Sec. 1 Fig. 1)."""
+    h = ctypes.c_void_p()
+    _check(load().grim_seed_index_build(_dev_ptr(ref2bit, "ref2bit", 1), length, k, _stream_ptr(stream),
+                                        ctypes.byref(h)), "grim_seed_index_build")
+    return SeedIndex(h)
+
+
+def grim_seed_candidates(idx: SeedIndex, reads: torch.Tensor, read_offsets: torch.Tensor, bin_len: int,
+                         n_bins: int, cap: int, capacity: int | None = None, stream=None):
+    """Candidate bins from exact seed locations (Sec. 3.3).  Returns
+    (cand_bins u32-as-int32, cand_offsets int64); synchronises the stream."""
+    n_reads = read_offsets.numel() - 1
+    if n_reads < 0:
+        raise ValueError("read_offsets needs n_reads + 1 entries")
+    co = torch.empty(n_reads + 1, dtype=torch.int64, device=read_offsets.device)
+    if capacity is None:
+        capacity = max(1024, n_reads * 64)
+    total = ctypes.c_int64()
+    for _ in range(2):
+        cb = torch.empty(max(capacity, 1), dtype=torch.int32, device=read_offsets.device)
+        st = load().grim_seed_candidates(idx.handle, _dev_ptr(reads, "reads", 1),
+                                         _dev_ptr(read_offsets, "read_offsets", 8), n_reads, bin_len, n_bins, cap,
+                                         _dev_ptr(cb, "cand_bins", 4), capacity, _dev_ptr(co, "cand_offsets", 8),
+                                         ctypes.byref(total), _stream_ptr(stream))
+        if st == GRIM_EOVERFLOW:
+            capacity = total.value
+            continue
+        _check(st, "grim_seed_candidates")
+        return cb[:total.value], co
+    raise GrimError(GRIM_EOVERFLOW, "grim_seed_candidates")
+
+
+class Located:
+    """Passing locations from grim_locate: read, bin, span [begin, end) and
+    optional segment rows; `n` = number of passing locations."""
+
+    def __init__(self, read, bin_, begin, end, segments, n):
+        self.read, self.bin, self.begin, self.end, self.segments, self.n = read, bin_, begin, end, segments, n
+
+
+def grim_locate(bank: Bank, cand_bins: torch.Tensor, cand_offsets: torch.Tensor, pass_: torch.Tensor,
+                ref2bit: torch.Tensor | None = None, seg_stride: int = 0, capacity: int | None = None,
+                stream=None) -> Located:
+    """Seed Location Checker (Sec. 3.3, Fig. 4): passing locations and their
+    reference segments.  capacity defaults to the number of passing bytes."""
+    n_reads = cand_offsets.numel() - 1
+    n_cands = pass_.numel()
+    dev = pass_.device
+    if capacity is None:
+        capacity = int(torch.count_nonzero(pass_).item()) if n_cands else 0
+    rd = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    bn = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    be = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev)
+    en = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev)
+    seg = torch.empty((max(capacity, 1), seg_stride), dtype=torch.uint8, device=dev) if seg_stride > 0 else None
+    n_loc = torch.zeros(1, dtype=torch.int64, device=dev)
+    _check(load().grim_locate(bank.handle, _dev_ptr(ref2bit, "ref2bit", 1, True), _dev_ptr(cand_bins, "cand_bins", 4),
+                              _dev_ptr(cand_offsets, "cand_offsets", 8), n_reads, n_cands,
+                              _dev_ptr(pass_, "pass", 1), _dev_ptr(rd, "loc_read", 4), _dev_ptr(bn, "loc_bin", 4),
+                              _dev_ptr(be, "loc_begin", 8), _dev_ptr(en, "loc_end", 8),
+                              _dev_ptr(seg, "segments", 1, True), seg_stride, capacity,
+                              _dev_ptr(n_loc, "n_loc", 8), _stream_ptr(stream)), "grim_locate")
+    n = int(n_loc.item())
+    m = min(n, capacity)
+    return Located(rd[:m], bn[:m], be[:m], en[:m], seg[:m] if seg is not None else None, n)

@@ -1,0 +1,708 @@
+// The steps either side of the filter in a seed-and-extend mapper.
+//
+// Before (Sec. 1, Fig. 1 steps 2-3): the read's seeds are looked up in a
+// table of reference locations; each location is a potential mapping, and
+// the filter checks the bins that hold one (Sec. 3.3).
+//   - grim_seed_index_build: a CSR table of the start positions of every
+//     k-mer of the reference (count, prefix sum, fill; the order of the
+//     positions of one k-mer is not specified);
+//   - grim_seed_candidates: non-overlapping k-mer seeds per read; every
+//     location p of the seed at offset o votes for the bin whose core holds
+//     max(0, p - o); distinct bins are kept, the `cap` most voted when
+//     there are more (equal votes: the lower bin), ascending.  Per batch of
+//     reads: hits per read (warp per read) -> prefix sum -> votes expanded
+//     into scratch -> one CTA per read sorts its votes (bitonic, in shared
+//     memory up to kDedupSmem, else in place in global memory), counts the
+//     runs, applies the cap (binary search on the vote threshold) and
+//     compacts -> prefix sum of the kept counts -> copy into the CSR output.
+// After (Sec. 3.3, Fig. 4 steps 2-3): the Seed Location Checker turns the
+// filter's bitmask into the list of passing locations and the reference
+// segments the aligner receives.
+//   - grim_locate: tile counts of passing bytes -> prefix sum -> ordered
+//     write of (read, bin, span); optional segment bases copied out of the
+//     2-bit reference (one warp per segment).
+#include "grim_internal.cuh"
+
+struct grim_seed_index {
+    int64_t len;
+    int k;
+    int device;
+    uint32_t* offsets;    // device, 4^k + 1 entries
+    uint32_t* positions;  // device, len - k + 1 entries
+};
+
+namespace grim {
+namespace {
+
+// ------------------------------------------------------------ prefix sums
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int64_t kScanTile = (int64_t)kScanThreads * kScanItems;
+
+// Block-wide exclusive scan of one value per thread (all threads call it);
+// *total receives the block's sum.
+template <typename T>
+__device__ T block_exclusive_scan(T v, T* warp_sums, T* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? warp_sums[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    const T before = warp == 0 ? T(0) : warp_sums[warp - 1];
+    *total = warp_sums[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+template <typename T>
+__global__ void set_value_kernel(T* p, T v) {
+    *p = v;
+}
+
+// tile sums over the same index sets scan_tiles_kernel uses
+template <typename T>
+__global__ void tile_sums_kernel(const T* __restrict__ in, int64_t n, T* __restrict__ sums) {
+    __shared__ T ws[32];
+    const int64_t t0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++)
+        if (t0 + i < n) s += in[t0 + i];
+    T total;
+    block_exclusive_scan<T>(s, ws, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// one block of 1024 threads: sums[b] <- init + sum of sums[0..b)
+template <typename T>
+__global__ void scan_sums_kernel(T* __restrict__ sums, int64_t n_tiles, T init) {
+    __shared__ T ws[32];
+    T carry = init;
+    for (int64_t b = 0; b < n_tiles; b += blockDim.x) {
+        const int64_t j = b + threadIdx.x;
+        const T v = j < n_tiles ? sums[j] : T(0);
+        T total;
+        const T ex = block_exclusive_scan<T>(v, ws, &total);
+        if (j < n_tiles) sums[j] = carry + ex;
+        carry += total;
+    }
+}
+
+// out[i] = tile base + sum of in[tile start .. i); out[n] = the grand total.
+// Each thread reads its own items before writing them, so in == out works.
+template <typename T>
+__global__ void scan_tiles_kernel(const T* in, T* out, int64_t n, const T* __restrict__ sums) {
+    __shared__ T ws[32];
+    const int64_t t0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    T v[kScanItems];
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        v[i] = t0 + i < n ? in[t0 + i] : T(0);
+        s += v[i];
+    }
+    T total;
+    T run = sums[blockIdx.x] + block_exclusive_scan<T>(s, ws, &total);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        if (t0 + i < n) out[t0 + i] = run;
+        run += v[i];
+        if (t0 + i == n - 1) out[n] = run;
+    }
+}
+
+}  // namespace
+
+// out[0..n]: out[i] = init + in[0] + ... + in[i-1]; in == out is allowed.
+template <typename T>
+int exclusive_scan(const T* in, T* out, int64_t n, T init, cudaStream_t s) {
+    if (n == 0) {
+        set_value_kernel<T><<<1, 1, 0, s>>>(out, init);
+        GRIM_CUDA_TRY(cudaGetLastError());
+        return GRIM_OK;
+    }
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    T* sums = nullptr;
+    GRIM_CUDA_TRY(cudaMallocAsync((void**)&sums, (size_t)tiles * sizeof(T), s));
+    tile_sums_kernel<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
+    scan_sums_kernel<T><<<1, 1024, 0, s>>>(sums, tiles, init);
+    scan_tiles_kernel<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(sums, s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GRIM_ECUDA;
+    }
+    return GRIM_OK;
+}
+
+namespace {
+
+__device__ __forceinline__ uint32_t ref_base(const uint8_t* __restrict__ ref2bit, int64_t i) {
+    return (__ldg(ref2bit + (i >> 2)) >> (2 * (i & 3))) & 3u;
+}
+
+// ------------------------------------------------------------- seed index
+
+constexpr int kIndexChunk = 64;  // consecutive positions per thread (rolling key)
+
+// FILL = false: counts[key]++ for every position; true: positions[cursor[key]++] = p.
+template <bool FILL>
+__global__ void seed_index_kernel(const uint8_t* __restrict__ ref2bit, int64_t npos, int k,
+                                  uint32_t* __restrict__ table, uint32_t* __restrict__ positions) {
+    const uint32_t mask = (k >= 16) ? 0xFFFFFFFFu : ((1u << (2 * k)) - 1u);
+    const int64_t chunks = (npos + kIndexChunk - 1) / kIndexChunk;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p0 = c * kIndexChunk;
+        const int64_t p1 = p0 + kIndexChunk < npos ? p0 + kIndexChunk : npos;
+        uint32_t key = 0;
+        for (int j = 0; j < k - 1; j++) key = (key << 2) | ref_base(ref2bit, p0 + j);
+        for (int64_t p = p0; p < p1; p++) {
+            key = ((key << 2) | ref_base(ref2bit, p + k - 1)) & mask;
+            if (FILL) {
+                const uint32_t slot = atomicAdd(&table[key], 1u);
+                positions[slot] = (uint32_t)p;
+            } else {
+                atomicAdd(&table[key], 1u);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------- seed candidates
+
+// Key of the k bases at s (first base most significant); false if one of
+// them is not a base code.
+__device__ __forceinline__ bool seed_key(const uint8_t* __restrict__ s, int k, uint32_t* key) {
+    uint32_t v = 0;
+    bool ok = true;
+    for (int j = 0; j < k; j++) {
+        const uint32_t c = __ldg(s + j);
+        ok &= c <= 3u;
+        v = (v << 2) | (c & 3u);
+    }
+    *key = v;
+    return ok;
+}
+
+__device__ __forceinline__ int64_t n_seeds_of(int64_t L, int k) { return L >= k ? L / k : 0; }
+
+// hits[r] = number of reference locations of read r's seeds (warp per read)
+__global__ void seed_hits_kernel(const uint32_t* __restrict__ idx_off, int k, const uint8_t* __restrict__ reads,
+                                 const int64_t* __restrict__ read_offsets, int64_t n, int64_t* __restrict__ hits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        const int64_t ro = read_offsets[r], L = read_offsets[r + 1] - ro;
+        const int64_t ns = n_seeds_of(L, k);
+        int64_t h = 0;
+        for (int64_t sd = lane; sd < ns; sd += 32) {
+            uint32_t key;
+            if (seed_key(reads + ro + sd * k, k, &key)) h += (int64_t)(idx_off[key + 1] - idx_off[key]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
+        if (lane == 0) hits[r] = h;
+    }
+}
+
+// The batch's votes: read r's bins at H[hit_off[r] - h0 ...] (warp per read;
+// seeds in order, each seed's locations spread over the lanes).
+__global__ void seed_expand_kernel(const uint32_t* __restrict__ idx_off, const uint32_t* __restrict__ idx_pos, int k,
+                                   const uint8_t* __restrict__ reads, const int64_t* __restrict__ read_offsets,
+                                   int64_t n, const int64_t* __restrict__ hit_off, int64_t h0, uint32_t bin_len,
+                                   uint32_t last_bin, uint32_t* __restrict__ H) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        const int64_t ro = read_offsets[r], L = read_offsets[r + 1] - ro;
+        const int64_t ns = n_seeds_of(L, k);
+        int64_t w = hit_off[r] - h0;
+        for (int64_t g = 0; g < ns; g += 32) {
+            // lane sd of this group looks up seed g + sd
+            uint32_t a = 0, b = 0;
+            if (g + lane < ns) {
+                uint32_t key;
+                if (seed_key(reads + ro + (g + lane) * k, k, &key)) {
+                    a = idx_off[key];
+                    b = idx_off[key + 1];
+                }
+            }
+            const int m = ns - g < 32 ? (int)(ns - g) : 32;
+            for (int sd = 0; sd < m; sd++) {
+                const uint32_t sa = __shfl_sync(kFull, a, sd), sb = __shfl_sync(kFull, b, sd);
+                const uint32_t o = (uint32_t)((g + sd) * k);
+                for (uint32_t j = sa + lane; j < sb; j += 32) {
+                    const uint32_t p = __ldg(idx_pos + j);
+                    const uint32_t start = p > o ? p - o : 0u;
+                    const uint32_t bin = start / bin_len;
+                    H[w + (j - sa)] = bin < last_bin ? bin : last_bin;
+                }
+                w += sb - sa;
+            }
+        }
+    }
+}
+
+// Ascending sort of A[0..n) by a bitonic network whose comparators all put
+// the smaller value at the lower index, over the array padded to a power
+// of two with +infinity.  The padding never moves under such comparators,
+// so pairs that reach into it are skipped and it needs no storage.  A is
+// shared or global memory owned by this CTA.
+__device__ void bitonic_sort(uint32_t* A, int64_t n) {
+    int lg = 0;
+    while ((int64_t(1) << lg) < n) lg++;
+    const int64_t half_p = (int64_t(1) << lg) >> 1;
+    for (int s = 1; s <= lg; s++) {
+        // merge blocks of 2^s: first each element against its mirror
+        for (int64_t t = threadIdx.x; t < half_p; t += blockDim.x) {
+            const int64_t blk = t >> (s - 1), off = t & ((int64_t(1) << (s - 1)) - 1);
+            const int64_t i = (blk << s) + off, j = (blk << s) + (int64_t(1) << s) - 1 - off;
+            if (j < n) {
+                const uint32_t x = A[i], y = A[j];
+                if (x > y) {
+                    A[i] = y;
+                    A[j] = x;
+                }
+            }
+        }
+        __syncthreads();
+        // then half-cleaners of decreasing stride
+        for (int d = s - 2; d >= 0; d--) {
+            for (int64_t t = threadIdx.x; t < half_p; t += blockDim.x) {
+                const int64_t i = ((t >> d) << (d + 1)) + (t & ((int64_t(1) << d) - 1)), j = i + (int64_t(1) << d);
+                if (j < n) {
+                    const uint32_t x = A[i], y = A[j];
+                    if (x > y) {
+                        A[i] = y;
+                        A[j] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+constexpr int kDedupThreads = 256;
+constexpr int kDedupSmem = 8192;  // votes sorted in shared memory up to this many
+
+// Block-wide count of S[0..u) entries with votes >= v (packed votes << 32 | bin).
+__device__ int64_t count_votes_at_least(const unsigned long long* S, int64_t u, uint32_t v, int64_t* ws) {
+    int64_t c = 0;
+    for (int64_t j = threadIdx.x; j < u; j += blockDim.x) c += (uint32_t)(S[j] >> 32) >= v;
+    int64_t total;
+    block_exclusive_scan<int64_t>(c, ws, &total);
+    return total;
+}
+
+// One CTA per read of the batch: sort its votes, count runs, apply the cap,
+// write the kept bins (ascending) to H[hit_off[r] - h0 ...] and their
+// number to kept[r].  S: scratch of one u64 per vote.
+__global__ void __launch_bounds__(kDedupThreads)
+seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, uint32_t* __restrict__ H,
+                   unsigned long long* __restrict__ S, int64_t* __restrict__ kept) {
+    __shared__ uint32_t A_s[kDedupSmem];
+    __shared__ int64_t ws[32];
+    __shared__ unsigned int max_votes;
+    const int64_t r = blockIdx.x;
+    const int64_t base = hit_off[r] - h0, n = hit_off[r + 1] - hit_off[r];
+    if (n <= 0) {
+        if (threadIdx.x == 0) kept[r] = 0;
+        return;
+    }
+    uint32_t* A;
+    if (n <= kDedupSmem) {
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) A_s[i] = H[base + i];
+        __syncthreads();
+        A = A_s;
+    } else {
+        A = H + base;
+    }
+    bitonic_sort(A, n);
+
+    // runs: first the start of run j goes to S[j], then at each run's end
+    // S[j] <- votes << 32 | bin (the run's own end reads and writes it)
+    unsigned long long* Sr = S + base;
+    int64_t u = 0;
+    for (int64_t i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        const int64_t f = (i < n && (i == 0 || A[i] != A[i - 1])) ? 1 : 0;
+        int64_t tot;
+        const int64_t ex = block_exclusive_scan<int64_t>(f, ws, &tot);
+        if (f) Sr[u + ex] = (unsigned long long)i;
+        u += tot;
+    }
+    __syncthreads();
+    int64_t seen = 0;
+    for (int64_t i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        const int64_t f = (i < n && (i == 0 || A[i] != A[i - 1])) ? 1 : 0;
+        int64_t tot;
+        const int64_t ex = block_exclusive_scan<int64_t>(f, ws, &tot);
+        if (i < n && (i == n - 1 || A[i + 1] != A[i])) {
+            const int64_t j = seen + ex + f - 1;  // the run holding i
+            const int64_t votes = i - (int64_t)Sr[j] + 1;
+            Sr[j] = ((unsigned long long)(votes < 0xFFFFFFFFll ? votes : 0xFFFFFFFFll) << 32) | A[i];
+        }
+        seen += tot;
+    }
+    __syncthreads();
+
+    // the cap: keep votes > v_star, and the first `need` (lowest bins) at v_star
+    uint32_t v_star = 0;
+    int64_t need = 0;
+    const bool capped = u > cap;
+    if (capped) {
+        if (threadIdx.x == 0) max_votes = 0;
+        __syncthreads();
+        for (int64_t j = threadIdx.x; j < u; j += blockDim.x) atomicMax(&max_votes, (unsigned)(Sr[j] >> 32));
+        __syncthreads();
+        uint32_t lo = 1, hi = max_votes;  // count(votes >= lo) >= cap always holds
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo + 1) / 2;
+            if (count_votes_at_least(Sr, u, mid, ws) >= cap) lo = mid;
+            else hi = mid - 1;
+        }
+        v_star = lo;
+        need = cap - count_votes_at_least(Sr, u, v_star + 1, ws);
+    }
+    // compaction in bin order (A is no longer read, so H may be overwritten)
+    uint32_t* out = H + base;
+    int64_t n_eq = 0, n_keep = 0;
+    for (int64_t j0 = 0; j0 < u; j0 += blockDim.x) {
+        const int64_t j = j0 + threadIdx.x;
+        const unsigned long long x = j < u ? Sr[j] : 0ull;
+        const uint32_t votes = (uint32_t)(x >> 32);
+        const int64_t eq = (j < u && capped && votes == v_star) ? 1 : 0;
+        int64_t tot_eq;
+        const int64_t ex_eq = block_exclusive_scan<int64_t>(eq, ws, &tot_eq);
+        const int64_t keep = (j < u && (!capped || votes > v_star || (eq && n_eq + ex_eq < need))) ? 1 : 0;
+        int64_t tot_keep;
+        const int64_t ex_keep = block_exclusive_scan<int64_t>(keep, ws, &tot_keep);
+        if (keep) out[n_keep + ex_keep] = (uint32_t)x;
+        n_eq += tot_eq;
+        n_keep += tot_keep;
+    }
+    if (threadIdx.x == 0) kept[r] = n_keep;
+}
+
+// cand_bins[cand_off[r] ...] <- the kept bins of read r (warp per read),
+// entries at or beyond `capacity` dropped.
+__global__ void seed_copy_kernel(const uint32_t* __restrict__ H, const int64_t* __restrict__ hit_off, int64_t h0,
+                                 const int64_t* __restrict__ cand_off, int64_t n, uint32_t* __restrict__ cand_bins,
+                                 int64_t capacity) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        const uint32_t* src = H + (hit_off[r] - h0);
+        const int64_t d = cand_off[r], m = cand_off[r + 1] - d;
+        for (int64_t j = lane; j < m; j += 32)
+            if (d + j < capacity) cand_bins[d + j] = src[j];
+    }
+}
+
+// next batch [r0, r1): the most reads after r0 whose votes fit `budget`
+// (at least one read), at most max_reads.  out = {hit_off[r0], r1, hit_off[r1]}.
+__global__ void batch_end_kernel(const int64_t* __restrict__ hit_off, int64_t n, int64_t r0, int64_t budget,
+                                 int64_t max_reads, int64_t* __restrict__ out) {
+    const int64_t h0 = hit_off[r0];
+    int64_t lo = r0 + 1, hi = (n - r0) < max_reads ? n : r0 + max_reads;
+    while (lo < hi) {  // largest r1 in [r0 + 1, hi] with hit_off[r1] - h0 <= budget (or r0 + 1)
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (hit_off[mid] - h0 <= budget) lo = mid;
+        else hi = mid - 1;
+    }
+    out[0] = h0;
+    out[1] = lo;
+    out[2] = hit_off[lo];
+}
+
+// ------------------------------------------------------ seed location checker
+
+constexpr int64_t kLocTile = kScanTile;
+
+__global__ void locate_count_kernel(const uint8_t* __restrict__ pass, int64_t n_cands, int64_t* __restrict__ counts) {
+    __shared__ int64_t ws[32];
+    const int64_t t0 = (int64_t)blockIdx.x * kLocTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t c = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++)
+        if (t0 + i < n_cands) c += pass[t0 + i] != 0;
+    int64_t total;
+    block_exclusive_scan<int64_t>(c, ws, &total);
+    if (threadIdx.x == 0) counts[blockIdx.x] = total;
+}
+
+// read holding candidate c: the last r with cand_offsets[r] <= c
+__device__ __forceinline__ int64_t read_of(const int64_t* __restrict__ co, int64_t n_reads, int64_t c) {
+    int64_t lo = 0, hi = n_reads - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (co[mid] <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void locate_write_kernel(const uint8_t* __restrict__ pass, const uint32_t* __restrict__ cand_bins,
+                                    const int64_t* __restrict__ cand_offsets, int64_t n_reads, int64_t n_cands,
+                                    const int64_t* __restrict__ tile_base, int64_t len, int64_t n_bins, int bin_len,
+                                    int overlap, int64_t capacity, uint32_t* __restrict__ loc_read,
+                                    uint32_t* __restrict__ loc_bin, int64_t* __restrict__ loc_begin,
+                                    int64_t* __restrict__ loc_end, uint32_t* __restrict__ status) {
+    __shared__ int64_t ws[32];
+    const int64_t t0 = (int64_t)blockIdx.x * kLocTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t c_own = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++)
+        if (t0 + i < n_cands) c_own += pass[t0 + i] != 0;
+    int64_t total;
+    int64_t o = tile_base[blockIdx.x] + block_exclusive_scan<int64_t>(c_own, ws, &total);
+    uint32_t flags = 0;
+    for (int i = 0; i < kScanItems; i++) {
+        const int64_t c = t0 + i;
+        if (c >= n_cands || !pass[c]) continue;
+        if (o < capacity) {
+            const uint32_t b = cand_bins[c];
+            int64_t begin = 0, end = 0;
+            if ((int64_t)b < n_bins) {
+                begin = (int64_t)b * bin_len;
+                end = begin + bin_len + overlap < len ? begin + bin_len + overlap : len;
+            } else {
+                flags |= GRIM_FLAG_BAD_BIN;
+            }
+            loc_read[o] = (uint32_t)read_of(cand_offsets, n_reads, c);
+            loc_bin[o] = b;
+            loc_begin[o] = begin;
+            loc_end[o] = end;
+        }
+        o++;
+    }
+    if (threadIdx.x == 0 && blockIdx.x == 0 && cand_offsets[n_reads] != n_cands) flags |= GRIM_FLAG_BAD_OFFSETS;
+    if (flags) atomicOr(status, flags);
+}
+
+// segment rows: the span's base codes, then 4 up to the stride (warp per row)
+__global__ void locate_segments_kernel(const uint8_t* __restrict__ ref2bit, const int64_t* __restrict__ n_loc,
+                                       int64_t capacity, const int64_t* __restrict__ loc_begin,
+                                       const int64_t* __restrict__ loc_end, uint8_t* __restrict__ seg,
+                                       int64_t stride) {
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = *n_loc < capacity ? *n_loc : capacity;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += warps) {
+        const int64_t b = loc_begin[i], e = loc_end[i];
+        uint8_t* row = seg + i * stride;
+        for (int64_t j = lane; j < stride; j += 32) row[j] = b + j < e ? (uint8_t)ref_base(ref2bit, b + j) : 4;
+    }
+}
+
+}  // namespace
+}  // namespace grim
+
+extern "C" {
+
+int grim_seed_index_build(const uint8_t* ref2bit, int64_t len, int k, void* stream, grim_seed_index** out) {
+    if (!out) return GRIM_EINVAL;
+    *out = nullptr;
+    if (!ref2bit || k < 1 || k > 15 || len < k || len > (int64_t)0xFFFFFFFFll) return GRIM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nk = int64_t(1) << (2 * k);
+    const int64_t npos = len - k + 1;
+    grim_seed_index* idx = new grim_seed_index();
+    idx->len = len;
+    idx->k = k;
+    if (cudaGetDevice(&idx->device) != cudaSuccess) {
+        delete idx;
+        return GRIM_ECUDA;
+    }
+    uint32_t* cursor = nullptr;
+    cudaError_t e = cudaMalloc((void**)&idx->offsets, (size_t)(nk + 1) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&idx->positions, (size_t)npos * 4);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&cursor, (size_t)nk * 4, s);
+    int rc = GRIM_OK;
+    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, (size_t)nk * 4, s);
+    if (e == cudaSuccess) {
+        const int blocks = grim::sm_count() * 8;
+        grim::seed_index_kernel<false><<<blocks, 256, 0, s>>>(ref2bit, npos, k, cursor, nullptr);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) rc = grim::exclusive_scan<uint32_t>(cursor, idx->offsets, nk, 0u, s);
+        if (e == cudaSuccess && rc == GRIM_OK)
+            e = cudaMemcpyAsync(cursor, idx->offsets, (size_t)nk * 4, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && rc == GRIM_OK) {
+            grim::seed_index_kernel<true><<<blocks, 256, 0, s>>>(ref2bit, npos, k, cursor, idx->positions);
+            e = cudaGetLastError();
+        }
+    }
+    if (cursor) cudaFreeAsync(cursor, s);
+    if (e != cudaSuccess || rc != GRIM_OK) {
+        if (e != cudaSuccess) {
+            grim::set_last_cuda_error(e);
+            rc = e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
+        }
+        cudaStreamSynchronize(s);
+        cudaFree(idx->offsets);
+        cudaFree(idx->positions);
+        delete idx;
+        return rc;
+    }
+    *out = idx;
+    return GRIM_OK;
+}
+
+int grim_seed_index_info(const grim_seed_index* idx, int64_t* len, int* k, const uint32_t** offsets,
+                         const uint32_t** positions) {
+    if (!idx) return GRIM_EINVAL;
+    if (len) *len = idx->len;
+    if (k) *k = idx->k;
+    if (offsets) *offsets = idx->offsets;
+    if (positions) *positions = idx->positions;
+    return GRIM_OK;
+}
+
+int grim_seed_index_free(grim_seed_index* idx) {
+    if (!idx) return GRIM_OK;
+    cudaDeviceSynchronize();
+    cudaFree(idx->offsets);
+    cudaFree(idx->positions);
+    delete idx;
+    return GRIM_OK;
+}
+
+int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const int64_t* read_offsets,
+                         int64_t n_reads, int bin_len, int64_t n_bins, int cap, uint32_t* cand_bins,
+                         int64_t capacity, int64_t* cand_offsets, int64_t* n_cands, void* stream) {
+    if (!idx || n_reads < 0 || bin_len < 1 || n_bins < 1 || n_bins > (int64_t)0xFFFFFFFFll || cap < 1 ||
+        capacity < 0 || !cand_offsets || !n_cands || (capacity > 0 && !cand_bins))
+        return GRIM_EINVAL;
+    *n_cands = 0;
+    if (n_reads > 0 && (!reads || !read_offsets)) return GRIM_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != idx->device) return GRIM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_reads == 0) return grim::exclusive_scan<int64_t>(nullptr, cand_offsets, 0, 0, s);
+
+    const int threads = 256;
+    const int64_t warp_blocks = (n_reads * 32 + threads - 1) / threads;
+    const unsigned blocks = (unsigned)(warp_blocks < 65535 ? warp_blocks : 65535);
+    int64_t* hit_off = nullptr;
+    int64_t* info = nullptr;  // batch bounds
+    GRIM_CUDA_TRY(cudaMallocAsync((void**)&hit_off, (size_t)(n_reads + 1) * 8, s));
+    GRIM_CUDA_TRY(cudaMallocAsync((void**)&info, 64, s));
+    int rc = GRIM_OK;
+    grim::seed_hits_kernel<<<blocks, threads, 0, s>>>(idx->offsets, idx->k, reads, read_offsets, n_reads, hit_off);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(hit_off, hit_off, n_reads, 0, s);
+
+    const int64_t kBudget = int64_t(1) << 28;     // votes per batch
+    const int64_t kMaxReads = int64_t(1) << 20;   // reads per batch
+    int64_t total = 0;
+    for (int64_t r0 = 0; r0 < n_reads && e == cudaSuccess && rc == GRIM_OK;) {
+        int64_t b[3];
+        grim::batch_end_kernel<<<1, 1, 0, s>>>(hit_off, n_reads, r0, kBudget, kMaxReads, info);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b, info, sizeof(b), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        const int64_t h0 = b[0], r1 = b[1], votes = b[2] - b[0], nb = r1 - r0;
+        uint32_t* H = nullptr;
+        unsigned long long* S = nullptr;
+        int64_t* kept = nullptr;
+        e = cudaMallocAsync((void**)&H, (size_t)(votes > 0 ? votes : 1) * 4, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&S, (size_t)(votes > 0 ? votes : 1) * 8, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&kept, (size_t)nb * 8, s);
+        if (e == cudaSuccess) {
+            const int64_t wb = (nb * 32 + threads - 1) / threads;
+            const unsigned bb = (unsigned)(wb < 65535 ? wb : 65535);
+            if (votes > 0)
+                grim::seed_expand_kernel<<<bb, threads, 0, s>>>(idx->offsets, idx->positions, idx->k, reads,
+                                                                 read_offsets + r0, nb, hit_off + r0, h0,
+                                                                 (uint32_t)bin_len, (uint32_t)(n_bins - 1), H);
+            grim::seed_dedupe_kernel<<<(unsigned)nb, grim::kDedupThreads, 0, s>>>(hit_off + r0, h0, cap, H, S, kept);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(kept, cand_offsets + r0, nb, total, s);
+            int64_t t_end = total;
+            if (e == cudaSuccess && rc == GRIM_OK)
+                e = cudaMemcpyAsync(&t_end, cand_offsets + r1, 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && rc == GRIM_OK) {
+                grim::seed_copy_kernel<<<bb, threads, 0, s>>>(H, hit_off + r0, h0, cand_offsets + r0, nb, cand_bins,
+                                                              capacity);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            total = t_end;
+        }
+        if (H) cudaFreeAsync(H, s);
+        if (S) cudaFreeAsync(S, s);
+        if (kept) cudaFreeAsync(kept, s);
+        r0 = r1;
+    }
+    cudaFreeAsync(hit_off, s);
+    cudaFreeAsync(info, s);
+    if (e != cudaSuccess) {
+        grim::set_last_cuda_error(e);
+        return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
+    }
+    if (rc != GRIM_OK) return rc;
+    *n_cands = total;
+    return total > capacity ? GRIM_EOVERFLOW : GRIM_OK;
+}
+
+int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* cand_bins,
+                const int64_t* cand_offsets, int64_t n_reads, int64_t n_cands, const uint8_t* pass,
+                uint32_t* loc_read, uint32_t* loc_bin, int64_t* loc_begin, int64_t* loc_end, uint8_t* segments,
+                int64_t seg_stride, int64_t capacity, int64_t* n_loc, void* stream) {
+    if (!bank || n_reads < 0 || n_cands < 0 || capacity < 0 || !n_loc || !cand_offsets) return GRIM_EINVAL;
+    if (n_cands > 0 && (!cand_bins || !pass)) return GRIM_EINVAL;
+    if (capacity > 0 && (!loc_read || !loc_bin || !loc_begin || !loc_end)) return GRIM_EINVAL;
+    if (segments && (seg_stride <= 0 || !ref2bit)) return GRIM_EINVAL;
+    if (n_cands > 0 && n_reads == 0) return GRIM_EINVAL;
+    int rc = grim::check_device(bank);
+    if (rc != GRIM_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_cands == 0) return grim::exclusive_scan<int64_t>(nullptr, n_loc, 0, 0, s);
+    const int64_t tiles = (n_cands + grim::kLocTile - 1) / grim::kLocTile;
+    int64_t* counts = nullptr;
+    GRIM_CUDA_TRY(cudaMallocAsync((void**)&counts, (size_t)(tiles + 1) * 8, s));
+    grim::locate_count_kernel<<<(unsigned)tiles, grim::kScanThreads, 0, s>>>(pass, n_cands, counts);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(counts, counts, tiles, 0, s);
+    if (e == cudaSuccess && rc == GRIM_OK)
+        e = cudaMemcpyAsync(n_loc, counts + tiles, 8, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && rc == GRIM_OK) {
+        grim::locate_write_kernel<<<(unsigned)tiles, grim::kScanThreads, 0, s>>>(
+            pass, cand_bins, cand_offsets, n_reads, n_cands, counts, bank->len, bank->n_bins, bank->bin_len,
+            bank->overlap, capacity, loc_read, loc_bin, loc_begin, loc_end, bank->status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && rc == GRIM_OK && segments && capacity > 0) {
+        grim::locate_segments_kernel<<<grim::sm_count() * 8, 256, 0, s>>>(ref2bit, n_loc, capacity, loc_begin,
+                                                                          loc_end, segments, seg_stride);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(counts, s);
+    if (e != cudaSuccess) {
+        grim::set_last_cuda_error(e);
+        return GRIM_ECUDA;
+    }
+    return rc;
+}
+
+}  // extern "C"
