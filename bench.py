@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched sub-measurement")
     ap.add_argument("--no-full-scan", action="store_true", help="skip the full-scan sub-measurement")
     ap.add_argument("--no-mixed", action="store_true", help="skip the dispatcher (mixed) sub-measurement")
-    ap.add_argument("--mixed-reads", type=int, default=65_536)
+    ap.add_argument("--mixed-reads", type=int, default=10_000_000)
     return ap.parse_args()
 
 
@@ -168,10 +168,12 @@ def make_fullscan(args, rank):
                           read_seed=synth.SEED_READS + 1000 * rank)
 
 
-def make_mixed(args, rank):
+def make_mixed(args, rank, cand_reads=0):
+    """Candidates come from the GPU seed table; cand_reads > 0 also builds
+    CPU lists for the first reads (the oracle's sample)."""
     import synth
     return synth.mixed_seeds(ref_len=args.scan_ref_bp, n_reads=args.mixed_reads,
-                             read_seed=synth.SEED_READS + 1000 * rank)
+                             read_seed=synth.SEED_READS + 1000 * rank, cand_reads=cand_reads)
 
 
 def describe(form, w):
@@ -194,12 +196,13 @@ def describe(form, w):
                              f"log-uniform 1-5000 candidates (mean {w.n_checks / w.n_reads:.0f})",
                     checks_per_gpu_step=w.n_checks)
     elif form == "mixed":
-        c = np.diff(w.cand_offsets)
         base.update(workload=f"dispatcher, {w.ref_len / 1e9:g} Gbp reference ({rep} at 5-20% divergence), q={w.q}, "
                              f"{w.n_reads} x {int(L[0])} bp reads/GPU, 12-mer seed candidates (cap 10000), "
-                             f"gather vs full scan chosen per batch",
-                    checks_per_gpu_step=w.n_checks, cands_per_read_mean=round(float(c.mean()), 2),
-                    cands_per_read_max=int(c.max()))
+                             f"gather vs full scan chosen per batch")
+        if w.cand_offsets is not None and len(w.cand_offsets) == w.n_reads + 1:
+            c = np.diff(w.cand_offsets)
+            base.update(checks_per_gpu_step=w.n_checks, cands_per_read_mean=round(float(c.mean()), 2),
+                        cands_per_read_max=int(c.max()))
     else:
         base.update(workload=f"full scan, {w.ref_len / 1e9:g} Gbp repeat-rich reference ({rep}), q={w.q}, "
                              f"{w.n_bins} bins, batch of {w.n_reads} x {int(L[0])} bp reads/GPU, every bin",
@@ -315,12 +318,33 @@ def run_form(form, args, ctx, primary):
 
     out = {"form": form}
     if form == "mixed":
-        ins = [dev(w.bases), dev(w.read_offsets), dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)]
-        pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
+        # the mapper's side of the filter on the GPU: seed table, candidates,
+        # then the dispatcher over every read, then the Seed Location Checker
+        torch.cuda.empty_cache()  # the library allocates from the CUDA pool, not torch's cache
+        ref_d = dev(w.ref2bit)
+        reads_d, offs_d, E_d = dev(w.bases), dev(w.read_offsets), dev(w.E)
+        s.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            idx = grim.grim_seed_index_build(ref_d, w.ref_len, w.meta["seed_k"], stream=s)
+        s.synchronize()
+        index_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            cb_d, co_d = grim.grim_seed_candidates(idx, reads_d, offs_d, w.bin_len, w.n_bins, w.meta["cap"],
+                                                   capacity=w.n_reads * 2048, stream=s)
+        s.synchronize()
+        cand_s = time.perf_counter() - t0
+        del ref_d
+        n_checks = int(cb_d.numel())
+        launches = -(-w.n_reads // 262144)
+        per_read = torch.diff(co_d)
+        ins = [reads_d, offs_d, cb_d, co_d, E_d]
+        pass_d = torch.empty(n_checks, dtype=torch.uint8, device="cuda")
         with torch.cuda.stream(s):
             tune = grim.grim_autotune(bank, *ins, pass_out=pass_d, stream=s)
         s.synchronize()
-        choice = grim.grim_choose_form(bank, w.n_reads, w.n_checks)
+        choice = grim.grim_choose_form(bank, w.n_reads, n_checks)
         scanned = []
 
         def call():
@@ -330,43 +354,62 @@ def run_form(form, args, ctx, primary):
         ms, clk = ctx.timed(call, steps, warmup, clocks=primary)
         ms_g, _ = ctx.timed(lambda: grim.grim_filter_batched(bank, *ins, pass_out=pass_d, tune=tune, stream=s),
                             args.sub_steps, 1)
-        res = grim.grim_scan(bank, ins[0], ins[1], ins[4], cap=1 << 24, stream=s)
-        ms_s, _ = ctx.timed(lambda: grim.grim_scan(bank, ins[0], ins[1], ins[4], out=res, stream=s), 1, 1)
+        nb = min(w.n_reads, 65_536)  # the full scan is timed on one batch of reads
+        scan_ins = (reads_d, offs_d[:nb + 1], E_d[:nb])
+        res = grim.grim_scan(bank, *scan_ins, cap=1 << 24, stream=s)
+        ms_s, _ = ctx.timed(lambda: grim.grim_scan(bank, *scan_ins, out=res, stream=s), 1, 1)
+        n_pass = int(torch.count_nonzero(pass_d).item())
+        ms_l, _ = ctx.timed(lambda: grim.grim_locate(bank, cb_d, co_d, pass_d, capacity=n_pass, stream=s), 1, 1)
+        loc = grim.grim_locate(bank, cb_d, co_d, pass_d, capacity=n_pass, stream=s)
         st, flags = grim.grim_bank_status(bank, s)
         assert st == grim.GRIM_OK, (st, flags)
-        units = w.n_checks
-        launches = -(-w.n_reads // 262144)
-        alg = gather_bytes(w, row)
-        peak, peak_kind = load_peaks()
+        units = n_checks
         avg = float(np.mean(ms))
-        g, sc = float(np.mean(ms_g)), float(np.mean(ms_s))
+        g, sc, lc = float(np.mean(ms_g)), float(np.mean(ms_s)), float(np.mean(ms_l))
+        alg = n_checks * (row + 4 + 1) + int(w.read_offsets[-1]) + (w.n_reads + 1) * 16 + w.n_reads * 2
+        peak, peak_kind = load_peaks()
         roof = {"bound": "hbm", "achieved": alg / (avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                 "frac": alg / (avg / 1e3) / 1e9 / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
                 "kernel": "dispatcher -> gather_kernel<5,8>", "avg_step_ms": avg}
+        out["config_extra"] = {"checks_per_gpu_step": n_checks,
+                               "cands_per_read_mean": round(n_checks / w.n_reads, 2),
+                               "cands_per_read_max": int(per_read.max().item()),
+                               "candidates": "GPU seed table + grim_seed_candidates (12-mer seeds, cap 10000)"}
         out["dispatch"] = {"choice": "scan" if choice == grim.GRIM_FORM_SCAN else "gather",
                            "reads_scanned_per_step": scanned[-1] if scanned else 0}
         out["gather_form"] = {"ms_per_step": g, "checks_per_s": units / (g / 1e3), "reads_per_s": w.n_reads / (g / 1e3)}
-        out["scan_form"] = {"ms_per_step": sc, "checks_per_s_all_bins": w.n_reads * w.n_bins / (sc / 1e3),
-                            "reads_per_s": w.n_reads / (sc / 1e3), "pairs_passing": res.n_pairs}
-        out["pass_rate"] = float(pass_d.float().mean().item())
+        out["scan_form"] = {"ms_per_batch": sc, "batch_reads": nb,
+                            "checks_per_s_all_bins": nb * w.n_bins / (sc / 1e3), "reads_per_s": nb / (sc / 1e3),
+                            "pairs_passing": res.n_pairs,
+                            "note": "one batch of reads timed; the dispatcher's choice runs every read"}
+        out["seed_pipeline"] = {"seed_table_s": index_s, "candidates_s": cand_s,
+                                "candidates_reads_per_s": w.n_reads / cand_s, "locate_ms": lc,
+                                "locations_passing": loc.n,
+                                "reads_per_s_serial": w.n_reads / (cand_s + avg / 1e3 + lc / 1e3)}
+        out["pass_rate"] = n_pass / max(1, n_checks)
+        del loc, res, ins, cb_d, co_d  # the end-to-end steps make their own candidate lists
         if primary:
-            h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.cand_bins), ctx.pin(w.cand_offsets),
-                    ctx.pin(w.E)]
-            h_out = torch.empty(w.n_checks, dtype=torch.uint8).pin_memory()
+            # end to end through the public calls: reads in from pinned host
+            # memory, candidates, filter, pass bytes back
+            h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.E)]
+            h_out = torch.empty(n_checks, dtype=torch.uint8).pin_memory()
 
             def e2e_step():
-                for h, d in zip(h_in, ins):
+                for h, d in zip(h_in, (reads_d, offs_d, E_d)):
                     d.copy_(h, non_blocking=True)
-                call()
+                cb2, co2 = grim.grim_seed_candidates(idx, reads_d, offs_d, w.bin_len, w.n_bins, w.meta["cap"],
+                                                     capacity=n_checks, stream=s)
+                grim.grim_filter_auto(bank, reads_d, offs_d, cb2, co2, E_d, pass_out=pass_d, stream=s)
                 h_out.copy_(pass_d, non_blocking=True)
 
             e2e_ms, _ = ctx.timed(e2e_step, steps, warmup)
             out["e2e"] = {"value": units * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3), "unit": UNIT,
                           "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
-                          "d2h_bytes_per_step": h_out.numel()}
-            if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
-                out["cpu_baseline"] = cpu_baseline_rows(w, args.cpu_seconds)
-        del ins, pass_d, res
+                          "d2h_bytes_per_step": h_out.numel(),
+                          "includes": "seed candidates on the GPU (synchronising), dispatcher, pass bytes to host"}
+        idx.free()
+        del pass_d, reads_d, offs_d, E_d
+        torch.cuda.empty_cache()
     elif form in ("gather", "batched"):
         ins = [dev(w.bases), dev(w.read_offsets), dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)]
         pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
@@ -474,6 +517,7 @@ def run_form(form, args, ctx, primary):
                 "reads_per_s": w.n_reads * ctx.world * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
                 "steps": steps, "roofline": roof, "gpu_launches": launches * steps, "clocks": clk,
                 "bank_build": bank_info, "config": describe(form, w)})
+    out["config"].update(out.pop("config_extra", {}))
     bank.free()
     del w
     torch.cuda.synchronize()
@@ -567,7 +611,7 @@ def run_reference(args):
 
         sample = f"first n reads x first {nb} bins per step"
     elif args.workload == "mixed":
-        w = make_mixed(args, 0)
+        w = make_mixed(args, 0, cand_reads=4096)
 
         def step(n):
             t = time.perf_counter()
@@ -593,7 +637,8 @@ def run_reference(args):
 
         sample = "first n reads per step"
     dt, _ = step(16)
-    n = min(w.n_reads, max(16, int(16 * per_step / max(dt, 1e-6))))
+    n_max = w.n_reads if w.cand_offsets is None else len(w.cand_offsets) - 1
+    n = min(n_max, max(16, int(16 * per_step / max(dt, 1e-6))))
     for _ in range(args.warmup):
         step(n)
     times, units = [], 0

@@ -418,6 +418,7 @@ def grim_locate(bank: Bank, cand_bins: torch.Tensor, cand_offsets: torch.Tensor,
                               _dev_ptr(be, "loc_begin", 8), _dev_ptr(en, "loc_end", 8),
                               _dev_ptr(seg, "segments", 1, True), seg_stride, capacity,
                               _dev_ptr(n_loc, "n_loc", 8), _stream_ptr(stream)), "grim_locate")
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
     n = int(n_loc.item())
     m = min(n, capacity)
     return Located(rd[:m], bn[:m], be[:m], en[:m], seg[:m] if seg is not None else None, n)

@@ -11,10 +11,11 @@
 //     max(0, p - o); distinct bins are kept, the `cap` most voted when
 //     there are more (equal votes: the lower bin), ascending.  Per batch of
 //     reads: hits per read (warp per read) -> prefix sum -> votes expanded
-//     into scratch -> one CTA per read sorts its votes (bitonic, in shared
-//     memory up to kDedupSmem, else in place in global memory), counts the
-//     runs, applies the cap (binary search on the vote threshold) and
-//     compacts -> prefix sum of the kept counts -> copy into the CSR output.
+//     into scratch -> one CTA per read sorts its votes (stable LSD radix
+//     sort, in shared memory up to kDedupSmem votes, else in global
+//     scratch), finds the runs, applies the cap (binary search on the vote
+//     threshold) and compacts -> prefix sum of the kept counts -> copy into
+//     the CSR output.
 // After (Sec. 3.3, Fig. 4 steps 2-3): the Seed Location Checker turns the
 // filter's bitmask into the list of passing locations and the reference
 // segments the aligner receives.
@@ -70,8 +71,8 @@ __device__ T block_exclusive_scan(T v, T* warp_sums, T* total) {
 }
 
 template <typename T>
-__global__ void set_value_kernel(T* p, T v) {
-    *p = v;
+__global__ void set_value_kernel(T* p, T v, const T* v_dev) {
+    *p = v_dev ? *v_dev : v;
 }
 
 // tile sums over the same index sets scan_tiles_kernel uses
@@ -88,11 +89,12 @@ __global__ void tile_sums_kernel(const T* __restrict__ in, int64_t n, T* __restr
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-// one block of 1024 threads: sums[b] <- init + sum of sums[0..b)
+// one block of 1024 threads: sums[b] <- init + sum of sums[0..b), init
+// read from init_dev when that is not null
 template <typename T>
-__global__ void scan_sums_kernel(T* __restrict__ sums, int64_t n_tiles, T init) {
+__global__ void scan_sums_kernel(T* __restrict__ sums, int64_t n_tiles, T init, const T* init_dev) {
     __shared__ T ws[32];
-    T carry = init;
+    T carry = init_dev ? *init_dev : init;
     for (int64_t b = 0; b < n_tiles; b += blockDim.x) {
         const int64_t j = b + threadIdx.x;
         const T v = j < n_tiles ? sums[j] : T(0);
@@ -129,10 +131,11 @@ __global__ void scan_tiles_kernel(const T* in, T* out, int64_t n, const T* __res
 }  // namespace
 
 // out[0..n]: out[i] = init + in[0] + ... + in[i-1]; in == out is allowed.
+// init_dev (nullable) supplies init from device memory (it may be out[0]).
 template <typename T>
-int exclusive_scan(const T* in, T* out, int64_t n, T init, cudaStream_t s) {
+int exclusive_scan(const T* in, T* out, int64_t n, T init, cudaStream_t s, const T* init_dev = nullptr) {
     if (n == 0) {
-        set_value_kernel<T><<<1, 1, 0, s>>>(out, init);
+        set_value_kernel<T><<<1, 1, 0, s>>>(out, init, init_dev);
         GRIM_CUDA_TRY(cudaGetLastError());
         return GRIM_OK;
     }
@@ -140,7 +143,7 @@ int exclusive_scan(const T* in, T* out, int64_t n, T init, cudaStream_t s) {
     T* sums = nullptr;
     GRIM_CUDA_TRY(cudaMallocAsync((void**)&sums, (size_t)tiles * sizeof(T), s));
     tile_sums_kernel<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
-    scan_sums_kernel<T><<<1, 1024, 0, s>>>(sums, tiles, init);
+    scan_sums_kernel<T><<<1, 1024, 0, s>>>(sums, tiles, init, init_dev);
     scan_tiles_kernel<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
     const cudaError_t e = cudaGetLastError();
     cudaFreeAsync(sums, s);
@@ -260,66 +263,104 @@ __global__ void seed_expand_kernel(const uint32_t* __restrict__ idx_off, const u
     }
 }
 
-// Ascending sort of A[0..n) by a bitonic network whose comparators all put
-// the smaller value at the lower index, over the array padded to a power
-// of two with +infinity.  The padding never moves under such comparators,
-// so pairs that reach into it are skipped and it needs no storage.  A is
-// shared or global memory owned by this CTA.
-__device__ void bitonic_sort(uint32_t* A, int64_t n) {
-    int lg = 0;
-    while ((int64_t(1) << lg) < n) lg++;
-    const int64_t half_p = (int64_t(1) << lg) >> 1;
-    for (int s = 1; s <= lg; s++) {
-        // merge blocks of 2^s: first each element against its mirror
-        for (int64_t t = threadIdx.x; t < half_p; t += blockDim.x) {
-            const int64_t blk = t >> (s - 1), off = t & ((int64_t(1) << (s - 1)) - 1);
-            const int64_t i = (blk << s) + off, j = (blk << s) + (int64_t(1) << s) - 1 - off;
-            if (j < n) {
-                const uint32_t x = A[i], y = A[j];
-                if (x > y) {
-                    A[i] = y;
-                    A[j] = x;
-                }
-            }
+constexpr int kDedupThreads = 256;
+constexpr int kDedupSmem = 4096;  // votes sorted in shared memory up to this many
+constexpr int kDedupItems = 8;    // consecutive entries per thread in the run and cap passes
+constexpr int64_t kDedupChunk = (int64_t)kDedupThreads * kDedupItems;
+constexpr int kRadixBits = 4;
+constexpr int kRadixBuckets = 1 << kRadixBits;
+constexpr int kDedupPadded = kDedupSmem + kDedupSmem / 32;
+constexpr size_t kDedupSmemBytes = (2 * (size_t)kDedupPadded + (size_t)kRadixBuckets * kDedupThreads) * 4;
+
+// Shared-memory key arrays get one pad word per 32 so that threads reading
+// consecutive blocks of keys do not collide on a bank.
+template <bool SMEM>
+__device__ __forceinline__ int64_t rx_at(int64_t i) {
+    return SMEM ? i + (i >> 5) : i;
+}
+
+// Stable ascending LSD radix sort of A[0..n) on `passes` (even) digits of
+// kRadixBits, with B as the second buffer; the result ends in A.  Thread t
+// owns the contiguous keys [t * ipt, (t + 1) * ipt) and column t of the
+// bucket-major counters cnt[bucket * 256 + t], so counting and scattering
+// need no atomics and keep equal digits in their original order.
+template <bool SMEM>
+__device__ void radix_sort(uint32_t* A, uint32_t* B, int64_t n, int passes, uint32_t* cnt, uint32_t* ws) {
+    const int t = threadIdx.x;
+    const int64_t ipt = (n + kDedupThreads - 1) / kDedupThreads;
+    const int64_t i0 = t * ipt < n ? t * ipt : n;
+    const int64_t i1 = i0 + ipt < n ? i0 + ipt : n;
+    for (int ps = 0; ps < passes; ps++) {
+        const int shift = ps * kRadixBits;
+        uint32_t* src = (ps & 1) ? B : A;
+        uint32_t* dst = (ps & 1) ? A : B;
+#pragma unroll
+        for (int b = 0; b < kRadixBuckets; b++) cnt[b * kDedupThreads + t] = 0;
+        for (int64_t i = i0; i < i1; i++) cnt[((src[rx_at<SMEM>(i)] >> shift) & (kRadixBuckets - 1)) * kDedupThreads + t]++;
+        __syncthreads();
+        // exclusive scan of the counters in bucket-major order
+        uint4* c4 = reinterpret_cast<uint4*>(cnt) + t * (kRadixBuckets / 4);
+        uint32_t v[kRadixBuckets];
+#pragma unroll
+        for (int q = 0; q < kRadixBuckets / 4; q++) {
+            const uint4 x = c4[q];
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+        }
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < kRadixBuckets; k++) sum += v[k];
+        uint32_t tot;
+        uint32_t run = block_exclusive_scan<uint32_t>(sum, ws, &tot);
+#pragma unroll
+        for (int k = 0; k < kRadixBuckets; k++) {
+            const uint32_t x = v[k];
+            v[k] = run;
+            run += x;
+        }
+#pragma unroll
+        for (int q = 0; q < kRadixBuckets / 4; q++) c4[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        __syncthreads();
+        for (int64_t i = i0; i < i1; i++) {
+            const uint32_t key = src[rx_at<SMEM>(i)];
+            const uint32_t pos = cnt[((key >> shift) & (kRadixBuckets - 1)) * kDedupThreads + t]++;
+            dst[rx_at<SMEM>(pos)] = key;
         }
         __syncthreads();
-        // then half-cleaners of decreasing stride
-        for (int d = s - 2; d >= 0; d--) {
-            for (int64_t t = threadIdx.x; t < half_p; t += blockDim.x) {
-                const int64_t i = ((t >> d) << (d + 1)) + (t & ((int64_t(1) << d) - 1)), j = i + (int64_t(1) << d);
-                if (j < n) {
-                    const uint32_t x = A[i], y = A[j];
-                    if (x > y) {
-                        A[i] = y;
-                        A[j] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
     }
 }
 
-constexpr int kDedupThreads = 256;
-constexpr int kDedupSmem = 8192;  // votes sorted in shared memory up to this many
+// Votes of run j of the sorted votes: starts st[0..u), n votes in all.
+__device__ __forceinline__ uint32_t run_votes(const uint32_t* st, int64_t u, int64_t n, int64_t j) {
+    return (uint32_t)((j + 1 < u ? (int64_t)st[j + 1] : n) - (int64_t)st[j]);
+}
 
-// Block-wide count of S[0..u) entries with votes >= v (packed votes << 32 | bin).
-__device__ int64_t count_votes_at_least(const unsigned long long* S, int64_t u, uint32_t v, int64_t* ws) {
+// Block-wide count of runs with at least v votes.
+__device__ int64_t count_votes_at_least(const uint32_t* st, int64_t u, int64_t n, uint32_t v, int64_t* ws) {
     int64_t c = 0;
-    for (int64_t j = threadIdx.x; j < u; j += blockDim.x) c += (uint32_t)(S[j] >> 32) >= v;
+    for (int64_t j = threadIdx.x; j < u; j += blockDim.x) c += run_votes(st, u, n, j) >= v;
     int64_t total;
     block_exclusive_scan<int64_t>(c, ws, &total);
     return total;
 }
 
-// One CTA per read of the batch: sort its votes, count runs, apply the cap,
-// write the kept bins (ascending) to H[hit_off[r] - h0 ...] and their
-// number to kept[r].  S: scratch of one u64 per vote.
+// One CTA per read of the batch: sort its votes, find the runs, apply the
+// cap, write the kept bins (ascending) to H[hit_off[r] - h0 ...] and their
+// number to kept[r].  S: scratch of 8 bytes per vote, used as 2n u32: run
+// starts from the front; reads sorted in global memory also use the back
+// half as the radix sort's second buffer and build their list after the
+// starts.  `passes`: radix digits covering every bin id (even).
 __global__ void __launch_bounds__(kDedupThreads)
-seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, uint32_t* __restrict__ H,
+seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, int passes, uint32_t* __restrict__ H,
                    unsigned long long* __restrict__ S, int64_t* __restrict__ kept) {
-    __shared__ uint32_t A_s[kDedupSmem];
+    extern __shared__ uint32_t dedupe_smem[];
+    uint32_t* A_s = dedupe_smem;
+    uint32_t* B_s = dedupe_smem + kDedupPadded;
+    uint32_t* cnt = dedupe_smem + 2 * kDedupPadded;
     __shared__ int64_t ws[32];
+    __shared__ uint32_t ws32[32];
     __shared__ unsigned int max_votes;
     const int64_t r = blockIdx.x;
     const int64_t base = hit_off[r] - h0, n = hit_off[r + 1] - hit_off[r];
@@ -327,78 +368,92 @@ seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, uin
         if (threadIdx.x == 0) kept[r] = 0;
         return;
     }
-    uint32_t* A;
-    if (n <= kDedupSmem) {
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) A_s[i] = H[base + i];
+    const bool in_smem = n <= kDedupSmem;
+    uint32_t* st = reinterpret_cast<uint32_t*>(S + base);  // 2n u32 of scratch
+    if (in_smem) {
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) A_s[rx_at<true>(i)] = H[base + i];
         __syncthreads();
-        A = A_s;
+        radix_sort<true>(A_s, B_s, n, passes, cnt, ws32);
     } else {
-        A = H + base;
+        radix_sort<false>(H + base, st + n, n, passes, cnt, ws32);
     }
-    bitonic_sort(A, n);
+    // the sorted votes, read through the layout they were sorted in
+    auto A = [&](int64_t i) -> uint32_t { return in_smem ? A_s[rx_at<true>(i)] : H[base + i]; };
 
-    // runs: first the start of run j goes to S[j], then at each run's end
-    // S[j] <- votes << 32 | bin (the run's own end reads and writes it)
-    unsigned long long* Sr = S + base;
+    // run starts -> st[0..u), kDedupItems consecutive votes per thread
     int64_t u = 0;
-    for (int64_t i0 = 0; i0 < n; i0 += blockDim.x) {
-        const int64_t i = i0 + threadIdx.x;
-        const int64_t f = (i < n && (i == 0 || A[i] != A[i - 1])) ? 1 : 0;
+    for (int64_t c0 = 0; c0 < n; c0 += kDedupChunk) {
+        const int64_t i0 = c0 + (int64_t)threadIdx.x * kDedupItems;
+        uint32_t fl = 0;
+#pragma unroll
+        for (int k = 0; k < kDedupItems; k++) {
+            const int64_t i = i0 + k;
+            if (i < n && (i == 0 || A(i) != A(i - 1))) fl |= 1u << k;
+        }
         int64_t tot;
-        const int64_t ex = block_exclusive_scan<int64_t>(f, ws, &tot);
-        if (f) Sr[u + ex] = (unsigned long long)i;
+        int64_t o = u + block_exclusive_scan<int64_t>(__popc(fl), ws, &tot);
+#pragma unroll
+        for (int k = 0; k < kDedupItems; k++)
+            if ((fl >> k) & 1u) st[o++] = (uint32_t)(i0 + k);
         u += tot;
     }
     __syncthreads();
-    int64_t seen = 0;
-    for (int64_t i0 = 0; i0 < n; i0 += blockDim.x) {
-        const int64_t i = i0 + threadIdx.x;
-        const int64_t f = (i < n && (i == 0 || A[i] != A[i - 1])) ? 1 : 0;
-        int64_t tot;
-        const int64_t ex = block_exclusive_scan<int64_t>(f, ws, &tot);
-        if (i < n && (i == n - 1 || A[i + 1] != A[i])) {
-            const int64_t j = seen + ex + f - 1;  // the run holding i
-            const int64_t votes = i - (int64_t)Sr[j] + 1;
-            Sr[j] = ((unsigned long long)(votes < 0xFFFFFFFFll ? votes : 0xFFFFFFFFll) << 32) | A[i];
-        }
-        seen += tot;
-    }
-    __syncthreads();
 
-    // the cap: keep votes > v_star, and the first `need` (lowest bins) at v_star
-    uint32_t v_star = 0;
-    int64_t need = 0;
-    const bool capped = u > cap;
-    if (capped) {
+    // reads sorted in shared memory write straight to H; the others build
+    // their list in the scratch after the starts, then copy it to H
+    uint32_t* out = in_smem ? H + base : st + u;
+    int64_t n_keep = 0;
+    if (u <= cap) {
+        for (int64_t j = threadIdx.x; j < u; j += blockDim.x) out[j] = A(st[j]);
+        n_keep = u;
+    } else {
+        // the cap: keep votes > v_star, and the first `need` (lowest bins) at v_star
         if (threadIdx.x == 0) max_votes = 0;
         __syncthreads();
-        for (int64_t j = threadIdx.x; j < u; j += blockDim.x) atomicMax(&max_votes, (unsigned)(Sr[j] >> 32));
+        for (int64_t j = threadIdx.x; j < u; j += blockDim.x) atomicMax(&max_votes, run_votes(st, u, n, j));
         __syncthreads();
         uint32_t lo = 1, hi = max_votes;  // count(votes >= lo) >= cap always holds
         while (lo < hi) {
             const uint32_t mid = lo + (hi - lo + 1) / 2;
-            if (count_votes_at_least(Sr, u, mid, ws) >= cap) lo = mid;
+            if (count_votes_at_least(st, u, n, mid, ws) >= cap) lo = mid;
             else hi = mid - 1;
         }
-        v_star = lo;
-        need = cap - count_votes_at_least(Sr, u, v_star + 1, ws);
+        const uint32_t v_star = lo;
+        const int64_t need = cap - count_votes_at_least(st, u, n, v_star + 1, ws);
+        int64_t n_eq = 0;
+        for (int64_t c0 = 0; c0 < u; c0 += kDedupChunk) {
+            const int64_t j0 = c0 + (int64_t)threadIdx.x * kDedupItems;
+            uint32_t gt = 0, eq = 0;
+#pragma unroll
+            for (int k = 0; k < kDedupItems; k++) {
+                const int64_t j = j0 + k;
+                if (j < u) {
+                    const uint32_t v = run_votes(st, u, n, j);
+                    if (v > v_star) gt |= 1u << k;
+                    else if (v == v_star) eq |= 1u << k;
+                }
+            }
+            int64_t tot_eq;
+            int64_t e = n_eq + block_exclusive_scan<int64_t>(__popc(eq), ws, &tot_eq);
+            uint32_t keep = gt;
+#pragma unroll
+            for (int k = 0; k < kDedupItems; k++)
+                if ((eq >> k) & 1u) {
+                    if (e < need) keep |= 1u << k;
+                    e++;
+                }
+            int64_t tot_keep;
+            int64_t o = n_keep + block_exclusive_scan<int64_t>(__popc(keep), ws, &tot_keep);
+#pragma unroll
+            for (int k = 0; k < kDedupItems; k++)
+                if ((keep >> k) & 1u) out[o++] = A(st[j0 + k]);
+            n_eq += tot_eq;
+            n_keep += tot_keep;
+        }
     }
-    // compaction in bin order (A is no longer read, so H may be overwritten)
-    uint32_t* out = H + base;
-    int64_t n_eq = 0, n_keep = 0;
-    for (int64_t j0 = 0; j0 < u; j0 += blockDim.x) {
-        const int64_t j = j0 + threadIdx.x;
-        const unsigned long long x = j < u ? Sr[j] : 0ull;
-        const uint32_t votes = (uint32_t)(x >> 32);
-        const int64_t eq = (j < u && capped && votes == v_star) ? 1 : 0;
-        int64_t tot_eq;
-        const int64_t ex_eq = block_exclusive_scan<int64_t>(eq, ws, &tot_eq);
-        const int64_t keep = (j < u && (!capped || votes > v_star || (eq && n_eq + ex_eq < need))) ? 1 : 0;
-        int64_t tot_keep;
-        const int64_t ex_keep = block_exclusive_scan<int64_t>(keep, ws, &tot_keep);
-        if (keep) out[n_keep + ex_keep] = (uint32_t)x;
-        n_eq += tot_eq;
-        n_keep += tot_keep;
+    if (!in_smem) {
+        __syncthreads();
+        for (int64_t j = threadIdx.x; j < n_keep; j += blockDim.x) H[base + j] = out[j];
     }
     if (threadIdx.x == 0) kept[r] = n_keep;
 }
@@ -419,7 +474,8 @@ __global__ void seed_copy_kernel(const uint32_t* __restrict__ H, const int64_t* 
 }
 
 // next batch [r0, r1): the most reads after r0 whose votes fit `budget`
-// (at least one read), at most max_reads.  out = {hit_off[r0], r1, hit_off[r1]}.
+// (at least one read), at most max_reads.
+// out = {hit_off[r0], r1, hit_off[r1], hit_off[n]}.
 __global__ void batch_end_kernel(const int64_t* __restrict__ hit_off, int64_t n, int64_t r0, int64_t budget,
                                  int64_t max_reads, int64_t* __restrict__ out) {
     const int64_t h0 = hit_off[r0];
@@ -432,19 +488,39 @@ __global__ void batch_end_kernel(const int64_t* __restrict__ hit_off, int64_t n,
     out[0] = h0;
     out[1] = lo;
     out[2] = hit_off[lo];
+    out[3] = hit_off[n];
 }
 
 // ------------------------------------------------------ seed location checker
 
 constexpr int64_t kLocTile = kScanTile;
 
-__global__ void locate_count_kernel(const uint8_t* __restrict__ pass, int64_t n_cands, int64_t* __restrict__ counts) {
+// Nonzero pass bytes among this thread's 16 (bit i = byte t0 + i): one
+// 16-byte load when the bytes are aligned and in range.  A byte b is
+// nonzero iff bit 7 of ((b & 0x7F) + 0x7F) | b is set.
+__device__ __forceinline__ uint32_t pass_mask16(const uint8_t* __restrict__ pass, int64_t t0, int64_t n,
+                                                bool aligned) {
+    uint32_t m = 0;
+    if (aligned && t0 + 16 <= n) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(pass + t0));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t b = (((w[k] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w[k]) & 0x80808080u;
+            m |= (((b >> 7) & 1u) | ((b >> 14) & 2u) | ((b >> 21) & 4u) | ((b >> 28) & 8u)) << (4 * k);
+        }
+        return m;
+    }
+    for (int i = 0; i < kScanItems; i++)
+        if (t0 + i < n && pass[t0 + i]) m |= 1u << i;
+    return m;
+}
+
+__global__ void locate_count_kernel(const uint8_t* __restrict__ pass, int64_t n_cands, bool aligned,
+                                    int64_t* __restrict__ counts) {
     __shared__ int64_t ws[32];
     const int64_t t0 = (int64_t)blockIdx.x * kLocTile + (int64_t)threadIdx.x * kScanItems;
-    int64_t c = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; i++)
-        if (t0 + i < n_cands) c += pass[t0 + i] != 0;
+    const int64_t c = __popc(pass_mask16(pass, t0, n_cands, aligned));
     int64_t total;
     block_exclusive_scan<int64_t>(c, ws, &total);
     if (threadIdx.x == 0) counts[blockIdx.x] = total;
@@ -461,38 +537,39 @@ __device__ __forceinline__ int64_t read_of(const int64_t* __restrict__ co, int64
     return lo;
 }
 
-__global__ void locate_write_kernel(const uint8_t* __restrict__ pass, const uint32_t* __restrict__ cand_bins,
-                                    const int64_t* __restrict__ cand_offsets, int64_t n_reads, int64_t n_cands,
-                                    const int64_t* __restrict__ tile_base, int64_t len, int64_t n_bins, int bin_len,
-                                    int overlap, int64_t capacity, uint32_t* __restrict__ loc_read,
-                                    uint32_t* __restrict__ loc_bin, int64_t* __restrict__ loc_begin,
-                                    int64_t* __restrict__ loc_end, uint32_t* __restrict__ status) {
+__global__ void locate_write_kernel(const uint8_t* __restrict__ pass, bool aligned,
+                                    const uint32_t* __restrict__ cand_bins, const int64_t* __restrict__ cand_offsets,
+                                    int64_t n_reads, int64_t n_cands, const int64_t* __restrict__ tile_base,
+                                    int64_t len, int64_t n_bins, int bin_len, int overlap, int64_t capacity,
+                                    uint32_t* __restrict__ loc_read, uint32_t* __restrict__ loc_bin,
+                                    int64_t* __restrict__ loc_begin, int64_t* __restrict__ loc_end,
+                                    uint32_t* __restrict__ status) {
     __shared__ int64_t ws[32];
     const int64_t t0 = (int64_t)blockIdx.x * kLocTile + (int64_t)threadIdx.x * kScanItems;
-    int64_t c_own = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; i++)
-        if (t0 + i < n_cands) c_own += pass[t0 + i] != 0;
+    uint32_t m = pass_mask16(pass, t0, n_cands, aligned);
     int64_t total;
-    int64_t o = tile_base[blockIdx.x] + block_exclusive_scan<int64_t>(c_own, ws, &total);
+    int64_t o = tile_base[blockIdx.x] + block_exclusive_scan<int64_t>(__popc(m), ws, &total);
     uint32_t flags = 0;
-    for (int i = 0; i < kScanItems; i++) {
+    int64_t r = -1;
+    while (m && o < capacity) {
+        const int i = __ffs(m) - 1;
+        m &= m - 1;
         const int64_t c = t0 + i;
-        if (c >= n_cands || !pass[c]) continue;
-        if (o < capacity) {
-            const uint32_t b = cand_bins[c];
-            int64_t begin = 0, end = 0;
-            if ((int64_t)b < n_bins) {
-                begin = (int64_t)b * bin_len;
-                end = begin + bin_len + overlap < len ? begin + bin_len + overlap : len;
-            } else {
-                flags |= GRIM_FLAG_BAD_BIN;
-            }
-            loc_read[o] = (uint32_t)read_of(cand_offsets, n_reads, c);
-            loc_bin[o] = b;
-            loc_begin[o] = begin;
-            loc_end[o] = end;
+        // the read: one search for the thread's first location, then forward
+        if (r < 0) r = read_of(cand_offsets, n_reads, c);
+        while (r + 1 < n_reads && cand_offsets[r + 1] <= c) r++;
+        const uint32_t b = cand_bins[c];
+        int64_t begin = 0, end = 0;
+        if ((int64_t)b < n_bins) {
+            begin = (int64_t)b * bin_len;
+            end = begin + bin_len + overlap < len ? begin + bin_len + overlap : len;
+        } else {
+            flags |= GRIM_FLAG_BAD_BIN;
         }
+        loc_read[o] = (uint32_t)r;
+        loc_bin[o] = b;
+        loc_begin[o] = begin;
+        loc_end[o] = end;
         o++;
     }
     if (threadIdx.x == 0 && blockIdx.x == 0 && cand_offsets[n_reads] != n_cands) flags |= GRIM_FLAG_BAD_OFFSETS;
@@ -605,55 +682,83 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
     int64_t* hit_off = nullptr;
     int64_t* info = nullptr;  // batch bounds
     GRIM_CUDA_TRY(cudaMallocAsync((void**)&hit_off, (size_t)(n_reads + 1) * 8, s));
-    GRIM_CUDA_TRY(cudaMallocAsync((void**)&info, 64, s));
+    GRIM_CUDA_TRY(cudaMallocAsync((void**)&info, 64, s));  // batch bounds
     int rc = GRIM_OK;
     grim::seed_hits_kernel<<<blocks, threads, 0, s>>>(idx->offsets, idx->k, reads, read_offsets, n_reads, hit_off);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(hit_off, hit_off, n_reads, 0, s);
 
+    // radix digits covering bin ids 0 .. n_bins - 1, rounded up to even
+    int bits = 0;
+    while (bits < 32 && ((n_bins - 1) >> bits) != 0) bits++;
+    const int passes = 2 * ((bits + 2 * grim::kRadixBits - 1) / (2 * grim::kRadixBits));
+    static bool smem_set[64] = {};
+    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
+        GRIM_CUDA_TRY(cudaFuncSetAttribute(grim::seed_dedupe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)grim::kDedupSmemBytes));
+        smem_set[dev] = true;
+    }
     const int64_t kBudget = int64_t(1) << 28;     // votes per batch
     const int64_t kMaxReads = int64_t(1) << 20;   // reads per batch
-    int64_t total = 0;
+    // scratch kept across batches (freeing it would hand it back to the
+    // pool at every synchronisation): votes as u32 (H) and 2 u32 per vote (S)
+    uint32_t* H = nullptr;
+    unsigned long long* S = nullptr;
+    int64_t* kept = nullptr;
+    int64_t cap_votes = 0;
+    if (e == cudaSuccess && rc == GRIM_OK) {
+        const int64_t max_nb = n_reads < kMaxReads ? n_reads : kMaxReads;
+        e = cudaMallocAsync((void**)&kept, (size_t)max_nb * 8, s);
+        if (e == cudaSuccess) {
+            grim::set_value_kernel<int64_t><<<1, 1, 0, s>>>(cand_offsets, 0, nullptr);
+            e = cudaGetLastError();
+        }
+    }
     for (int64_t r0 = 0; r0 < n_reads && e == cudaSuccess && rc == GRIM_OK;) {
-        int64_t b[3];
+        int64_t b[4];
         grim::batch_end_kernel<<<1, 1, 0, s>>>(hit_off, n_reads, r0, kBudget, kMaxReads, info);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(b, info, sizeof(b), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) break;
         const int64_t h0 = b[0], r1 = b[1], votes = b[2] - b[0], nb = r1 - r0;
-        uint32_t* H = nullptr;
-        unsigned long long* S = nullptr;
-        int64_t* kept = nullptr;
-        e = cudaMallocAsync((void**)&H, (size_t)(votes > 0 ? votes : 1) * 4, s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)&S, (size_t)(votes > 0 ? votes : 1) * 8, s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)&kept, (size_t)nb * 8, s);
-        if (e == cudaSuccess) {
-            const int64_t wb = (nb * 32 + threads - 1) / threads;
-            const unsigned bb = (unsigned)(wb < 65535 ? wb : 65535);
-            if (votes > 0)
-                grim::seed_expand_kernel<<<bb, threads, 0, s>>>(idx->offsets, idx->positions, idx->k, reads,
-                                                                 read_offsets + r0, nb, hit_off + r0, h0,
-                                                                 (uint32_t)bin_len, (uint32_t)(n_bins - 1), H);
-            grim::seed_dedupe_kernel<<<(unsigned)nb, grim::kDedupThreads, 0, s>>>(hit_off + r0, h0, cap, H, S, kept);
-            e = cudaGetLastError();
-            if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(kept, cand_offsets + r0, nb, total, s);
-            int64_t t_end = total;
-            if (e == cudaSuccess && rc == GRIM_OK)
-                e = cudaMemcpyAsync(&t_end, cand_offsets + r1, 8, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess && rc == GRIM_OK) {
-                grim::seed_copy_kernel<<<bb, threads, 0, s>>>(H, hit_off + r0, h0, cand_offsets + r0, nb, cand_bins,
-                                                              capacity);
-                e = cudaGetLastError();
-            }
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            total = t_end;
+        if (votes > cap_votes) {
+            // the first batch sizes it for the largest regular batch
+            const int64_t want = votes > kBudget ? votes : (b[3] - h0 < kBudget ? b[3] - h0 : kBudget);
+            if (H) cudaFreeAsync(H, s);
+            if (S) cudaFreeAsync(S, s);
+            H = nullptr;
+            S = nullptr;
+            e = cudaMallocAsync((void**)&H, (size_t)(want > 0 ? want : 1) * 4, s);
+            if (e == cudaSuccess) e = cudaMallocAsync((void**)&S, (size_t)(want > 0 ? want : 1) * 8, s);
+            if (e != cudaSuccess) break;
+            cap_votes = want;
         }
-        if (H) cudaFreeAsync(H, s);
-        if (S) cudaFreeAsync(S, s);
-        if (kept) cudaFreeAsync(kept, s);
+        const int64_t wb = (nb * 32 + threads - 1) / threads;
+        const unsigned bb = (unsigned)(wb < 65535 ? wb : 65535);
+        if (votes > 0)
+            grim::seed_expand_kernel<<<bb, threads, 0, s>>>(idx->offsets, idx->positions, idx->k, reads,
+                                                             read_offsets + r0, nb, hit_off + r0, h0,
+                                                             (uint32_t)bin_len, (uint32_t)(n_bins - 1), H);
+        grim::seed_dedupe_kernel<<<(unsigned)nb, grim::kDedupThreads, grim::kDedupSmemBytes, s>>>(
+            hit_off + r0, h0, cap, passes, H, S, kept);
+        e = cudaGetLastError();
+        // offsets continue from the previous batch's total in cand_offsets[r0]
+        if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(kept, cand_offsets + r0, nb, 0, s, cand_offsets + r0);
+        if (e == cudaSuccess && rc == GRIM_OK) {
+            grim::seed_copy_kernel<<<bb, threads, 0, s>>>(H, hit_off + r0, h0, cand_offsets + r0, nb, cand_bins,
+                                                          capacity);
+            e = cudaGetLastError();
+        }
         r0 = r1;
     }
+    int64_t total = 0;
+    if (e == cudaSuccess && rc == GRIM_OK)
+        e = cudaMemcpyAsync(&total, cand_offsets + n_reads, 8, cudaMemcpyDeviceToHost, s);
+    if (H) cudaFreeAsync(H, s);
+    if (S) cudaFreeAsync(S, s);
+    if (kept) cudaFreeAsync(kept, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFreeAsync(hit_off, s);
     cudaFreeAsync(info, s);
     if (e != cudaSuccess) {
@@ -681,14 +786,15 @@ int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* c
     const int64_t tiles = (n_cands + grim::kLocTile - 1) / grim::kLocTile;
     int64_t* counts = nullptr;
     GRIM_CUDA_TRY(cudaMallocAsync((void**)&counts, (size_t)(tiles + 1) * 8, s));
-    grim::locate_count_kernel<<<(unsigned)tiles, grim::kScanThreads, 0, s>>>(pass, n_cands, counts);
+    const bool aligned = ((uintptr_t)pass & 15) == 0;
+    grim::locate_count_kernel<<<(unsigned)tiles, grim::kScanThreads, 0, s>>>(pass, n_cands, aligned, counts);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(counts, counts, tiles, 0, s);
     if (e == cudaSuccess && rc == GRIM_OK)
         e = cudaMemcpyAsync(n_loc, counts + tiles, 8, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && rc == GRIM_OK) {
         grim::locate_write_kernel<<<(unsigned)tiles, grim::kScanThreads, 0, s>>>(
-            pass, cand_bins, cand_offsets, n_reads, n_cands, counts, bank->len, bank->n_bins, bank->bin_len,
+            pass, aligned, cand_bins, cand_offsets, n_reads, n_cands, counts, bank->len, bank->n_bins, bank->bin_len,
             bank->overlap, capacity, loc_read, loc_bin, loc_begin, loc_end, bank->status);
         e = cudaGetLastError();
     }

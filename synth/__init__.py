@@ -282,21 +282,28 @@ def batched_varlen(ref_len: int = 100_000_000, n_reads: int = 2_000_000, lmin: i
 def mixed_seeds(ref_len: int = 3_100_000_000, n_reads: int = 65_536, L: int = 100, q: int = 5,
                 bin_len: int = 256, overlap: int = 100, E: int = 5, cap: int = 10_000, repeat_frac: float = 0.40,
                 div_lo: float = 0.05, div_hi: float = 0.20, sub: float = 0.03, indel: float = 0.01, seed_k: int = 12,
-                read_seed: int = SEED_READS) -> Workload:
+                read_seed: int = SEED_READS, cand_reads: int | None = None) -> Workload:
     """Genome-scale reference with 40% repeats at 5-20% divergence; 100 bp
     reads; candidates = bins of all exact 12-mer seed hits, capped at
-    10,000 per read (dense for reads from repeat families)."""
+    10,000 per read (dense for reads from repeat families).  cand_reads
+    limits the CPU candidate lists to the first cand_reads reads (0: none;
+    None: every read)."""
     codes = ref_with_repeats(ref_len, SEED_REF + 100, repeat_frac, div_lo=div_lo, div_hi=div_hi)
     off = read_offsets(n_reads, L, L, read_seed)
     bases, starts = reads(codes, off, read_seed, sub, indel)
     n_bins = -(-ref_len // bin_len)
-    idx = seed_index_for_reads(codes, bases, off, seed_k)
-    cb, co = cands_seeds(idx, bases, off, bin_len, n_bins, cap, seed_k)
-    del idx
+    m = n_reads if cand_reads is None else min(cand_reads, n_reads)
+    cb = co = None
+    if m > 0:
+        sub_off = off[:m + 1]
+        sub_bases = bases[:sub_off[-1]]
+        idx = seed_index_for_reads(codes, sub_bases, sub_off, seed_k)
+        cb, co = cands_seeds(idx, sub_bases, sub_off, bin_len, n_bins, cap, seed_k)
+        del idx
     return Workload(f"mixed_seeds_{ref_len}bp_q{q}_L{L}_cap{cap}", codes, pack2bit(codes), q, bin_len, overlap,
                     bases, off, starts, np.full(n_reads, E, dtype=np.uint16), cb, co,
                     {"sub": sub, "indel": indel, "repeat_frac": repeat_frac, "seed_k": seed_k,
-                     "div": [div_lo, div_hi]})
+                     "div": [div_lo, div_hi], "cap": cap})
 
 
 def fullscan(ref_len: int = 3_100_000_000, n_reads: int = 65_536, L: int = 100, q: int = 5,

@@ -91,3 +91,39 @@ def test_dispatch_3gbp_mixed_sampled(oracle):
            if tb[r] in w.cand_bins[w.cand_offsets[r]:w.cand_offsets[r + 1]]]
     assert np.mean(hit) > 0.9
     bank.free()
+
+
+def test_dispatch_3gbp_10m_reads_gpu_candidates_sampled(oracle):
+    """The genome-scale mixed workload at its full 10M x 100 bp reads:
+    candidates from the GPU seed table, the dispatcher over every read;
+    sampled reads' candidate lists against the generator, sampled pass
+    bytes against the oracle's per-check sum."""
+    w = synth.mixed_seeds(n_reads=10_000_000, cand_reads=0)
+    bank = grim.grim_build_bank(dev(w.ref2bit), w.ref_len, w.q, w.bin_len, w.overlap)
+    idx = grim.grim_seed_index_build(dev(w.ref2bit), w.ref_len, 12)
+    reads_d, offs_d = dev(w.bases), dev(w.read_offsets)
+    cb, co = grim.grim_seed_candidates(idx, reads_d, offs_d, w.bin_len, w.n_bins, 10_000,
+                                       capacity=w.n_reads * 2048)
+    idx.free()
+    p, scanned = grim.grim_filter_auto(bank, reads_d, offs_d, cb, co, dev(w.E))
+    assert grim.grim_bank_status(bank) == (grim.GRIM_OK, 0)
+    assert scanned == 0
+    rng = np.random.default_rng(9)
+    sample = np.sort(rng.choice(w.n_reads, 200, replace=False))
+    co_h = host(co, np.int64)
+    sub_off = np.concatenate([[0], np.cumsum(np.diff(w.read_offsets)[sample])]).astype(np.int64)
+    sub_bases = np.concatenate([w.bases[w.read_offsets[r]:w.read_offsets[r + 1]] for r in sample])
+    want_cb, want_co = synth.cands_seeds(synth.seed_index_for_reads(w.codes, sub_bases, sub_off), sub_bases,
+                                         sub_off, w.bin_len, w.n_bins, 10_000)
+    for j, r in enumerate(sample):
+        got = host(cb[co_h[r]:co_h[r + 1]], np.uint32)
+        assert np.array_equal(got, want_cb[want_co[j]:want_co[j + 1]]), r
+    T = (100 - w.q + 1) - w.q * 5
+    checks = rng.integers(0, int(co_h[-1]), 1500)
+    reads_of = np.searchsorted(co_h, checks, side="right") - 1
+    bins = host(cb[torch.as_tensor(checks, device="cuda")], np.uint32)
+    passes = host(p[torch.as_tensor(checks, device="cuda")], np.uint8)
+    for c, r, b, got in zip(checks, reads_of, bins, passes):
+        row = oracle.bin_row(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap, int(b))
+        assert got == int(oracle.sum_one(row, w.q, w.bases[w.read_offsets[r]:w.read_offsets[r + 1]]) >= T), c
+    bank.free()
