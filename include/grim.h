@@ -186,7 +186,9 @@ int grim_choose_form(const grim_bank* bank, int64_t n_reads, int64_t n_checks, i
  * Dispatching filter: grim_filter's pass bytes (no sums), computed batch by
  * batch (batch_reads reads, <= 0: 262,144) with the form grim_choose_form
  * picks.  A scanned batch's passing pairs are joined back onto its
- * candidates on the device, so both forms give the same bytes.  Reads each
+ * candidates on the device, so both forms give the same bytes.  Gathered
+ * batches use the launch shape grim_autotune chose for this bank's q on
+ * this device (the defaults before it has run), without graphs.  Reads each
  * batch's candidate count from the device (synchronising `stream` once per
  * batch) and allocates the scan's working memory with cudaMallocAsync.
  * *n_scanned (host, nullable) receives the number of reads that went

@@ -48,6 +48,16 @@ int check_args(const grim_bank* bank, const uint8_t* reads, const int64_t* read_
 
 }  // namespace
 
+namespace grim {
+// The launch shape grim_filter_batched(tune = NULL) would use for this bank.
+grim_tune tuned_shape(const grim_bank* bank) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (bank->device >= 0 && bank->device < 64 && g_has_tuned[bank->device][bank->q])
+        return g_tuned[bank->device][bank->q];
+    return default_tune();
+}
+}  // namespace grim
+
 extern "C" {
 
 int grim_filter_batched(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,

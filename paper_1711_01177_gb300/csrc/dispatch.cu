@@ -126,7 +126,11 @@ int grim_filter_auto(const grim_bank* bank, const uint8_t* reads, const int64_t*
     if (rc != GRIM_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (batch_reads <= 0) batch_reads = 262144;
-    grim_tune t = {0, 0, 0, 0, batch_reads};
+    // the autotuned shape, launched directly (each batch's pointers differ,
+    // so a graph per batch would only churn the bank's graph cache)
+    grim_tune t = grim::tuned_shape(bank);
+    t.use_graph = 0;
+    t.batch_reads = batch_reads;
     for (int64_t r0 = 0; r0 < n_reads; r0 += batch_reads) {
         const int64_t n = (n_reads - r0) < batch_reads ? (n_reads - r0) : batch_reads;
         int64_t bounds[2];
@@ -176,7 +180,6 @@ int grim_filter_auto(const grim_bank* bank, const uint8_t* reads, const int64_t*
             if (rc != GRIM_OK) return rc;
         }
         if (!done) {
-            t.use_graph = 0;
             rc = grim_filter_batched(bank, reads, read_offsets + r0, n, cand_bins, cand_offsets + r0, E + r0, pass,
                                      nullptr, &t, stream);
             if (rc != GRIM_OK) return rc;

@@ -81,6 +81,10 @@ int launch_gather_batches(const grim_bank* bank, const GatherArgs& a, const grim
 
 size_t scan_scratch_bytes(int q, int64_t n_reads);
 
+// The autotuned launch shape for this bank's q on its device (defaults
+// when grim_autotune has not run).
+grim_tune tuned_shape(const grim_bank* bank);
+
 // Gather rate (checks/s) measured by the autotuner, used by the dispatcher.
 void record_gather_rate(const grim_bank* bank, double checks_per_s);
 int launch_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
