@@ -331,6 +331,49 @@ int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* c
                 uint32_t* loc_read, uint32_t* loc_bin, int64_t* loc_begin, int64_t* loc_end, uint8_t* segments,
                 int64_t seg_stride, int64_t capacity, int64_t* n_loc, void* stream);
 
+/* ---- verification: the aligner's check and the paper's quality metrics -- */
+
+/*
+ * Edit distance of each location's read against its bin's span: the fewest
+ * substitutions, insertions and deletions that turn the read into some
+ * substring of the span [b * bin_len, min(len, b * bin_len + bin_len +
+ * overlap)) (semi-global, Sellers' recurrence; computed with Myers'
+ * bit-vector form).  A location results in a mapping (Sec. 5: locations
+ * that "do not result in a mapping" after alignment count against the
+ * filter) when the distance is <= the read's E.
+ *   bank        geometry of the spans; ref2bit: device, the 2-bit packed
+ *               reference the bank was built from.
+ *   reads, read_offsets, n_reads   as for grim_filter (codes > 3 match
+ *               nothing).
+ *   loc_read, loc_bin   device u32 [n_loc]: the locations (for example the
+ *               outputs of grim_locate).
+ *   dist        device u16 output [n_loc] (distances above 65,534 read
+ *               65,535).
+ * Reads up to 512 bases; a longer read, a read id >= n_reads, a bin id >=
+ * n_bins or decreasing offsets give 65,535 and raise the bank's
+ * GRIM_FLAG_LONG_READ / BAD_OFFSETS / BAD_BIN flag.  Enqueues on `stream`.
+ */
+int grim_verify(const grim_bank* bank, const uint8_t* ref2bit, const uint8_t* reads, const int64_t* read_offsets,
+                int64_t n_reads, const uint32_t* loc_read, const uint32_t* loc_bin, int64_t n_loc, uint16_t* dist,
+                void* stream);
+
+/*
+ * Counts over n locations (device u64 counts[4], overwritten):
+ *   counts[0] passing (pass byte != 0; every location when pass is NULL),
+ *   counts[1] passing without a mapping (dist > E[read]),
+ *   counts[2] rejected,
+ *   counts[3] rejected with a mapping (dist <= E[read]).
+ * The paper's "false negative rate" is counts[1] / counts[0]; its zero-miss
+ * guarantee is counts[3] == 0 (no correct mapping filtered out); with one
+ * location per candidate bin, counts[0] / (reads x n_bins) is the average
+ * read existence of Sec. 6.1.
+ *   pass       device u8 [n] or NULL; dist: device u16 [n] (grim_verify);
+ *   loc_read   device u32 [n]; E: device u16 [n_reads].
+ * Enqueues on `stream`.
+ */
+int grim_verify_stats(const uint8_t* pass, const uint16_t* dist, const uint32_t* loc_read, const uint16_t* E,
+                      int64_t n_reads, int64_t n, unsigned long long* counts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,8 @@ SIGNATURES = {
     "grim_seed_index_free": (_I32, [_P]),
     "grim_seed_candidates": (_I32, [_P, _P, _P, _I64, _I32, _I64, _I32, _P, _I64, _P, ctypes.POINTER(_I64), _P]),
     "grim_locate": (_I32, [_P, _P, _P, _P, _I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _I64, _P, _P]),
+    "grim_verify": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P]),
+    "grim_verify_stats": (_I32, [_P, _P, _P, _P, _I64, _I64, _P, _P]),
 }
 GRIM_FORM_GATHER, GRIM_FORM_SCAN = 0, 1
 
@@ -422,3 +424,35 @@ def grim_locate(bank: Bank, cand_bins: torch.Tensor, cand_offsets: torch.Tensor,
     n = int(n_loc.item())
     m = min(n, capacity)
     return Located(rd[:m], bn[:m], be[:m], en[:m], seg[:m] if seg is not None else None, n)
+
+
+def grim_verify(bank: Bank, ref2bit: torch.Tensor, reads: torch.Tensor, read_offsets: torch.Tensor,
+                loc_read: torch.Tensor, loc_bin: torch.Tensor, dist: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """Semi-global edit distance of each location's read against its bin's
+    span (the aligner's check behind Sec. 5's metrics).  Returns dist (int16
+    holding u16 values)."""
+    n_loc = loc_read.numel()
+    if loc_bin.numel() != n_loc:
+        raise ValueError("loc_read and loc_bin differ in length")
+    if dist is None:
+        dist = torch.empty(n_loc, dtype=torch.int16, device=loc_read.device)
+    _check(load().grim_verify(bank.handle, _dev_ptr(ref2bit, "ref2bit", 1), _dev_ptr(reads, "reads", 1),
+                              _dev_ptr(read_offsets, "read_offsets", 8), read_offsets.numel() - 1,
+                              _dev_ptr(loc_read, "loc_read", 4), _dev_ptr(loc_bin, "loc_bin", 4), n_loc,
+                              _dev_ptr(dist, "dist", 2), _stream_ptr(stream)), "grim_verify")
+    return dist
+
+
+def grim_verify_stats(dist: torch.Tensor, loc_read: torch.Tensor, E: torch.Tensor, pass_: torch.Tensor | None = None,
+                      stream=None) -> dict:
+    """Passing / rejected locations with and without a mapping (Sec. 5):
+    {"passed", "passed_unmapped", "rejected", "rejected_mapped"}; the
+    paper's false negative rate is passed_unmapped / passed."""
+    counts = torch.empty(4, dtype=torch.int64, device=dist.device)
+    _check(load().grim_verify_stats(_dev_ptr(pass_, "pass", 1, True), _dev_ptr(dist, "dist", 2),
+                                    _dev_ptr(loc_read, "loc_read", 4), _dev_ptr(E, "E", 2), E.numel(), dist.numel(),
+                                    _dev_ptr(counts, "counts", 8), _stream_ptr(stream)), "grim_verify_stats")
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+    c = counts.tolist()
+    return {"passed": c[0], "passed_unmapped": c[1], "rejected": c[2], "rejected_mapped": c[3]}
