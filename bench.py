@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-full-scan", action="store_true", help="skip the full-scan sub-measurement")
     ap.add_argument("--no-mixed", action="store_true", help="skip the dispatcher (mixed) sub-measurement")
     ap.add_argument("--mixed-reads", type=int, default=10_000_000)
+    ap.add_argument("--no-q-sweep", action="store_true", help="skip the token-size sweep (q = 4, 5, 6)")
+    ap.add_argument("--q-sweep-reads", type=int, default=262_144)
     return ap.parse_args()
 
 
@@ -387,7 +389,29 @@ def run_form(form, args, ctx, primary):
                                 "locations_passing": loc.n,
                                 "reads_per_s_serial": w.n_reads / (cand_s + avg / 1e3 + lc / 1e3)}
         out["pass_rate"] = n_pass / max(1, n_checks)
-        del loc, res, ins, cb_d, co_d  # the end-to-end steps make their own candidate lists
+        # the paper's metrics (Sec. 5, 6.1): every passing location aligned
+        # against its bin's span; every candidate of the first reads too, to
+        # count misses (rejected locations that map)
+        ref_d = dev(w.ref2bit)
+        ms_v, _ = ctx.timed(lambda: grim.grim_verify(bank, ref_d, reads_d, offs_d, loc.read, loc.bin, stream=s), 1, 1)
+        dist = grim.grim_verify(bank, ref_d, reads_d, offs_d, loc.read, loc.bin, stream=s)
+        st_pass = grim.grim_verify_stats(dist, loc.read, E_d, stream=s)
+        nz = min(w.n_reads, 65_536)
+        nz_c = int(co_d[nz].item())
+        every = grim.grim_locate(bank, cb_d[:nz_c], co_d[:nz + 1], torch.ones(nz_c, dtype=torch.uint8, device="cuda"),
+                                 capacity=nz_c, stream=s)
+        dist_all = grim.grim_verify(bank, ref_d, reads_d, offs_d, every.read, every.bin, stream=s)
+        st_all = grim.grim_verify_stats(dist_all, every.read, E_d, pass_=pass_d[:nz_c], stream=s)
+        out["verification"] = {
+            "false_negative_rate": st_pass["passed_unmapped"] / max(1, st_pass["passed"]),
+            "locations_passing": st_pass["passed"], "passing_without_mapping": st_pass["passed_unmapped"],
+            "average_read_existence": st_pass["passed"] / (w.n_reads * w.n_bins),
+            "verify_ms": float(np.mean(ms_v)), "verify_locations_per_s": st_pass["passed"] / (np.mean(ms_v) / 1e3),
+            "zero_miss_check": {"reads": nz, "candidates": nz_c, "rejected_with_mapping": st_all["rejected_mapped"],
+                                "passing_with_mapping": st_all["passed"] - st_all["passed_unmapped"]},
+            "note": "mapping = semi-global edit distance <= E of the read into the bin's span (grim_verify); "
+                    "false negative rate in the paper's sense: passing locations without a mapping / passing"}
+        del loc, res, ins, cb_d, co_d, dist, dist_all, every, ref_d  # the end-to-end steps make their own lists
         if primary:
             # end to end through the public calls: reads in from pinned host
             # memory, candidates, filter, pass bytes back
@@ -521,6 +545,46 @@ def run_form(form, args, ctx, primary):
     bank.free()
     del w
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def q_sweep(args, ctx):
+    """Token sizes 4-6 on the same 100 Mbp reads and seed candidates (the
+    paper sweeps them in Sec. 6.1): bank size and build time, gather time,
+    checks/s, fraction of HBM and the share of candidates that pass."""
+    import torch
+
+    import paper_1711_01177_gb300 as grim
+    import synth
+    w = synth.gather_seeds(ref_len=args.ref_bp, n_reads=args.q_sweep_reads,
+                           read_seed=synth.SEED_READS + 1000 * ctx.rank + 7)
+    dev, s = ctx.dev, ctx.stream
+    ref_d = dev(w.ref2bit)
+    ins = [dev(w.bases), dev(w.read_offsets), dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)]
+    pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
+    peak, _ = load_peaks()
+    out = {"workload": f"{args.ref_bp / 1e6:g} Mbp repeat-rich reference, {w.n_reads} x 150 bp reads, "
+                       f"12-mer seed candidates ({w.n_checks} checks), E = 7 for every q", "by_q": {}}
+    for q in (4, 5, 6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e0.record(s)
+            bank = grim.grim_build_bank(ref_d, w.ref_len, q, w.bin_len, w.overlap, stream=s)
+            e1.record(s)
+        s.synchronize()
+        ms, _ = ctx.timed(lambda: grim.grim_filter(bank, *ins, pass_out=pass_d, stream=s), args.sub_steps, 2)
+        st, flags = grim.grim_bank_status(bank, s)
+        assert st == grim.GRIM_OK, (st, flags)
+        avg = float(np.mean(ms))
+        row = bank.row_words * 4
+        alg = gather_bytes(w, row)
+        out["by_q"][str(q)] = {"bank_bytes": bank.n_bins * row, "bank_build_ms": e0.elapsed_time(e1),
+                               "ms_per_step": avg, "checks_per_s": w.n_checks / (avg / 1e3),
+                               "hbm_frac": alg / (avg / 1e3) / 1e9 / peak,
+                               "pass_rate": float(pass_d.float().mean().item())}
+        bank.free()
+    del ins, pass_d, ref_d
     torch.cuda.empty_cache()
     return out
 
@@ -680,6 +744,8 @@ def run_ours(args):
         subs["full_scan"] = run_form("fullscan", args, ctx, primary=False)
     if args.workload != "mixed" and not args.no_mixed:
         subs["mixed"] = run_form("mixed", args, ctx, primary=False)
+    if not args.no_q_sweep:
+        subs["q_sweep"] = q_sweep(args, ctx)
     if rank == 0:
         m = main_form
         line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,

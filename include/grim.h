@@ -45,6 +45,7 @@ extern "C" {
 #define GRIM_ETIMEOUT 6  /* a bounded device-side wait ran out */
 #define GRIM_ENOTSUP 7   /* parameters outside what the kernels implement */
 #define GRIM_ESCRATCH 8  /* the request needs more than grim_scan_noalloc's fixed scratch */
+#define GRIM_EIO 9       /* a bank file could not be written, or is not a valid bank file */
 
 /* ---- device status flags (grim_bank_status) --------------------------- */
 #define GRIM_FLAG_BAD_BASE 0x1u    /* a read holds a code > 3 */
@@ -100,6 +101,22 @@ int grim_bank_status(grim_bank* bank, void* stream, uint32_t* flags);
 
 /* Free the bank (synchronises the device first). NULL is a no-op. */
 int grim_bank_free(grim_bank* bank);
+
+/*
+ * Bank files: the bank depends only on the reference and (q, bin_len,
+ * overlap), so it is built once and kept (the paper stores it with the
+ * reference, Sec. 3.1).  The file is a 64-byte header (magic "GRIMBNK1",
+ * geometry, payload size, a 64-bit checksum of the payload) followed by the
+ * rows in their device layout, in the host's byte order.
+ * grim_bank_save synchronises `stream`, then copies the rows out through a
+ * pinned staging buffer; GRIM_EIO if the file cannot be written.
+ * grim_bank_load validates the header and the file size before any device
+ * work, allocates a bank on the current device and fills it; GRIM_EIO for a
+ * file that cannot be read, is not a bank file, has the wrong size or fails
+ * its checksum (no bank is returned then).  Synchronises `stream`.
+ */
+int grim_bank_save(const grim_bank* bank, const char* path, void* stream);
+int grim_bank_load(const char* path, void* stream, grim_bank** out);
 
 /*
  * Gather-form filter: the Filter Bitmask Generator of Sec. 3.3 over a
@@ -330,6 +347,14 @@ int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* c
                 const int64_t* cand_offsets, int64_t n_reads, int64_t n_cands, const uint8_t* pass,
                 uint32_t* loc_read, uint32_t* loc_bin, int64_t* loc_begin, int64_t* loc_end, uint8_t* segments,
                 int64_t seg_stride, int64_t capacity, int64_t* n_loc, void* stream);
+
+/*
+ * The seed location filter bitmask of Sec. 3.3 at one bit per location:
+ * bit i % 32 of bits[i / 32] is 1 iff pass[i] != 0 (device u8 [n] in,
+ * device u32 [ceil(n / 32)] out; the unused high bits of the last word are
+ * 0).  Enqueues on `stream`.
+ */
+int grim_pack_mask(const uint8_t* pass, int64_t n, uint32_t* bits, void* stream);
 
 /* ---- verification: the aligner's check and the paper's quality metrics -- */
 

@@ -17,7 +17,7 @@ from ._build import LIB as _LIB_PATH
 from ._build import build as _build_lib
 
 (GRIM_OK, GRIM_EINVAL, GRIM_EDATA, GRIM_ENOMEM, GRIM_ECUDA, GRIM_EOVERFLOW, GRIM_ETIMEOUT, GRIM_ENOTSUP,
- GRIM_ESCRATCH) = range(9)
+ GRIM_ESCRATCH, GRIM_EIO) = range(10)
 GRIM_SCAN_NOALLOC_SCRATCH_BYTES = 64 << 20
 GRIM_FLAG_BAD_BASE = 0x1
 GRIM_FLAG_BAD_BIN = 0x2
@@ -50,6 +50,9 @@ SIGNATURES = {
     "grim_seed_index_free": (_I32, [_P]),
     "grim_seed_candidates": (_I32, [_P, _P, _P, _I64, _I32, _I64, _I32, _P, _I64, _P, ctypes.POINTER(_I64), _P]),
     "grim_locate": (_I32, [_P, _P, _P, _P, _I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _I64, _P, _P]),
+    "grim_bank_save": (_I32, [_P, ctypes.c_char_p, _P]),
+    "grim_bank_load": (_I32, [ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
+    "grim_pack_mask": (_I32, [_P, _I64, _P, _P]),
     "grim_verify": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P]),
     "grim_verify_stats": (_I32, [_P, _P, _P, _P, _I64, _I64, _P, _P]),
 }
@@ -456,3 +459,26 @@ def grim_verify_stats(dist: torch.Tensor, loc_read: torch.Tensor, E: torch.Tenso
     (stream if stream is not None else torch.cuda.current_stream()).synchronize()
     c = counts.tolist()
     return {"passed": c[0], "passed_unmapped": c[1], "rejected": c[2], "rejected_mapped": c[3]}
+
+
+def grim_bank_save(bank: Bank, path: str, stream=None) -> None:
+    """Write the bank to a file (built once per reference, Sec. 3.1)."""
+    _check(load().grim_bank_save(bank.handle, os.fsencode(path), _stream_ptr(stream)), "grim_bank_save")
+
+
+def grim_bank_load(path: str, stream=None) -> Bank:
+    """A bank read back from grim_bank_save's file onto the current device."""
+    h = ctypes.c_void_p()
+    _check(load().grim_bank_load(os.fsencode(path), _stream_ptr(stream), ctypes.byref(h)), "grim_bank_load")
+    return Bank(h)
+
+
+def grim_pack_mask(pass_: torch.Tensor, bits: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """One bit per location (Sec. 3.3): bit i % 32 of word i / 32 (int32
+    tensor holding u32 words)."""
+    n = pass_.numel()
+    if bits is None:
+        bits = torch.empty(max(1, (n + 31) // 32), dtype=torch.int32, device=pass_.device)
+    _check(load().grim_pack_mask(_dev_ptr(pass_, "pass", 1), n, _dev_ptr(bits, "bits", 4), _stream_ptr(stream)),
+           "grim_pack_mask")
+    return bits[:(n + 31) // 32]

@@ -27,6 +27,57 @@ int sm_count() {
     return cached[dev];
 }
 
+// A bank of the given geometry with unset rows and a cleared status word.
+int new_bank(int64_t len, int q, int bin_len, int overlap, cudaStream_t s, grim_bank** out) {
+    *out = nullptr;
+    if (len < 1 || bin_len < 1 || overlap < 0) return GRIM_EINVAL;
+    if (q < 1 || q > GRIM_MAX_Q) return GRIM_ENOTSUP;
+    const int64_t n_bins = (len + bin_len - 1) / bin_len;
+    if (n_bins > (int64_t)0xFFFFFFFFu) return GRIM_ENOTSUP;
+    const int64_t rw = row_words_for(q);
+    grim_bank* bank = new grim_bank();
+    bank->len = len;
+    bank->n_bins = n_bins;
+    bank->row_words = rw;
+    bank->q = q;
+    bank->bin_len = bin_len;
+    bank->overlap = overlap;
+    if (cudaGetDevice(&bank->device) != cudaSuccess) {
+        delete bank;
+        return GRIM_ECUDA;
+    }
+    const size_t bytes = (size_t)n_bins * (size_t)rw * 4;
+    const size_t tail = ((bytes + 255) & ~(size_t)255);  // status word, then the work counters
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, tail + 256 + 8 * (1 + kGraphCache));
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        delete bank;
+        return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
+    }
+    bank->bits = (uint32_t*)mem;
+    bank->status = (uint32_t*)((char*)mem + tail);
+    bank->counters = (unsigned long long*)((char*)mem + tail + 256);
+    bank->graphs = new std::vector<GraphEntry>();
+    bank->graph_clock = 0;
+    e = cudaMemsetAsync(bank->status, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        delete_bank(bank);
+        return GRIM_ECUDA;
+    }
+    *out = bank;
+    return GRIM_OK;
+}
+
+// Releases a bank that no graph has been captured for (creation failures).
+void delete_bank(grim_bank* bank) {
+    cudaDeviceSynchronize();
+    cudaFree(bank->bits);
+    delete bank->graphs;
+    delete bank;
+}
+
 }  // namespace grim
 
 extern "C" {
@@ -42,6 +93,7 @@ const char* grim_strerror(int status) {
         case GRIM_ETIMEOUT: return "bounded device-side wait ran out";
         case GRIM_ENOTSUP: return "parameters not supported by the kernels";
         case GRIM_ESCRATCH: return "request exceeds the fixed scratch of the allocation-free scan";
+        case GRIM_EIO: return "bank file could not be written or is not a valid bank file";
         default: return "unknown status";
     }
 }
@@ -52,50 +104,14 @@ int grim_build_bank(const uint8_t* ref2bit, int64_t len, int q, int bin_len, int
                     grim_bank** out) {
     if (!out) return GRIM_EINVAL;
     *out = nullptr;
-    if (!ref2bit || len < 1 || bin_len < 1 || overlap < 0) return GRIM_EINVAL;
-    if (q < 1 || q > GRIM_MAX_Q) return GRIM_ENOTSUP;
-    const int64_t n_bins = (len + bin_len - 1) / bin_len;
-    if (n_bins > (int64_t)0xFFFFFFFFu) return GRIM_ENOTSUP;
-    const int64_t rw = grim::row_words_for(q);
+    if (!ref2bit) return GRIM_EINVAL;
+    grim_bank* bank = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
-
-    grim_bank* bank = new grim_bank();
-    bank->len = len;
-    bank->n_bins = n_bins;
-    bank->row_words = rw;
-    bank->q = q;
-    bank->bin_len = bin_len;
-    bank->overlap = overlap;
-    if (cudaGetDevice(&bank->device) != cudaSuccess) {
-        delete bank;
-        return GRIM_ECUDA;
-    }
-    const size_t bytes = (size_t)n_bins * (size_t)rw * 4;
-    const size_t tail = ((bytes + 255) & ~(size_t)255);  // status word, then the work counters
-    void* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, tail + 256 + 8 * (1 + grim::kGraphCache));
-    if (e != cudaSuccess) {
-        grim::set_last_cuda_error(e);
-        delete bank;
-        return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
-    }
-    bank->bits = (uint32_t*)mem;
-    bank->status = (uint32_t*)((char*)mem + tail);
-    bank->counters = (unsigned long long*)((char*)mem + tail + 256);
-    bank->graphs = new std::vector<grim::GraphEntry>();
-    bank->graph_clock = 0;
-    int rc = GRIM_OK;
-    e = cudaMemsetAsync(bank->status, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) {
-        grim::set_last_cuda_error(e);
-        rc = GRIM_ECUDA;
-    } else {
-        rc = grim::launch_bank_build(ref2bit, bank, s);
-    }
+    int rc = grim::new_bank(len, q, bin_len, overlap, s, &bank);
+    if (rc != GRIM_OK) return rc;
+    rc = grim::launch_bank_build(ref2bit, bank, s);
     if (rc != GRIM_OK) {
-        cudaFree(mem);
-        delete bank->graphs;
-        delete bank;
+        grim::delete_bank(bank);
         return rc;
     }
     *out = bank;

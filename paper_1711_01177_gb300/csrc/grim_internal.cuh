@@ -46,6 +46,19 @@ struct Geo {
     static constexpr int kRowWords = (kBits / 32) < 4 ? 4 : (kBits / 32);
 };
 
+// 16 bytes as a 16-bit mask of the nonzero ones (bit i = byte i): a byte
+// b is nonzero iff bit 7 of ((b & 0x7F) + 0x7F) | b is set.
+__device__ __forceinline__ uint32_t nonzero_bytes16(const uint4& v) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t b = (((w[k] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w[k]) & 0x80808080u;
+        m |= (((b >> 7) & 1u) | ((b >> 14) & 2u) | ((b >> 21) & 4u) | ((b >> 28) & 8u)) << (4 * k);
+    }
+    return m;
+}
+
 inline int64_t row_words_for(int q) {
     int64_t w = (int64_t(1) << (2 * q)) / 32;
     return w < 4 ? 4 : w;
@@ -56,6 +69,11 @@ void set_last_cuda_error(cudaError_t e);
 
 // Current device must be the bank's device.
 int check_device(const grim_bank* bank);
+
+// A bank of the given geometry (rows unset, status cleared) and its release
+// after a failed creation.
+int new_bank(int64_t len, int q, int bin_len, int overlap, cudaStream_t s, grim_bank** out);
+void delete_bank(grim_bank* bank);
 
 int launch_bank_build(const uint8_t* ref2bit, grim_bank* bank, cudaStream_t stream);
 int launch_gather(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,

@@ -496,21 +496,11 @@ __global__ void batch_end_kernel(const int64_t* __restrict__ hit_off, int64_t n,
 constexpr int64_t kLocTile = kScanTile;
 
 // Nonzero pass bytes among this thread's 16 (bit i = byte t0 + i): one
-// 16-byte load when the bytes are aligned and in range.  A byte b is
-// nonzero iff bit 7 of ((b & 0x7F) + 0x7F) | b is set.
+// 16-byte load when the bytes are aligned and in range.
 __device__ __forceinline__ uint32_t pass_mask16(const uint8_t* __restrict__ pass, int64_t t0, int64_t n,
                                                 bool aligned) {
+    if (aligned && t0 + 16 <= n) return nonzero_bytes16(__ldg(reinterpret_cast<const uint4*>(pass + t0)));
     uint32_t m = 0;
-    if (aligned && t0 + 16 <= n) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(pass + t0));
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint32_t b = (((w[k] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w[k]) & 0x80808080u;
-            m |= (((b >> 7) & 1u) | ((b >> 14) & 2u) | ((b >> 21) & 4u) | ((b >> 28) & 8u)) << (4 * k);
-        }
-        return m;
-    }
     for (int i = 0; i < kScanItems; i++)
         if (t0 + i < n && pass[t0 + i]) m |= 1u << i;
     return m;
