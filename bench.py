@@ -411,7 +411,29 @@ def run_form(form, args, ctx, primary):
                                 "passing_with_mapping": st_all["passed"] - st_all["passed_unmapped"]},
             "note": "mapping = semi-global edit distance <= E of the read into the bin's span (grim_verify); "
                     "false negative rate in the paper's sense: passing locations without a mapping / passing"}
-        del loc, res, ins, cb_d, co_d, dist, dist_all, every, ref_d  # the end-to-end steps make their own lists
+        del loc, res, ins, cb_d, co_d, dist, dist_all, every  # the end-to-end steps make their own lists
+        torch.cuda.empty_cache()
+        # the whole path around the filter, alignment overlapping the next
+        # batch's filtering (grim_map, 1M-read batches): once to warm, once timed
+        align = torch.cuda.Stream()
+        cap_loc = int(n_pass * 1.25) + 1024
+        with torch.cuda.stream(s):
+            grim.grim_map(bank, idx, ref_d, reads_d, offs_d, E_d, cap=w.meta["cap"], batch_reads=1 << 20,
+                          capacity=cap_loc, stream=s, align_stream=align)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            mp = grim.grim_map(bank, idx, ref_d, reads_d, offs_d, E_d, cap=w.meta["cap"], batch_reads=1 << 20,
+                               capacity=cap_loc, stream=s, align_stream=align)
+        torch.cuda.synchronize()
+        map_s = time.perf_counter() - t0
+        serial_s = cand_s + avg / 1e3 + lc / 1e3 + float(np.mean(ms_v)) / 1e3
+        out["seed_pipeline"].update({"overlapped_s": map_s, "overlapped_reads_per_s": w.n_reads / map_s,
+                                     "serial_sum_s": serial_s, "overlapped_locations": mp.n,
+                                     "overlapped_mapped": int(((mp.dist.to(torch.int32) & 0xFFFF) <= (
+                                         E_d.to(torch.int32) & 0xFFFF)[mp.read.long()]).sum().item())})
+        del mp, ref_d
+        torch.cuda.empty_cache()
         if primary:
             # end to end through the public calls: reads in from pinned host
             # memory, candidates, filter, pass bytes back
@@ -546,6 +568,7 @@ def run_form(form, args, ctx, primary):
     del w
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    grim.grim_release_scratch()
     return out
 
 

@@ -16,6 +16,9 @@
  *    caller synchronises before reading outputs or freeing inputs;
  *  - the library never frees or keeps caller memory; the bank is owned by
  *    the library from grim_build_bank until grim_bank_free;
+ *  - working memory (scratch) comes from a stream-ordered memory pool per
+ *    device that the library owns: freed blocks stay cached for later calls
+ *    until grim_release_scratch hands them back to the device;
  *  - every call returns a status code (GRIM_OK = 0).  Host-side argument
  *    checks return GRIM_EINVAL / GRIM_ENOTSUP without enqueuing anything.
  *    Problems found in the DATA on the device (a base code > 3, a bin id
@@ -60,6 +63,10 @@ extern "C" {
 #define GRIM_MAX_READ_LEN 65535    /* so that every sum fits 16 bits */
 
 typedef struct grim_bank grim_bank;
+
+/* Synchronise the current device and return the library pool's cached
+ * scratch memory on it to the device.  Safe to call at any time. */
+int grim_release_scratch(void);
 
 /* Text for a status code (static storage). */
 const char* grim_strerror(int status);
@@ -207,7 +214,7 @@ int grim_choose_form(const grim_bank* bank, int64_t n_reads, int64_t n_checks, i
  * batches use the launch shape grim_autotune chose for this bank's q on
  * this device (the defaults before it has run), without graphs.  Reads each
  * batch's candidate count from the device (synchronising `stream` once per
- * batch) and allocates the scan's working memory with cudaMallocAsync.
+ * batch) and takes the scan's working memory from the library's pool.
  * *n_scanned (host, nullable) receives the number of reads that went
  * through the full scan.
  */
@@ -232,7 +239,7 @@ int grim_filter_auto(const grim_bank* bank, const uint8_t* reads, const int64_t*
  *                       (which may exceed cap).
  *   read_pass           device u32 [n_reads] or NULL: passing bins per read.
  * Token sizes 1..5 (GRIM_ENOTSUP above).  Allocates its scratch with
- * cudaMallocAsync on `stream` and frees it with cudaFreeAsync.
+ * the library's pool, ordered on `stream`, and frees it the same way.
  */
 int grim_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
               const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,
@@ -242,8 +249,8 @@ int grim_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_o
  * grim_scan_noalloc - grim_scan that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they call the filter, for example a
- * process whose device memory is all owned by its own pool allocator (so a
- * cudaMallocAsync from this library could fail or fragment that pool), or
+ * process whose device memory is all owned by its own pool allocator (so an
+ * allocation by this library could fail or compete with that pool), or
  * a service that fixes its device footprint at start-up and must not grow
  * it while serving.  Arguments, outputs and results are those of grim_scan.
  *
@@ -315,7 +322,7 @@ int grim_seed_index_free(grim_seed_index* idx);
  * first `capacity` bins are written; call again with a larger buffer).
  * Unlike the filter entry points this call SYNCHRONISES `stream`: reads are
  * processed in batches whose vote scratch (12 bytes per seed location,
- * cudaMallocAsync) is sized from per-read location counts read back to
+ * library's pool) is sized from per-read location counts read back to
  * the host.
  */
 int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const int64_t* read_offsets,
@@ -332,7 +339,8 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
  *                     cand_offsets[0] = 0, cand_offsets[n_reads] = n_cands).
  *   pass              device u8 [n_cands]: the filter bitmask.
  *   loc_read, loc_bin device u32 outputs, loc_begin, loc_end device int64
- *                     outputs, `capacity` entries each.
+ *                     outputs (each of the two may be NULL: not written;
+ *                     both are needed with segments), `capacity` entries.
  *   segments          device u8 [capacity * seg_stride] or NULL: row i holds
  *                     the base codes of location i's span, then code 4 up
  *                     to seg_stride (a span longer than seg_stride is cut);
@@ -398,6 +406,36 @@ int grim_verify(const grim_bank* bank, const uint8_t* ref2bit, const uint8_t* re
  */
 int grim_verify_stats(const uint8_t* pass, const uint16_t* dist, const uint32_t* loc_read, const uint16_t* E,
                       int64_t n_reads, int64_t n, unsigned long long* counts, void* stream);
+
+/* ---- the mapper's path around the filter, overlapped --------------------- */
+
+/*
+ * Seed candidates -> filter -> Seed Location Checker -> edit distance of
+ * every passing location, over batches of batch_reads reads (<= 0: 2^20),
+ * with the aligner's work on one batch overlapping the filter's work on the
+ * next (Sec. 4.2 / 6.1: alignment proceeds while the Filter Bitmask
+ * Generator moves on, with a double-buffered bitmask between them).  The
+ * filter steps run on `stream`, the distances on `align_stream` (NULL: a
+ * stream created for the call).
+ *   bank, idx, ref2bit   the bank, the seed table (grim_seed_index_build)
+ *                        and the 2-bit reference, of the same reference.
+ *   reads, read_offsets, n_reads (< 2^32), E   as for grim_filter.
+ *   cap                  the candidate cap of grim_seed_candidates.
+ *   loc_read, loc_bin    device u32 outputs, loc_dist device u16 output,
+ *                        `capacity` entries each: every passing location in
+ *                        read order (candidate order within a read) with its
+ *                        semi-global edit distance (grim_verify); a location
+ *                        results in a mapping when loc_dist <= E[read].
+ *   *n_loc               host: the number of passing locations.
+ * Returns GRIM_EOVERFLOW when n_loc > capacity (the first `capacity` are
+ * written).  Synchronises both streams; working memory (library pool): two
+ * candidate slots sized to the largest batch (5 bytes per candidate each),
+ * plus the scratch of the steps it calls.
+ */
+int grim_map(const grim_bank* bank, const grim_seed_index* idx, const uint8_t* ref2bit, const uint8_t* reads,
+             const int64_t* read_offsets, int64_t n_reads, const uint16_t* E, int cap, int64_t batch_reads,
+             uint32_t* loc_read, uint32_t* loc_bin, uint16_t* loc_dist, int64_t capacity, int64_t* n_loc,
+             void* stream, void* align_stream);
 
 #ifdef __cplusplus
 }

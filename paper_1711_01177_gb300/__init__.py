@@ -34,6 +34,7 @@ _P, _I64, _I32, _U32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_u
 SIGNATURES = {
     "grim_strerror": (ctypes.c_char_p, [_I32]),
     "grim_last_cuda_error": (_I32, []),
+    "grim_release_scratch": (_I32, []),
     "grim_build_bank": (_I32, [_P, _I64, _I32, _I32, _I32, _P, ctypes.POINTER(_P)]),
     "grim_bank_info": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "grim_bank_status": (_I32, [_P, _P, ctypes.POINTER(_U32)]),
@@ -54,6 +55,7 @@ SIGNATURES = {
     "grim_bank_load": (_I32, [ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
     "grim_pack_mask": (_I32, [_P, _I64, _P, _P]),
     "grim_verify": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P]),
+    "grim_map": (_I32, [_P, _P, _P, _P, _P, _I64, _P, _I32, _I64, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P, _P]),
     "grim_verify_stats": (_I32, [_P, _P, _P, _P, _I64, _I64, _P, _P]),
 }
 GRIM_FORM_GATHER, GRIM_FORM_SCAN = 0, 1
@@ -98,6 +100,11 @@ def load(path: str | None = None):
             fn.argtypes = args
         _lib = lib
     return _lib
+
+
+def grim_release_scratch() -> None:
+    """Return the library's cached scratch memory on the current device."""
+    _check(load().grim_release_scratch(), "grim_release_scratch")
 
 
 def _check(status: int, what: str):
@@ -482,3 +489,38 @@ def grim_pack_mask(pass_: torch.Tensor, bits: torch.Tensor | None = None, stream
     _check(load().grim_pack_mask(_dev_ptr(pass_, "pass", 1), n, _dev_ptr(bits, "bits", 4), _stream_ptr(stream)),
            "grim_pack_mask")
     return bits[:(n + 31) // 32]
+
+
+class Mapped:
+    """grim_map's outputs: every passing location (read, bin) with its edit
+    distance; `n` = number of passing locations."""
+
+    def __init__(self, read, bin_, dist, n):
+        self.read, self.bin, self.dist, self.n = read, bin_, dist, n
+
+
+def grim_map(bank: Bank, idx: SeedIndex, ref2bit: torch.Tensor, reads: torch.Tensor, read_offsets: torch.Tensor,
+             E: torch.Tensor, cap: int = 10_000, batch_reads: int = 0, capacity: int | None = None, stream=None,
+             align_stream=None) -> Mapped:
+    """Seed candidates -> filter -> Seed Location Checker -> edit distances,
+    batch by batch with alignment overlapping the next batch's filtering
+    (Sec. 4.2 / 6.1).  Synchronises both streams."""
+    n_reads = read_offsets.numel() - 1
+    if capacity is None:
+        capacity = max(1024, n_reads * 64)
+    n = ctypes.c_int64()
+    for _ in range(2):
+        rd = torch.empty(max(capacity, 1), dtype=torch.int32, device=reads.device)
+        bn = torch.empty(max(capacity, 1), dtype=torch.int32, device=reads.device)
+        ds = torch.empty(max(capacity, 1), dtype=torch.int16, device=reads.device)
+        st = load().grim_map(bank.handle, idx.handle, _dev_ptr(ref2bit, "ref2bit", 1), _dev_ptr(reads, "reads", 1),
+                             _dev_ptr(read_offsets, "read_offsets", 8), n_reads, _dev_ptr(E, "E", 2), cap,
+                             batch_reads, _dev_ptr(rd, "loc_read", 4), _dev_ptr(bn, "loc_bin", 4),
+                             _dev_ptr(ds, "loc_dist", 2), capacity, ctypes.byref(n), _stream_ptr(stream),
+                             ctypes.c_void_p(align_stream.cuda_stream) if align_stream is not None else None)
+        if st == GRIM_EOVERFLOW:
+            capacity = n.value
+            continue
+        _check(st, "grim_map")
+        return Mapped(rd[:n.value], bn[:n.value], ds[:n.value], n.value)
+    raise GrimError(GRIM_EOVERFLOW, "grim_map")

@@ -1,5 +1,8 @@
-// Host side of the C ABI: argument checks, bank ownership, status word.
+// Host side of the C ABI: argument checks, bank ownership, status word,
+// the library's scratch pool.
 #include <string.h>
+
+#include <mutex>
 
 #include "grim_internal.cuh"
 
@@ -25,6 +28,41 @@ int sm_count() {
         cached[dev] = n;
     }
     return cached[dev];
+}
+
+// Working memory of the entry points comes from one stream-ordered pool per
+// device, owned by the library, whose release threshold keeps freed blocks
+// cached: the default pool would hand them back to the driver at every
+// synchronisation, and calls that allocate gigabytes of scratch would map
+// them again each time.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+static cudaMemPool_t scratch_pool(int dev) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = scratch_pool(dev);
+    if (!pool) return cudaMallocAsync(p, bytes, s);
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
 // A bank of the given geometry with unset rows and a cleared status word.
@@ -99,6 +137,20 @@ const char* grim_strerror(int status) {
 }
 
 int grim_last_cuda_error(void) { return grim::g_last_cuda_error; }
+
+int grim_release_scratch(void) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GRIM_ECUDA;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(grim::g_pool_mu);
+        if (dev >= 0 && dev < 64) pool = grim::g_pool[dev];
+    }
+    if (!pool) return GRIM_OK;
+    GRIM_CUDA_TRY(cudaDeviceSynchronize());
+    GRIM_CUDA_TRY(cudaMemPoolTrimTo(pool, 0));
+    return GRIM_OK;
+}
 
 int grim_build_bank(const uint8_t* ref2bit, int64_t len, int q, int bin_len, int overlap, void* stream,
                     grim_bank** out) {
@@ -199,7 +251,7 @@ int grim_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_o
     }
     if (!reads || !read_offsets || !E) return GRIM_EINVAL;
     void* scratch = nullptr;
-    GRIM_CUDA_TRY(cudaMallocAsync(&scratch, grim::scan_scratch_bytes(bank->q, n_reads), s));
+    GRIM_CUDA_TRY(grim::scratch_alloc(&scratch, grim::scan_scratch_bytes(bank->q, n_reads), s));
     rc = grim::launch_scan(bank, reads, read_offsets, n_reads, E, bin_begin, bin_end, pair_read, pair_bin, pair_sum,
                            cap, n_pairs, read_pass, scratch, s);
     cudaError_t e = cudaFreeAsync(scratch, s);

@@ -147,7 +147,7 @@ int grim_filter_auto(const grim_bank* bank, const uint8_t* reads, const int64_t*
             while (table_n < 2 * (size_t)cap) table_n <<= 1;
             uint8_t* mem = nullptr;
             const size_t bytes = (size_t)cap * 8 + 256 + table_n * 8;
-            GRIM_CUDA_TRY(cudaMallocAsync((void**)&mem, bytes, s));
+            GRIM_CUDA_TRY(grim::scratch_alloc((void**)&mem, bytes, s));
             uint32_t* pr = (uint32_t*)mem;
             uint32_t* pb = pr + cap;
             int64_t* np_dev = (int64_t*)(mem + (size_t)cap * 8);

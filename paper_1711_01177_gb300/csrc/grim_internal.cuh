@@ -64,6 +64,10 @@ inline int64_t row_words_for(int q) {
     return w < 4 ? 4 : w;
 }
 
+// Stream-ordered working memory from the library's pool on the current
+// device (freed with cudaFreeAsync; kept cached until grim_release_scratch).
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s);
+
 // Records the CUDA error of a failing call for grim_last_cuda_error.
 void set_last_cuda_error(cudaError_t e);
 

@@ -141,7 +141,7 @@ int exclusive_scan(const T* in, T* out, int64_t n, T init, cudaStream_t s, const
     }
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     T* sums = nullptr;
-    GRIM_CUDA_TRY(cudaMallocAsync((void**)&sums, (size_t)tiles * sizeof(T), s));
+    GRIM_CUDA_TRY(grim::scratch_alloc((void**)&sums, (size_t)tiles * sizeof(T), s));
     tile_sums_kernel<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
     scan_sums_kernel<T><<<1, 1024, 0, s>>>(sums, tiles, init, init_dev);
     scan_tiles_kernel<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
@@ -558,8 +558,8 @@ __global__ void locate_write_kernel(const uint8_t* __restrict__ pass, bool align
         }
         loc_read[o] = (uint32_t)r;
         loc_bin[o] = b;
-        loc_begin[o] = begin;
-        loc_end[o] = end;
+        if (loc_begin) loc_begin[o] = begin;
+        if (loc_end) loc_end[o] = end;
         o++;
     }
     if (threadIdx.x == 0 && blockIdx.x == 0 && cand_offsets[n_reads] != n_cands) flags |= GRIM_FLAG_BAD_OFFSETS;
@@ -603,7 +603,7 @@ int grim_seed_index_build(const uint8_t* ref2bit, int64_t len, int k, void* stre
     uint32_t* cursor = nullptr;
     cudaError_t e = cudaMalloc((void**)&idx->offsets, (size_t)(nk + 1) * 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&idx->positions, (size_t)npos * 4);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&cursor, (size_t)nk * 4, s);
+    if (e == cudaSuccess) e = grim::scratch_alloc((void**)&cursor, (size_t)nk * 4, s);
     int rc = GRIM_OK;
     if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, (size_t)nk * 4, s);
     if (e == cudaSuccess) {
@@ -671,8 +671,8 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
     const unsigned blocks = (unsigned)(warp_blocks < 65535 ? warp_blocks : 65535);
     int64_t* hit_off = nullptr;
     int64_t* info = nullptr;  // batch bounds
-    GRIM_CUDA_TRY(cudaMallocAsync((void**)&hit_off, (size_t)(n_reads + 1) * 8, s));
-    GRIM_CUDA_TRY(cudaMallocAsync((void**)&info, 64, s));  // batch bounds
+    GRIM_CUDA_TRY(grim::scratch_alloc((void**)&hit_off, (size_t)(n_reads + 1) * 8, s));
+    GRIM_CUDA_TRY(grim::scratch_alloc((void**)&info, 64, s));  // batch bounds
     int rc = GRIM_OK;
     grim::seed_hits_kernel<<<blocks, threads, 0, s>>>(idx->offsets, idx->k, reads, read_offsets, n_reads, hit_off);
     cudaError_t e = cudaGetLastError();
@@ -698,7 +698,7 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
     int64_t cap_votes = 0;
     if (e == cudaSuccess && rc == GRIM_OK) {
         const int64_t max_nb = n_reads < kMaxReads ? n_reads : kMaxReads;
-        e = cudaMallocAsync((void**)&kept, (size_t)max_nb * 8, s);
+        e = grim::scratch_alloc((void**)&kept, (size_t)max_nb * 8, s);
         if (e == cudaSuccess) {
             grim::set_value_kernel<int64_t><<<1, 1, 0, s>>>(cand_offsets, 0, nullptr);
             e = cudaGetLastError();
@@ -719,8 +719,8 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
             if (S) cudaFreeAsync(S, s);
             H = nullptr;
             S = nullptr;
-            e = cudaMallocAsync((void**)&H, (size_t)(want > 0 ? want : 1) * 4, s);
-            if (e == cudaSuccess) e = cudaMallocAsync((void**)&S, (size_t)(want > 0 ? want : 1) * 8, s);
+            e = grim::scratch_alloc((void**)&H, (size_t)(want > 0 ? want : 1) * 4, s);
+            if (e == cudaSuccess) e = grim::scratch_alloc((void**)&S, (size_t)(want > 0 ? want : 1) * 8, s);
             if (e != cudaSuccess) break;
             cap_votes = want;
         }
@@ -766,8 +766,8 @@ int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* c
                 int64_t seg_stride, int64_t capacity, int64_t* n_loc, void* stream) {
     if (!bank || n_reads < 0 || n_cands < 0 || capacity < 0 || !n_loc || !cand_offsets) return GRIM_EINVAL;
     if (n_cands > 0 && (!cand_bins || !pass)) return GRIM_EINVAL;
-    if (capacity > 0 && (!loc_read || !loc_bin || !loc_begin || !loc_end)) return GRIM_EINVAL;
-    if (segments && (seg_stride <= 0 || !ref2bit)) return GRIM_EINVAL;
+    if (capacity > 0 && (!loc_read || !loc_bin)) return GRIM_EINVAL;
+    if (segments && (seg_stride <= 0 || !ref2bit || !loc_begin || !loc_end)) return GRIM_EINVAL;
     if (n_cands > 0 && n_reads == 0) return GRIM_EINVAL;
     int rc = grim::check_device(bank);
     if (rc != GRIM_OK) return rc;
@@ -775,7 +775,7 @@ int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* c
     if (n_cands == 0) return grim::exclusive_scan<int64_t>(nullptr, n_loc, 0, 0, s);
     const int64_t tiles = (n_cands + grim::kLocTile - 1) / grim::kLocTile;
     int64_t* counts = nullptr;
-    GRIM_CUDA_TRY(cudaMallocAsync((void**)&counts, (size_t)(tiles + 1) * 8, s));
+    GRIM_CUDA_TRY(grim::scratch_alloc((void**)&counts, (size_t)(tiles + 1) * 8, s));
     const bool aligned = ((uintptr_t)pass & 15) == 0;
     grim::locate_count_kernel<<<(unsigned)tiles, grim::kScanThreads, 0, s>>>(pass, n_cands, aligned, counts);
     cudaError_t e = cudaGetLastError();
