@@ -12,11 +12,10 @@
 // One warp per read (grid-stride over reads):
 //   0. the first candidate rows are requested before anything else, so
 //      their latency hides behind the token work;
-//   1. lanes load the read 32 bases at a time; two ballots per 32 bases give
-//      the low and high bits of every base code, and a funnel shift puts the
-//      q bases starting at the lane's position side by side; a per-CTA
-//      table of 4^q entries turns those 2q bits into the token value
-//      (the q-gram window of Sec. 3.2 step 1);
+//   1. each lane packs 4 consecutive bases of a 128-base block (2 bits per
+//      base, first base highest), two shuffles bring it the next 8, and its
+//      4 tokens are shifts and masks of that 12-base window (the q-gram
+//      window of Sec. 3.2 step 1);
 //   2. each token is added to the read's bit-sliced count planes in shared
 //      memory with a carry chain of atomicXor (bit p flips; a bit that was
 //      set carries into plane p+1);
@@ -45,14 +44,13 @@ struct GatherGeo {
     static constexpr int kVPL = kRowWords >= 32 ? 2 : 1;        // vectors per lane per row
     static constexpr int kLPB = kRowVecs / kVPL;               // lanes per row
     static constexpr int kBPS = 32 / kLPB;                     // rows per warp step
-    static constexpr int kTabWords = TokenTable<Q>::kWords;
     static constexpr int kPlaneWords = kPlanes * kRowWords;    // per warp
     static_assert(kLPB >= 1 && kLPB <= 32 && 32 % kBPS == 0, "bad gather geometry");
 };
 
 template <int Q>
 constexpr size_t gather_smem_bytes(int warps = kGatherWarps) {
-    return 4 * ((size_t)GatherGeo<Q>::kTabWords + (size_t)warps * GatherGeo<Q>::kPlaneWords);
+    return 4 * (size_t)warps * GatherGeo<Q>::kPlaneWords;
 }
 
 __device__ __forceinline__ uint32_t and_popc(const uint4& a, const uint4& b) {
@@ -189,12 +187,11 @@ __device__ __forceinline__ void write_constant(int64_t co, int64_t ce, const uin
     }
 }
 
-// Shared-memory set-up of a gather CTA: token table and zeroed count planes.
+// Shared-memory set-up of a gather CTA: zeroed count planes.
 template <int Q>
 __device__ __forceinline__ void gather_cta_setup(uint4* smem, int warps) {
     using G = GatherGeo<Q>;
-    build_token_table<Q>(reinterpret_cast<uint16_t*>(smem));
-    uint32_t* planes_all = reinterpret_cast<uint32_t*>(smem) + G::kTabWords;
+    uint32_t* planes_all = reinterpret_cast<uint32_t*>(smem);
     for (int i = threadIdx.x; i < warps * G::kPlaneWords; i += blockDim.x) planes_all[i] = 0;
     __syncthreads();
 }
@@ -208,8 +205,8 @@ __device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restric
                                             const uint32_t* __restrict__ cand_bins,
                                             const int64_t* __restrict__ cand_offsets,
                                             const uint16_t* __restrict__ E, uint8_t* __restrict__ pass,
-                                            uint16_t* __restrict__ sums, const uint16_t* __restrict__ tab,
-                                            uint32_t* __restrict__ planes, int lane, uint32_t& flags) {
+                                            uint16_t* __restrict__ sums, uint32_t* __restrict__ planes, int lane,
+                                            uint32_t& flags) {
     constexpr int RW = GatherGeo<Q>::kRowWords;
     const uint4* planes4 = reinterpret_cast<const uint4*>(planes);
     const int64_t ro = read_offsets[r], re = read_offsets[r + 1];
@@ -242,7 +239,7 @@ __device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restric
     // 1-2. tokens into bit-sliced count planes
     uint32_t bad_base = 0;
     int top = -1;  // highest plane this lane set
-    for_each_token<Q>(rd, L, lane, tab, bad_base, [&](uint32_t tok) {
+    for_each_token4<Q>(rd, L, lane, bad_base, [&](uint32_t tok) {
         const uint32_t w = tok >> 5, m = 1u << (tok & 31);
         int p = 0;
         while (p < kPlanes) {
@@ -359,8 +356,7 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
         }
     }
     gather_cta_setup<Q>(gather_smem, WARPS);  // ends with a CTA barrier
-    const uint16_t* tab = reinterpret_cast<const uint16_t*>(gather_smem);
-    uint32_t* planes = reinterpret_cast<uint32_t*>(gather_smem) + G::kTabWords + warp * G::kPlaneWords;
+    uint32_t* planes = reinterpret_cast<uint32_t*>(gather_smem) + warp * G::kPlaneWords;
     const int64_t r_end = counter ? n_reads : end_read;
     unsigned long long* next = counter ? counter : &next_read;
 
@@ -372,8 +368,8 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
         if ((int64_t)r0 >= r_end) break;
         const int64_t r1 = (int64_t)r0 + claim < r_end ? (int64_t)r0 + claim : r_end;
         for (int64_t r = (int64_t)r0; r < r1; r++)
-            gather_read<Q>(r, bank, n_bins, reads, read_offsets, cand_bins, cand_offsets, E, pass, sums, tab, planes,
-                           lane, flags);
+            gather_read<Q>(r, bank, n_bins, reads, read_offsets, cand_bins, cand_offsets, E, pass, sums, planes, lane,
+                           flags);
     }
     flags = __reduce_or_sync(kFull, flags);
     if (lane == 0 && flags) atomicOr(status, flags);

@@ -65,4 +65,42 @@ __device__ __forceinline__ void for_each_token(const uint8_t* __restrict__ rd, i
     }
 }
 
+// Calls f(token) on the lane that owns each token position i (i + Q <= L),
+// lane l owning positions 128 b + 4 l .. 128 b + 4 l + 3 of block b.  Each
+// lane packs its 4 bases, 2 bits each with the first base highest; two
+// shuffles bring the next 8 bases (lanes 30 and 31 take them from the next
+// block, loaded one block ahead); the 24-bit window of 12 bases then holds
+// the lane's 4 tokens, each a shift and a mask (Q <= 6).  Whole warp, L
+// warp-uniform.  bad_base collects codes > 3 (the tokens then use the
+// code's low two bits; the caller rejects the read).
+template <int Q, typename F>
+__device__ __forceinline__ void for_each_token4(const uint8_t* __restrict__ rd, int L, int lane, uint32_t& bad_base,
+                                                F&& f) {
+    static_assert(Q >= 1 && Q <= 6, "window of 12 bases");
+    constexpr uint32_t kMask = (1u << (2 * Q)) - 1;
+    auto pack = [&](int p0) -> uint32_t {
+        uint32_t v = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int i = p0 + k;
+            const uint32_t c = i < L ? (uint32_t)__ldg(rd + i) : 0u;
+            bad_base |= (uint32_t)(c > 3u);
+            v = (v << 2) | (c & 3u);
+        }
+        return v;
+    };
+    if (L <= 0) return;
+    uint32_t cur = pack(4 * lane);
+    for (int b0 = 0; b0 < L; b0 += 128) {
+        const uint32_t nxt = b0 + 128 < L ? pack(b0 + 128 + 4 * lane) : 0u;  // warp-uniform condition
+        const uint32_t d1 = __shfl_sync(kFull, lane == 0 ? nxt : cur, (lane + 1) & 31);
+        const uint32_t d2 = __shfl_sync(kFull, lane < 2 ? nxt : cur, (lane + 2) & 31);
+        const uint32_t w = (cur << 16) | (d1 << 8) | d2;  // bases 4l .. 4l + 11 of the block
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (b0 + 4 * lane + k + Q <= L) f((w >> (24 - 2 * (k + Q))) & kMask);
+        cur = nxt;
+    }
+}
+
 }  // namespace grim
