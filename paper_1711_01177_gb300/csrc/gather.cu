@@ -57,6 +57,50 @@ __device__ __forceinline__ uint32_t and_popc(const uint4& a, const uint4& b) {
     return __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
 }
 
+// Carry-save adder over words: bitwise, a + b + c = lo + 2 hi.
+__device__ __forceinline__ void csa(uint32_t& hi, uint32_t& lo, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    hi = (a & b) | (u & c);
+    lo = u ^ c;
+}
+
+// popcount(x AND p0) + 2 popcount(x AND p1) over a lane's 8 words (two
+// 16-byte vectors), p1 only when NP == 2.  Full adders first reduce words
+// of equal weight (Harley-Seal), so 6 popcounts (4 for one plane) replace
+// 16 (8): for rows of 512 bytes the popcount pipe's latency, not issue
+// slots, limits the gather.
+template <int NP>
+__device__ __forceinline__ uint32_t row_sum_csa(const uint4 (&v)[2], const uint4 (&p)[NP][2]) {
+    const uint32_t a0 = v[0].x & p[0][0].x, a1 = v[0].y & p[0][0].y, a2 = v[0].z & p[0][0].z,
+                   a3 = v[0].w & p[0][0].w, a4 = v[1].x & p[0][1].x, a5 = v[1].y & p[0][1].y,
+                   a6 = v[1].z & p[0][1].z, a7 = v[1].w & p[0][1].w;
+    uint32_t c1, s1, c2, s2, c3, s3;
+    csa(c1, s1, a0, a1, a2);
+    csa(c2, s2, a3, a4, a5);
+    csa(c3, s3, s1, s2, a6);
+    if constexpr (NP == 1) {
+        uint32_t d1, s4;
+        csa(d1, s4, c1, c2, c3);
+        return __popc(s3) + __popc(a7) + 2 * __popc(s4) + 4 * __popc(d1);
+    } else {
+        const uint32_t b0 = v[0].x & p[1][0].x, b1 = v[0].y & p[1][0].y, b2 = v[0].z & p[1][0].z,
+                       b3 = v[0].w & p[1][0].w, b4 = v[1].x & p[1][1].x, b5 = v[1].y & p[1][1].y,
+                       b6 = v[1].z & p[1][1].z, b7 = v[1].w & p[1][1].w;
+        // weight 2: c1 c2 c3 b0..b7
+        uint32_t d1, s4, d2, s5, d3, s6, d4, s7, d5, s8;
+        csa(d1, s4, c1, c2, c3);
+        csa(d2, s5, b0, b1, b2);
+        csa(d3, s6, b3, b4, b5);
+        csa(d4, s7, s4, s5, s6);
+        csa(d5, s8, s7, b6, b7);
+        // weight 4: d1..d5
+        uint32_t e1, s9, e2, s10;
+        csa(e1, s9, d1, d2, d3);
+        csa(e2, s10, s9, d4, d5);
+        return __popc(s3) + __popc(a7) + 2 * __popc(s8) + 4 * __popc(s10) + 8 * (__popc(e1) + __popc(e2));
+    }
+}
+
 // The candidate stream of one read.  Step k scores rows k*BPS .. k*BPS+BPS-1
 // (lane group g = lane / LPB takes row k*BPS + g).  Candidate ids arrive in
 // windows of 32 (one per lane, the next window prefetched); rows are
@@ -140,7 +184,9 @@ __device__ __forceinline__ void score_read(Stream<Q>& st, const uint4* __restric
             // score this step's rows
             const uint4 (&v)[G::kVPL] = st.r[t % S::kBufs];
             uint32_t part = 0;
-            if (NP > 0) {
+            if constexpr (NP > 0 && Q >= 6 && G::kVPL == 2) {
+                part = row_sum_csa<NP>(v, pl);
+            } else if (NP > 0) {
 #pragma unroll
                 for (int p = 0; p < (NP > 0 ? NP : 1); p++) {
                     uint32_t q = 0;
