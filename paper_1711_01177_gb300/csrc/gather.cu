@@ -480,7 +480,7 @@ int launch_gather(const grim_bank* bank, const uint8_t* reads, const int64_t* re
                   const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
                   uint16_t* sums, cudaStream_t s) {
     const GatherArgs a{reads, read_offsets, n_reads, cand_bins, cand_offsets, E, pass, sums};
-    const grim_tune t = {kGatherWarps, 1, 0, 0, 0};  // one launch over every read
+    const grim_tune t = {kGatherWarps, 4, 0, 0, 0};  // one launch over every read, 4 reads per claim
     return launch_gather_batches(bank, a, t, nullptr, s);
 }
 
