@@ -43,6 +43,7 @@ SIGNATURES = {
     "grim_scan": (_I32, [_P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P]),
     "grim_scan_noalloc": (_I32, [_P, _P, _P, _I64, _P, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P]),
     "grim_filter_batched": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
+    "grim_filter_host": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _I64, _P]),
     "grim_autotune": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
     "grim_choose_form": (_I32, [_P, _I64, _I64, ctypes.POINTER(_I32)]),
     "grim_filter_auto": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
@@ -524,3 +525,37 @@ def grim_map(bank: Bank, idx: SeedIndex, ref2bit: torch.Tensor, reads: torch.Ten
         _check(st, "grim_map")
         return Mapped(rd[:n.value], bn[:n.value], ds[:n.value], n.value)
     raise GrimError(GRIM_EOVERFLOW, "grim_map")
+
+
+def _host_ptr(t: torch.Tensor, name: str, elem_size: int):
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.element_size() != elem_size:
+        raise ValueError(f"{name} must have {elem_size}-byte elements")
+    return ctypes.c_void_p(t.data_ptr()) if t.numel() else ctypes.c_void_p(ctypes.addressof(_HOST_DUMMY))
+
+
+_HOST_DUMMY = ctypes.create_string_buffer(16)
+
+
+def grim_filter_host(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor, cand_bins: torch.Tensor,
+                     cand_offsets: torch.Tensor, E: torch.Tensor, pass_out: torch.Tensor | None = None,
+                     chunk_reads: int = 0, stream=None) -> torch.Tensor:
+    """grim_filter on host tensors (page-locked for overlapped copies):
+    chunks of reads copied in, filtered and copied out on overlapping
+    streams.  Returns pass_out (host u8); synchronises the stream."""
+    n_reads = read_offsets.numel() - 1
+    if n_reads < 0:
+        raise ValueError("read_offsets needs n_reads + 1 entries")
+    if cand_offsets.numel() != n_reads + 1 or E.numel() != n_reads:
+        raise ValueError("cand_offsets / E sizes do not match read_offsets")
+    if pass_out is None:
+        pass_out = torch.empty(cand_bins.numel(), dtype=torch.uint8)
+    _check(load().grim_filter_host(bank.handle, _host_ptr(reads, "reads", 1), _host_ptr(read_offsets, "read_offsets", 8),
+                                   n_reads, _host_ptr(cand_bins, "cand_bins", 4),
+                                   _host_ptr(cand_offsets, "cand_offsets", 8), _host_ptr(E, "E", 2),
+                                   _host_ptr(pass_out, "pass", 1), chunk_reads, _stream_ptr(stream)),
+           "grim_filter_host")
+    return pass_out

@@ -1,0 +1,144 @@
+// grim_filter from host memory: the reads and candidate lists are copied in,
+// filtered and the pass bytes copied out in chunks of reads, with three
+// streams so that the copies of one chunk overlap the filtering of another.
+//
+// Two device slots.  For chunk k (slot k % 2):
+//   copy-in stream: wait until the filter is done with chunk k - 2 (its
+//     inputs); copy bases, offsets, candidate bins, E; record "in(slot)";
+//   filter stream (the caller's): wait "in(slot)" and until chunk k - 2's
+//     pass bytes have left (the slot's output); rebase the chunk's offsets
+//     to the slot; gather; record "done(slot)";
+//   copy-out stream: wait "done(slot)"; copy the pass bytes to the caller's
+//     buffer; record "out(slot)".
+#include <string.h>
+
+#include "grim_internal.cuh"
+
+namespace grim {
+namespace {
+
+__global__ void rebase_kernel(int64_t* __restrict__ ro, int64_t* __restrict__ co, int64_t n1, int64_t ro0,
+                              int64_t co0) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x) {
+        ro[i] -= ro0;
+        co[i] -= co0;
+    }
+}
+
+struct HostSlot {
+    uint8_t* reads = nullptr;
+    int64_t* ro = nullptr;
+    int64_t* co = nullptr;
+    uint32_t* cb = nullptr;
+    uint16_t* E = nullptr;
+    uint8_t* pass = nullptr;
+    cudaEvent_t in = nullptr, done = nullptr, out = nullptr;
+};
+
+}  // namespace
+}  // namespace grim
+
+extern "C" {
+
+int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                     const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
+                     int64_t chunk_reads, void* stream) {
+    if (!bank || n_reads < 0) return GRIM_EINVAL;
+    if (n_reads == 0) return GRIM_OK;
+    if (!reads || !read_offsets || !cand_bins || !cand_offsets || !E || !pass) return GRIM_EINVAL;
+    if (read_offsets[n_reads] < read_offsets[0] || cand_offsets[n_reads] < cand_offsets[0]) return GRIM_EINVAL;
+    int rc = grim::check_device(bank);
+    if (rc != GRIM_OK) return rc;
+    if (chunk_reads <= 0) chunk_reads = n_reads / 8 > 65536 ? (n_reads + 7) / 8 : 65536;
+    const int64_t n_chunks = (n_reads + chunk_reads - 1) / chunk_reads;
+    // the largest chunk, in bases and candidates (offsets are host memory here)
+    int64_t max_bases = 1, max_cands = 1;
+    for (int64_t c = 0; c < n_chunks; c++) {
+        const int64_t r0 = c * chunk_reads, r1 = r0 + chunk_reads < n_reads ? r0 + chunk_reads : n_reads;
+        const int64_t nb = read_offsets[r1] - read_offsets[r0], nc = cand_offsets[r1] - cand_offsets[r0];
+        if (nb < 0 || nc < 0) return GRIM_EINVAL;  // decreasing offsets across a chunk
+        max_bases = nb > max_bases ? nb : max_bases;
+        max_cands = nc > max_cands ? nc : max_cands;
+    }
+    const int64_t max_nr = chunk_reads < n_reads ? chunk_reads : n_reads;
+    cudaStream_t sf = (cudaStream_t)stream, si = nullptr, so = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&si, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&so, cudaStreamNonBlocking);
+    grim::HostSlot slot[2];
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+        grim::HostSlot& s = slot[i];
+        e = grim::scratch_alloc((void**)&s.reads, (size_t)max_bases, sf);
+        if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.ro, (size_t)(max_nr + 1) * 8, sf);
+        if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.co, (size_t)(max_nr + 1) * 8, sf);
+        if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.cb, (size_t)max_cands * 4, sf);
+        if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.E, (size_t)max_nr * 2, sf);
+        if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.pass, (size_t)max_cands, sf);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.in, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.out, cudaEventDisableTiming);
+    }
+    cudaEvent_t ready = nullptr;  // the slots' memory exists on the filter stream
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ready, sf);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(si, ready, 0);
+    for (int64_t c = 0; c < n_chunks && e == cudaSuccess && rc == GRIM_OK; c++) {
+        grim::HostSlot& s = slot[c & 1];
+        const int64_t r0 = c * chunk_reads, r1 = r0 + chunk_reads < n_reads ? r0 + chunk_reads : n_reads;
+        const int64_t nr = r1 - r0;
+        const int64_t ro0 = read_offsets[r0], co0 = cand_offsets[r0];
+        const int64_t nb = read_offsets[r1] - ro0, nc = cand_offsets[r1] - co0;
+        if (c >= 2) e = cudaStreamWaitEvent(si, s.done, 0);  // chunk c - 2 no longer reads the slot
+        if (e == cudaSuccess && nb > 0) e = cudaMemcpyAsync(s.reads, reads + ro0, (size_t)nb, cudaMemcpyHostToDevice, si);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s.ro, read_offsets + r0, (size_t)(nr + 1) * 8, cudaMemcpyHostToDevice, si);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s.co, cand_offsets + r0, (size_t)(nr + 1) * 8, cudaMemcpyHostToDevice, si);
+        if (e == cudaSuccess && nc > 0)
+            e = cudaMemcpyAsync(s.cb, cand_bins + co0, (size_t)nc * 4, cudaMemcpyHostToDevice, si);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.E, E + r0, (size_t)nr * 2, cudaMemcpyHostToDevice, si);
+        if (e == cudaSuccess) e = cudaEventRecord(s.in, si);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sf, s.in, 0);
+        if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(sf, s.out, 0);  // chunk c - 2's bytes have left
+        if (e != cudaSuccess) break;
+        const int64_t need = (nr + 1 + 255) / 256;
+        grim::rebase_kernel<<<(unsigned)(need < 1024 ? need : 1024), 256, 0, sf>>>(s.ro, s.co, nr + 1, ro0, co0);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        rc = grim::launch_gather(bank, s.reads, s.ro, nr, s.cb, s.co, s.E, s.pass, nullptr, sf);
+        if (rc != GRIM_OK) break;
+        e = cudaEventRecord(s.done, sf);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(so, s.done, 0);
+        if (e == cudaSuccess && nc > 0) e = cudaMemcpyAsync(pass + co0, s.pass, (size_t)nc, cudaMemcpyDeviceToHost, so);
+        if (e == cudaSuccess) e = cudaEventRecord(s.out, so);
+    }
+    // the caller's stream completes once every copy out has
+    for (int i = 0; i < 2; i++)
+        if (slot[i].out && e == cudaSuccess) e = cudaStreamWaitEvent(sf, slot[i].out, 0);
+    cudaError_t e2 = cudaStreamSynchronize(so);
+    if (e == cudaSuccess) e = e2;
+    e2 = cudaStreamSynchronize(si);
+    if (e == cudaSuccess) e = e2;
+    for (int i = 0; i < 2; i++) {
+        grim::HostSlot& s = slot[i];
+        void* bufs[6] = {s.reads, s.ro, s.co, s.cb, s.E, s.pass};
+        for (void* b : bufs)
+            if (b) cudaFreeAsync(b, sf);
+    }
+    e2 = cudaStreamSynchronize(sf);
+    if (e == cudaSuccess) e = e2;
+    for (int i = 0; i < 2; i++) {
+        if (slot[i].in) cudaEventDestroy(slot[i].in);
+        if (slot[i].done) cudaEventDestroy(slot[i].done);
+        if (slot[i].out) cudaEventDestroy(slot[i].out);
+    }
+    if (ready) cudaEventDestroy(ready);
+    if (si) cudaStreamDestroy(si);
+    if (so) cudaStreamDestroy(so);
+    if (e != cudaSuccess) {
+        grim::set_last_cuda_error(e);
+        return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
+    }
+    return rc;
+}
+
+}  // extern "C"
