@@ -791,6 +791,10 @@ def run_ours(args):
 
 
 def main():
+    # ranks on one host share its cores for the synthetic inputs (OpenMP)
+    local_world = int(os.environ.get("LOCAL_WORLD_SIZE", os.environ.get("WORLD_SIZE", "1")))
+    if local_world > 1 and "OMP_NUM_THREADS" not in os.environ:
+        os.environ["OMP_NUM_THREADS"] = str(max(1, (os.cpu_count() or 1) // local_world))
     args = parse()
     if args.impl == "reference":
         run_reference(args)
