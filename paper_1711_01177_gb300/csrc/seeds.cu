@@ -270,165 +270,140 @@ constexpr int64_t kDedupChunk = (int64_t)kDedupThreads * kDedupItems;
 constexpr int kRadixBits = 4;
 constexpr int kRadixBuckets = 1 << kRadixBits;
 constexpr int kDedupPadded = kDedupSmem + kDedupSmem / 32;
-constexpr size_t kDedupSmemBytes = (2 * (size_t)kDedupPadded + (size_t)kRadixBuckets * kDedupThreads) * 4;
+constexpr int kCountWords = kRadixBuckets * kDedupThreads + kRadixBuckets * kDedupThreads / 16;
+constexpr size_t kDedupSmemBytes = (2 * (size_t)kDedupPadded + (size_t)kCountWords) * 4;
+
+// Counter (bucket d, thread t) lives at word l + l / 16 for l = d * 256 + t:
+// a thread's column (fixed t) and the scan's 16 consecutive counters of a
+// thread (l = 16 t' + k, at word 17 t' + k) both spread over the banks.
+__device__ __forceinline__ int cnt_at(int l) { return l + (l >> 4); }
 
 // Shared-memory key arrays get one pad word per 32 so that threads reading
 // consecutive blocks of keys do not collide on a bank.
-template <bool SMEM>
-__device__ __forceinline__ int64_t rx_at(int64_t i) {
+template <bool SMEM, typename I>
+__device__ __forceinline__ I rx_at(I i) {
     return SMEM ? i + (i >> 5) : i;
 }
 
 // Stable ascending LSD radix sort of A[0..n) on `passes` (even) digits of
 // kRadixBits, with B as the second buffer; the result ends in A.  Thread t
 // owns the contiguous keys [t * ipt, (t + 1) * ipt) and column t of the
-// bucket-major counters cnt[bucket * 256 + t], so counting and scattering
-// need no atomics and keep equal digits in their original order.
-template <bool SMEM>
-__device__ void radix_sort(uint32_t* A, uint32_t* B, int64_t n, int passes, uint32_t* cnt, uint32_t* ws) {
+// bucket-major counters, so counting and scattering need no atomics and
+// keep equal digits in their original order.  I: index type (32-bit for
+// the shared-memory case).
+template <bool SMEM, typename I>
+__device__ __forceinline__ void radix_sort(uint32_t* A, uint32_t* B, I n, int passes, uint32_t* cnt, uint32_t* ws) {
     const int t = threadIdx.x;
-    const int64_t ipt = (n + kDedupThreads - 1) / kDedupThreads;
-    const int64_t i0 = t * ipt < n ? t * ipt : n;
-    const int64_t i1 = i0 + ipt < n ? i0 + ipt : n;
+    const I ipt = (n + kDedupThreads - 1) / kDedupThreads;
+    const I i0 = (I)t * ipt < n ? (I)t * ipt : n;
+    const I i1 = i0 + ipt < n ? i0 + ipt : n;
     for (int ps = 0; ps < passes; ps++) {
         const int shift = ps * kRadixBits;
         uint32_t* src = (ps & 1) ? B : A;
         uint32_t* dst = (ps & 1) ? A : B;
 #pragma unroll
-        for (int b = 0; b < kRadixBuckets; b++) cnt[b * kDedupThreads + t] = 0;
-        for (int64_t i = i0; i < i1; i++) cnt[((src[rx_at<SMEM>(i)] >> shift) & (kRadixBuckets - 1)) * kDedupThreads + t]++;
+        for (int b = 0; b < kRadixBuckets; b++) cnt[cnt_at(b * kDedupThreads + t)] = 0;
+        for (I i = i0; i < i1; i++)
+            cnt[cnt_at((int)((src[rx_at<SMEM>(i)] >> shift) & (kRadixBuckets - 1)) * kDedupThreads + t)]++;
         __syncthreads();
-        // exclusive scan of the counters in bucket-major order
-        uint4* c4 = reinterpret_cast<uint4*>(cnt) + t * (kRadixBuckets / 4);
+        // exclusive scan of the counters in bucket-major order: thread t owns
+        // counters 16 t .. 16 t + 15 of that order (words 17 t .. 17 t + 15)
+        uint32_t* mine = cnt + 17 * t;
         uint32_t v[kRadixBuckets];
-#pragma unroll
-        for (int q = 0; q < kRadixBuckets / 4; q++) {
-            const uint4 x = c4[q];
-            v[4 * q] = x.x;
-            v[4 * q + 1] = x.y;
-            v[4 * q + 2] = x.z;
-            v[4 * q + 3] = x.w;
-        }
         uint32_t sum = 0;
 #pragma unroll
-        for (int k = 0; k < kRadixBuckets; k++) sum += v[k];
+        for (int k = 0; k < kRadixBuckets; k++) {
+            v[k] = mine[k];
+            sum += v[k];
+        }
         uint32_t tot;
         uint32_t run = block_exclusive_scan<uint32_t>(sum, ws, &tot);
 #pragma unroll
         for (int k = 0; k < kRadixBuckets; k++) {
-            const uint32_t x = v[k];
-            v[k] = run;
-            run += x;
+            mine[k] = run;
+            run += v[k];
         }
-#pragma unroll
-        for (int q = 0; q < kRadixBuckets / 4; q++) c4[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         __syncthreads();
-        for (int64_t i = i0; i < i1; i++) {
+        for (I i = i0; i < i1; i++) {
             const uint32_t key = src[rx_at<SMEM>(i)];
-            const uint32_t pos = cnt[((key >> shift) & (kRadixBuckets - 1)) * kDedupThreads + t]++;
-            dst[rx_at<SMEM>(pos)] = key;
+            const uint32_t pos = cnt[cnt_at((int)((key >> shift) & (kRadixBuckets - 1)) * kDedupThreads + t)]++;
+            dst[rx_at<SMEM>((I)pos)] = key;
         }
         __syncthreads();
     }
 }
 
 // Votes of run j of the sorted votes: starts st[0..u), n votes in all.
-__device__ __forceinline__ uint32_t run_votes(const uint32_t* st, int64_t u, int64_t n, int64_t j) {
-    return (uint32_t)((j + 1 < u ? (int64_t)st[j + 1] : n) - (int64_t)st[j]);
+template <typename I>
+__device__ __forceinline__ uint32_t run_votes(const uint32_t* st, I u, I n, I j) {
+    return (uint32_t)((j + 1 < u ? (I)st[j + 1] : n) - (I)st[j]);
 }
 
 // Block-wide count of runs with at least v votes.
-__device__ int64_t count_votes_at_least(const uint32_t* st, int64_t u, int64_t n, uint32_t v, int64_t* ws) {
+template <typename I>
+__device__ int64_t count_votes_at_least(const uint32_t* st, I u, I n, uint32_t v, int64_t* ws) {
     int64_t c = 0;
-    for (int64_t j = threadIdx.x; j < u; j += blockDim.x) c += run_votes(st, u, n, j) >= v;
+    for (I j = threadIdx.x; j < u; j += blockDim.x) c += run_votes<I>(st, u, n, j) >= v;
     int64_t total;
     block_exclusive_scan<int64_t>(c, ws, &total);
     return total;
 }
 
-// One CTA per read of the batch: sort its votes, find the runs, apply the
-// cap, write the kept bins (ascending) to H[hit_off[r] - h0 ...] and their
-// number to kept[r].  S: scratch of 8 bytes per vote, used as 2n u32: run
-// starts from the front; reads sorted in global memory also use the back
-// half as the radix sort's second buffer and build their list after the
-// starts.  `passes`: radix digits covering every bin id (even).
-__global__ void __launch_bounds__(kDedupThreads)
-seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, int passes, uint32_t* __restrict__ H,
-                   unsigned long long* __restrict__ S, int64_t* __restrict__ kept) {
-    extern __shared__ uint32_t dedupe_smem[];
-    uint32_t* A_s = dedupe_smem;
-    uint32_t* B_s = dedupe_smem + kDedupPadded;
-    uint32_t* cnt = dedupe_smem + 2 * kDedupPadded;
-    __shared__ int64_t ws[32];
-    __shared__ uint32_t ws32[32];
-    __shared__ unsigned int max_votes;
-    const int64_t r = blockIdx.x;
-    const int64_t base = hit_off[r] - h0, n = hit_off[r + 1] - hit_off[r];
-    if (n <= 0) {
-        if (threadIdx.x == 0) kept[r] = 0;
-        return;
-    }
-    const bool in_smem = n <= kDedupSmem;
-    uint32_t* st = reinterpret_cast<uint32_t*>(S + base);  // 2n u32 of scratch
-    if (in_smem) {
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) A_s[rx_at<true>(i)] = H[base + i];
-        __syncthreads();
-        radix_sort<true>(A_s, B_s, n, passes, cnt, ws32);
-    } else {
-        radix_sort<false>(H + base, st + n, n, passes, cnt, ws32);
-    }
-    // the sorted votes, read through the layout they were sorted in
-    auto A = [&](int64_t i) -> uint32_t { return in_smem ? A_s[rx_at<true>(i)] : H[base + i]; };
-
+// One read's votes A[0..n) (B: second buffer): sort, runs, cap, and the
+// kept bins (ascending) to out[0..); returns their number.  st: scratch of
+// n u32 for the run starts.  The shared-memory case (SMEM, 32-bit
+// indices) reads A through the padded layout; the other case is global
+// memory throughout.
+template <bool SMEM, typename I>
+__device__ __forceinline__ int64_t dedupe_read(uint32_t* A, uint32_t* B, I n, int cap, int passes, uint32_t* cnt,
+                                               uint32_t* st, uint32_t* out, uint32_t* ws32, int64_t* ws,
+                                               unsigned int* max_votes) {
+    radix_sort<SMEM, I>(A, B, n, passes, cnt, ws32);
     // run starts -> st[0..u), kDedupItems consecutive votes per thread
-    int64_t u = 0;
-    for (int64_t c0 = 0; c0 < n; c0 += kDedupChunk) {
-        const int64_t i0 = c0 + (int64_t)threadIdx.x * kDedupItems;
+    I u = 0;
+    for (I c0 = 0; c0 < n; c0 += (I)kDedupChunk) {
+        const I i0 = c0 + (I)threadIdx.x * kDedupItems;
         uint32_t fl = 0;
 #pragma unroll
         for (int k = 0; k < kDedupItems; k++) {
-            const int64_t i = i0 + k;
-            if (i < n && (i == 0 || A(i) != A(i - 1))) fl |= 1u << k;
+            const I i = i0 + k;
+            if (i < n && (i == 0 || A[rx_at<SMEM>(i)] != A[rx_at<SMEM>((I)(i - 1))])) fl |= 1u << k;
         }
-        int64_t tot;
-        int64_t o = u + block_exclusive_scan<int64_t>(__popc(fl), ws, &tot);
+        uint32_t tot;
+        I o = u + (I)block_exclusive_scan<uint32_t>((uint32_t)__popc(fl), ws32, &tot);
 #pragma unroll
         for (int k = 0; k < kDedupItems; k++)
             if ((fl >> k) & 1u) st[o++] = (uint32_t)(i0 + k);
-        u += tot;
+        u += (I)tot;
     }
     __syncthreads();
-
-    // reads sorted in shared memory write straight to H; the others build
-    // their list in the scratch after the starts, then copy it to H
-    uint32_t* out = in_smem ? H + base : st + u;
     int64_t n_keep = 0;
-    if (u <= cap) {
-        for (int64_t j = threadIdx.x; j < u; j += blockDim.x) out[j] = A(st[j]);
+    if (u <= (I)cap) {
+        for (I j = threadIdx.x; j < u; j += blockDim.x) out[j] = A[rx_at<SMEM>((I)st[j])];
         n_keep = u;
     } else {
         // the cap: keep votes > v_star, and the first `need` (lowest bins) at v_star
-        if (threadIdx.x == 0) max_votes = 0;
+        if (threadIdx.x == 0) *max_votes = 0;
         __syncthreads();
-        for (int64_t j = threadIdx.x; j < u; j += blockDim.x) atomicMax(&max_votes, run_votes(st, u, n, j));
+        for (I j = threadIdx.x; j < u; j += blockDim.x) atomicMax(max_votes, run_votes<I>(st, u, n, j));
         __syncthreads();
-        uint32_t lo = 1, hi = max_votes;  // count(votes >= lo) >= cap always holds
+        uint32_t lo = 1, hi = *max_votes;  // count(votes >= lo) >= cap always holds
         while (lo < hi) {
             const uint32_t mid = lo + (hi - lo + 1) / 2;
-            if (count_votes_at_least(st, u, n, mid, ws) >= cap) lo = mid;
+            if (count_votes_at_least<I>(st, u, n, mid, ws) >= cap) lo = mid;
             else hi = mid - 1;
         }
         const uint32_t v_star = lo;
-        const int64_t need = cap - count_votes_at_least(st, u, n, v_star + 1, ws);
+        const int64_t need = cap - count_votes_at_least<I>(st, u, n, v_star + 1, ws);
         int64_t n_eq = 0;
-        for (int64_t c0 = 0; c0 < u; c0 += kDedupChunk) {
-            const int64_t j0 = c0 + (int64_t)threadIdx.x * kDedupItems;
+        for (I c0 = 0; c0 < u; c0 += (I)kDedupChunk) {
+            const I j0 = c0 + (I)threadIdx.x * kDedupItems;
             uint32_t gt = 0, eq = 0;
 #pragma unroll
             for (int k = 0; k < kDedupItems; k++) {
-                const int64_t j = j0 + k;
+                const I j = j0 + k;
                 if (j < u) {
-                    const uint32_t v = run_votes(st, u, n, j);
+                    const uint32_t v = run_votes<I>(st, u, n, j);
                     if (v > v_star) gt |= 1u << k;
                     else if (v == v_star) eq |= 1u << k;
                 }
@@ -446,14 +421,51 @@ seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, int
             int64_t o = n_keep + block_exclusive_scan<int64_t>(__popc(keep), ws, &tot_keep);
 #pragma unroll
             for (int k = 0; k < kDedupItems; k++)
-                if ((keep >> k) & 1u) out[o++] = A(st[j0 + k]);
+                if ((keep >> k) & 1u) out[o++] = A[rx_at<SMEM>((I)st[j0 + k])];
             n_eq += tot_eq;
             n_keep += tot_keep;
         }
     }
-    if (!in_smem) {
+    return n_keep;
+}
+
+// One CTA per read of the batch: its votes sorted, runs found, the cap
+// applied and the kept bins (ascending) written to H[hit_off[r] - h0 ...],
+// their number to kept[r].  S: scratch of 8 bytes per vote, used as 2n u32:
+// run starts from the front; reads too long for shared memory also use the
+// back half as the sort's second buffer and build their list after the
+// starts before copying it to H.  `passes`: radix digits covering every bin
+// id (even).
+__global__ void __launch_bounds__(kDedupThreads)
+seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, int passes, uint32_t* __restrict__ H,
+                   unsigned long long* __restrict__ S, int64_t* __restrict__ kept) {
+    extern __shared__ uint32_t dedupe_smem[];
+    __shared__ int64_t ws[32];
+    __shared__ uint32_t ws32[32];
+    __shared__ unsigned int max_votes;
+    const int64_t r = blockIdx.x;
+    const int64_t base = hit_off[r] - h0, n = hit_off[r + 1] - hit_off[r];
+    if (n <= 0) {
+        if (threadIdx.x == 0) kept[r] = 0;
+        return;
+    }
+    uint32_t* st = reinterpret_cast<uint32_t*>(S + base);  // 2n u32 of scratch
+    int64_t n_keep;
+    if (n <= kDedupSmem) {
+        uint32_t* A_s = dedupe_smem;
+        uint32_t* B_s = dedupe_smem + kDedupPadded;
+        uint32_t* cnt = dedupe_smem + 2 * kDedupPadded;
+        const int ni = (int)n;
+        for (int i = threadIdx.x; i < ni; i += blockDim.x) A_s[rx_at<true>(i)] = H[base + i];
         __syncthreads();
-        for (int64_t j = threadIdx.x; j < n_keep; j += blockDim.x) H[base + j] = out[j];
+        n_keep = dedupe_read<true, int>(A_s, B_s, ni, cap, passes, cnt, st, H + base, ws32, ws, &max_votes);
+    } else {
+        uint32_t* cnt = dedupe_smem + 2 * kDedupPadded;
+        // the list is built after the starts (st + n: the sort's buffer, free by then)
+        uint32_t* list = st + n;
+        n_keep = dedupe_read<false, int64_t>(H + base, st + n, n, cap, passes, cnt, st, list, ws32, ws, &max_votes);
+        __syncthreads();
+        for (int64_t j = threadIdx.x; j < n_keep; j += blockDim.x) H[base + j] = list[j];
     }
     if (threadIdx.x == 0) kept[r] = n_keep;
 }
