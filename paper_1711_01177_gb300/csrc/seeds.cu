@@ -528,9 +528,34 @@ __global__ void locate_count_kernel(const uint8_t* __restrict__ pass, int64_t n_
     if (threadIdx.x == 0) counts[blockIdx.x] = total;
 }
 
-// read holding candidate c: the last r with cand_offsets[r] <= c
-__device__ __forceinline__ int64_t read_of(const int64_t* __restrict__ co, int64_t n_reads, int64_t c) {
-    int64_t lo = 0, hi = n_reads - 1;
+// Reads holding candidates c0 (lanes 0-15) and c1 (lanes 16-31): the last
+// r in [0, n_reads - 1] with cand_offsets[r] <= c, by a 16-ary search per
+// half-warp (about log16(n_reads) rounds of parallel loads).  Whole warp.
+__device__ int64_t reads_of_half_warps(const int64_t* __restrict__ co, int64_t n_reads, int64_t c0, int64_t c1,
+                                       int lane) {
+    const int j = lane & 15;
+    const int64_t c = lane < 16 ? c0 : c1;
+    int64_t lo = 0, hi = n_reads - 1;  // the answer lies in [lo, hi]; co[0] <= c
+    while (__any_sync(kFull, hi - lo > 15)) {  // then 16 lanes cover [lo, hi]
+        const int64_t p = lo + 1 + (hi - lo - 1 > 0 ? (hi - lo - 1) * j / 15 : 0);  // samples in (lo, hi]
+        const bool le = p <= hi && __ldg(co + p) <= c;
+        const unsigned b = __ballot_sync(kFull, le);
+        const unsigned half = lane < 16 ? b & 0xFFFFu : b >> 16;
+        const int k = __popc(half);  // the samples at or below c are a prefix
+        const int64_t p_last = __shfl_sync(kFull, p, (lane & 16) + (k > 0 ? k - 1 : 0));
+        const int64_t p_next = __shfl_sync(kFull, p, (lane & 16) + (k < 16 ? k : 15));
+        if (k > 0) lo = p_last;
+        if (k < 16 && p_next - 1 < hi) hi = p_next - 1;
+        if (hi < lo) hi = lo;  // only with decreasing (invalid) offsets
+    }
+    const int64_t p = lo + j;
+    const unsigned b = __ballot_sync(kFull, p <= hi && __ldg(co + p) <= c);
+    const int cnt = __popc(lane < 16 ? b & 0xFFFFu : b >> 16);
+    return cnt > 0 ? lo + cnt - 1 : lo;
+}
+
+// read holding candidate c: the last r in [lo, hi] with cand_offsets[r] <= c
+__device__ __forceinline__ int64_t read_of(const int64_t* __restrict__ co, int64_t lo, int64_t hi, int64_t c) {
     while (lo < hi) {
         const int64_t mid = lo + (hi - lo + 1) / 2;
         if (co[mid] <= c) lo = mid;
@@ -547,18 +572,33 @@ __global__ void locate_write_kernel(const uint8_t* __restrict__ pass, bool align
                                     int64_t* __restrict__ loc_begin, int64_t* __restrict__ loc_end,
                                     uint32_t* __restrict__ status) {
     __shared__ int64_t ws[32];
-    const int64_t t0 = (int64_t)blockIdx.x * kLocTile + (int64_t)threadIdx.x * kScanItems;
+    __shared__ int64_t tile_reads[2];
+    const int64_t tile0 = (int64_t)blockIdx.x * kLocTile;
+    const int64_t t0 = tile0 + (int64_t)threadIdx.x * kScanItems;
     uint32_t m = pass_mask16(pass, t0, n_cands, aligned);
+    uint32_t flags = 0;
+    if (threadIdx.x == 0 && blockIdx.x == 0 && cand_offsets[n_reads] != n_cands) flags |= GRIM_FLAG_BAD_OFFSETS;
     int64_t total;
     int64_t o = tile_base[blockIdx.x] + block_exclusive_scan<int64_t>(__popc(m), ws, &total);
-    uint32_t flags = 0;
+    if (total == 0) {  // nothing passes in this tile (block-uniform)
+        if (flags) atomicOr(status, flags);
+        return;
+    }
+    if (threadIdx.x < 32) {  // the reads of the tile's first and last candidates
+        const int64_t last = (tile0 + kLocTile < n_cands ? tile0 + kLocTile : n_cands) - 1;
+        const int64_t rr = reads_of_half_warps(cand_offsets, n_reads, tile0, last, threadIdx.x);
+        if (threadIdx.x == 0) tile_reads[0] = rr;
+        if (threadIdx.x == 16) tile_reads[1] = rr;
+    }
+    __syncthreads();
+    const int64_t tr0 = tile_reads[0], tr1 = tile_reads[1] > tile_reads[0] ? tile_reads[1] : tile_reads[0];
     int64_t r = -1;
     while (m && o < capacity) {
         const int i = __ffs(m) - 1;
         m &= m - 1;
         const int64_t c = t0 + i;
-        // the read: one search for the thread's first location, then forward
-        if (r < 0) r = read_of(cand_offsets, n_reads, c);
+        // the read: one search within the tile's reads, then forward
+        if (r < 0) r = read_of(cand_offsets, tr0, tr1, c);
         while (r + 1 < n_reads && cand_offsets[r + 1] <= c) r++;
         const uint32_t b = cand_bins[c];
         int64_t begin = 0, end = 0;
@@ -574,7 +614,6 @@ __global__ void locate_write_kernel(const uint8_t* __restrict__ pass, bool align
         if (loc_end) loc_end[o] = end;
         o++;
     }
-    if (threadIdx.x == 0 && blockIdx.x == 0 && cand_offsets[n_reads] != n_cands) flags |= GRIM_FLAG_BAD_OFFSETS;
     if (flags) atomicOr(status, flags);
 }
 
