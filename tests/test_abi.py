@@ -63,6 +63,28 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert lib.grim_build_bank(ctypes.c_void_p(16), 100, 5, 0, 100, None, ctypes.byref(h)) == grim.GRIM_EINVAL
     assert lib.grim_filter(None, None, None, 0, None, None, None, None, None, None) == grim.GRIM_EINVAL
     assert lib.grim_bank_free(None) == grim.GRIM_OK
+    # the entry points around the filter check their arguments first too
+    n = ctypes.c_int64()
+    fake = ctypes.c_void_p(16)
+    assert lib.grim_seed_index_build(None, 100, 12, None, ctypes.byref(h)) == grim.GRIM_EINVAL
+    assert lib.grim_seed_index_build(fake, 100, 16, None, ctypes.byref(h)) == grim.GRIM_EINVAL  # k <= 15
+    assert lib.grim_seed_index_build(fake, 10, 12, None, ctypes.byref(h)) == grim.GRIM_EINVAL  # len < k
+    assert lib.grim_seed_index_free(None) == grim.GRIM_OK
+    assert lib.grim_seed_candidates(None, fake, fake, 1, 256, 10, 100, fake, 10, fake, ctypes.byref(n),
+                                    None) == grim.GRIM_EINVAL
+    assert lib.grim_locate(None, None, fake, fake, 1, 1, fake, fake, fake, None, None, None, 0, 1, fake,
+                           None) == grim.GRIM_EINVAL
+    assert lib.grim_verify(None, fake, fake, fake, 1, fake, fake, 1, fake, None) == grim.GRIM_EINVAL
+    assert lib.grim_verify_stats(None, fake, fake, fake, 1, -1, fake, None) == grim.GRIM_EINVAL
+    assert lib.grim_verify_stats(None, fake, fake, fake, 1, 1, None, None) == grim.GRIM_EINVAL
+    assert lib.grim_pack_mask(fake, -1, fake, None) == grim.GRIM_EINVAL
+    assert lib.grim_pack_mask(None, 5, fake, None) == grim.GRIM_EINVAL
+    assert lib.grim_map(None, fake, fake, fake, fake, 1, fake, 100, 0, fake, fake, fake, 1, ctypes.byref(n), None,
+                        None) == grim.GRIM_EINVAL
+    assert lib.grim_filter_host(None, fake, fake, 1, fake, fake, fake, fake, 0, None) == grim.GRIM_EINVAL
+    assert lib.grim_bank_save(None, b"/nonexistent", None) == grim.GRIM_EINVAL
+    assert lib.grim_bank_load(None, None, ctypes.byref(h)) == grim.GRIM_EINVAL
+    assert lib.grim_strerror(grim.GRIM_EIO) != lib.grim_strerror(12345)
 
 
 def test_no_oracle_in_product_path():
