@@ -155,7 +155,8 @@ int grim_filter(const grim_bank* bank, const uint8_t* reads, const int64_t* read
  * grim_filter from HOST memory: every pointer below is host memory (reads,
  * read_offsets, cand_bins, cand_offsets, E in; pass out), with the meanings
  * of grim_filter.  The reads are processed in chunks of chunk_reads (<= 0:
- * an eighth of the reads, at least 65,536): each chunk's inputs are copied
+ * an eighth of the reads, at least 65,536, the last eighth in four
+ * quarters): each chunk's inputs are copied
  * in and its pass bytes copied out on two streams of the library's, while
  * the filter runs on `stream`, so that the copies of one chunk overlap the
  * filtering of another.  Page-locked host buffers let the copies overlap;

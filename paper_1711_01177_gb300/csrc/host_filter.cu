@@ -4,7 +4,8 @@
 //
 // Two device slots.  For chunk k (slot k % 2):
 //   copy-in stream: wait until the filter is done with chunk k - 2 (its
-//     inputs); copy bases, offsets, candidate bins, E; record "in(slot)";
+//     inputs); copy bases and candidate bins; record "in(slot)" (the
+//     offsets and E of every read are copied once, before the first chunk);
 //   filter stream (the caller's): wait "in(slot)" and until chunk k - 2's
 //     pass bytes have left (the slot's output); rebase the chunk's offsets
 //     to the slot; gather; record "done(slot)";
@@ -12,16 +13,20 @@
 //     buffer; record "out(slot)".
 #include <string.h>
 
+#include <vector>
+
 #include "grim_internal.cuh"
 
 namespace grim {
 namespace {
 
-__global__ void rebase_kernel(int64_t* __restrict__ ro, int64_t* __restrict__ co, int64_t n1, int64_t ro0,
+// the chunk's offsets, relative to its slot: ro[i] = ro_all[i] - ro_all[0]
+__global__ void rebase_kernel(const int64_t* __restrict__ ro_all, const int64_t* __restrict__ co_all,
+                              int64_t* __restrict__ ro, int64_t* __restrict__ co, int64_t n1, int64_t ro0,
                               int64_t co0) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x) {
-        ro[i] -= ro0;
-        co[i] -= co0;
+        ro[i] = ro_all[i] - ro0;
+        co[i] = co_all[i] - co0;
     }
 }
 
@@ -30,7 +35,6 @@ struct HostSlot {
     int64_t* ro = nullptr;
     int64_t* co = nullptr;
     uint32_t* cb = nullptr;
-    uint16_t* E = nullptr;
     uint8_t* pass = nullptr;
     cudaEvent_t in = nullptr, done = nullptr, out = nullptr;
 };
@@ -49,29 +53,47 @@ int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t*
     if (read_offsets[n_reads] < read_offsets[0] || cand_offsets[n_reads] < cand_offsets[0]) return GRIM_EINVAL;
     int rc = grim::check_device(bank);
     if (rc != GRIM_OK) return rc;
-    if (chunk_reads <= 0) chunk_reads = n_reads / 8 > 65536 ? (n_reads + 7) / 8 : 65536;
-    const int64_t n_chunks = (n_reads + chunk_reads - 1) / chunk_reads;
-    // the largest chunk, in bases and candidates (offsets are host memory here)
-    int64_t max_bases = 1, max_cands = 1;
+    // chunk boundaries: by default an eighth of the reads each, with the last
+    // eighth cut in four so that little filtering is left once the copies in
+    // (the critical path) have finished
+    std::vector<int64_t> bounds{0};
+    if (chunk_reads > 0) {
+        for (int64_t r = chunk_reads; r < n_reads; r += chunk_reads) bounds.push_back(r);
+    } else {
+        const int64_t c = n_reads / 8 > 65536 ? (n_reads + 7) / 8 : 65536;
+        int64_t r = 0;
+        while (n_reads - r > c) bounds.push_back(r += c);
+        const int64_t rest = n_reads - r, q4 = (rest + 3) / 4;
+        if (rest >= 4 * 4096)
+            for (int k = 1; k < 4; k++) bounds.push_back(r + k * q4);
+    }
+    bounds.push_back(n_reads);
+    const int64_t n_chunks = (int64_t)bounds.size() - 1;
+    // the largest chunk, in reads, bases and candidates (offsets are host memory here)
+    int64_t max_nr = 1, max_bases = 1, max_cands = 1;
     for (int64_t c = 0; c < n_chunks; c++) {
-        const int64_t r0 = c * chunk_reads, r1 = r0 + chunk_reads < n_reads ? r0 + chunk_reads : n_reads;
+        const int64_t r0 = bounds[c], r1 = bounds[c + 1];
         const int64_t nb = read_offsets[r1] - read_offsets[r0], nc = cand_offsets[r1] - cand_offsets[r0];
         if (nb < 0 || nc < 0) return GRIM_EINVAL;  // decreasing offsets across a chunk
+        max_nr = r1 - r0 > max_nr ? r1 - r0 : max_nr;
         max_bases = nb > max_bases ? nb : max_bases;
         max_cands = nc > max_cands ? nc : max_cands;
     }
-    const int64_t max_nr = chunk_reads < n_reads ? chunk_reads : n_reads;
     cudaStream_t sf = (cudaStream_t)stream, si = nullptr, so = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&si, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&so, cudaStreamNonBlocking);
     grim::HostSlot slot[2];
+    int64_t *ro_all = nullptr, *co_all = nullptr;
+    uint16_t* E_all = nullptr;
+    if (e == cudaSuccess) e = grim::scratch_alloc((void**)&ro_all, (size_t)(n_reads + 1) * 8, sf);
+    if (e == cudaSuccess) e = grim::scratch_alloc((void**)&co_all, (size_t)(n_reads + 1) * 8, sf);
+    if (e == cudaSuccess) e = grim::scratch_alloc((void**)&E_all, (size_t)n_reads * 2, sf);
     for (int i = 0; i < 2 && e == cudaSuccess; i++) {
         grim::HostSlot& s = slot[i];
         e = grim::scratch_alloc((void**)&s.reads, (size_t)max_bases, sf);
         if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.ro, (size_t)(max_nr + 1) * 8, sf);
         if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.co, (size_t)(max_nr + 1) * 8, sf);
         if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.cb, (size_t)max_cands * 4, sf);
-        if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.E, (size_t)max_nr * 2, sf);
         if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.pass, (size_t)max_cands, sf);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.in, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
@@ -81,30 +103,32 @@ int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t*
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(ready, sf);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(si, ready, 0);
+    // every read's offsets and E, once
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ro_all, read_offsets, (size_t)(n_reads + 1) * 8, cudaMemcpyHostToDevice, si);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(co_all, cand_offsets, (size_t)(n_reads + 1) * 8, cudaMemcpyHostToDevice, si);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E_all, E, (size_t)n_reads * 2, cudaMemcpyHostToDevice, si);
     for (int64_t c = 0; c < n_chunks && e == cudaSuccess && rc == GRIM_OK; c++) {
         grim::HostSlot& s = slot[c & 1];
-        const int64_t r0 = c * chunk_reads, r1 = r0 + chunk_reads < n_reads ? r0 + chunk_reads : n_reads;
+        const int64_t r0 = bounds[c], r1 = bounds[c + 1];
         const int64_t nr = r1 - r0;
         const int64_t ro0 = read_offsets[r0], co0 = cand_offsets[r0];
         const int64_t nb = read_offsets[r1] - ro0, nc = cand_offsets[r1] - co0;
         if (c >= 2) e = cudaStreamWaitEvent(si, s.done, 0);  // chunk c - 2 no longer reads the slot
         if (e == cudaSuccess && nb > 0) e = cudaMemcpyAsync(s.reads, reads + ro0, (size_t)nb, cudaMemcpyHostToDevice, si);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s.ro, read_offsets + r0, (size_t)(nr + 1) * 8, cudaMemcpyHostToDevice, si);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s.co, cand_offsets + r0, (size_t)(nr + 1) * 8, cudaMemcpyHostToDevice, si);
         if (e == cudaSuccess && nc > 0)
             e = cudaMemcpyAsync(s.cb, cand_bins + co0, (size_t)nc * 4, cudaMemcpyHostToDevice, si);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s.E, E + r0, (size_t)nr * 2, cudaMemcpyHostToDevice, si);
         if (e == cudaSuccess) e = cudaEventRecord(s.in, si);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(sf, s.in, 0);
         if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(sf, s.out, 0);  // chunk c - 2's bytes have left
         if (e != cudaSuccess) break;
         const int64_t need = (nr + 1 + 255) / 256;
-        grim::rebase_kernel<<<(unsigned)(need < 1024 ? need : 1024), 256, 0, sf>>>(s.ro, s.co, nr + 1, ro0, co0);
+        grim::rebase_kernel<<<(unsigned)(need < 1024 ? need : 1024), 256, 0, sf>>>(ro_all + r0, co_all + r0, s.ro,
+                                                                                  s.co, nr + 1, ro0, co0);
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
-        rc = grim::launch_gather(bank, s.reads, s.ro, nr, s.cb, s.co, s.E, s.pass, nullptr, sf);
+        rc = grim::launch_gather(bank, s.reads, s.ro, nr, s.cb, s.co, E_all + r0, s.pass, nullptr, sf);
         if (rc != GRIM_OK) break;
         e = cudaEventRecord(s.done, sf);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(so, s.done, 0);
@@ -120,10 +144,13 @@ int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t*
     if (e == cudaSuccess) e = e2;
     for (int i = 0; i < 2; i++) {
         grim::HostSlot& s = slot[i];
-        void* bufs[6] = {s.reads, s.ro, s.co, s.cb, s.E, s.pass};
+        void* bufs[5] = {s.reads, s.ro, s.co, s.cb, s.pass};
         for (void* b : bufs)
             if (b) cudaFreeAsync(b, sf);
     }
+    if (ro_all) cudaFreeAsync(ro_all, sf);
+    if (co_all) cudaFreeAsync(co_all, sf);
+    if (E_all) cudaFreeAsync(E_all, sf);
     e2 = cudaStreamSynchronize(sf);
     if (e == cudaSuccess) e = e2;
     for (int i = 0; i < 2; i++) {
