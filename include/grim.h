@@ -68,6 +68,17 @@ typedef struct grim_bank grim_bank;
  * scratch memory on it to the device.  Safe to call at any time. */
 int grim_release_scratch(void);
 
+/*
+ * Diagnostic of the bounded waits in the library's tensor-core pipeline (the
+ * full scan's mbarrier waits, which on expiry raise GRIM_FLAG_TIMEOUT, drain
+ * and return instead of hanging): one thread runs the same wait for limit_ns
+ * (1 ms .. 2 s, else GRIM_EINVAL) on a barrier that nothing ever completes.
+ * Returns GRIM_ETIMEOUT when the wait gave up as designed (GRIM_OK would
+ * mean it did not); the device and the context stay usable.  Synchronises
+ * `stream`.  The paper has no counterpart.
+ */
+int grim_wait_selfcheck(unsigned long long limit_ns, void* stream);
+
 /* Text for a status code (static storage). */
 const char* grim_strerror(int status);
 

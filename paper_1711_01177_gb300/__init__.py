@@ -35,6 +35,7 @@ SIGNATURES = {
     "grim_strerror": (ctypes.c_char_p, [_I32]),
     "grim_last_cuda_error": (_I32, []),
     "grim_release_scratch": (_I32, []),
+    "grim_wait_selfcheck": (_I32, [ctypes.c_ulonglong, _P]),
     "grim_build_bank": (_I32, [_P, _I64, _I32, _I32, _I32, _P, ctypes.POINTER(_P)]),
     "grim_bank_info": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "grim_bank_status": (_I32, [_P, _P, ctypes.POINTER(_U32)]),
@@ -101,6 +102,11 @@ def load(path: str | None = None):
             fn.argtypes = args
         _lib = lib
     return _lib
+
+
+def grim_wait_selfcheck(limit_ns: int, stream=None) -> int:
+    """Status of the bounded-wait diagnostic (GRIM_ETIMEOUT when it works)."""
+    return load().grim_wait_selfcheck(limit_ns, _stream_ptr(stream))
 
 
 def grim_release_scratch() -> None:

@@ -138,6 +138,13 @@ const char* grim_strerror(int status) {
 
 int grim_last_cuda_error(void) { return grim::g_last_cuda_error; }
 
+int grim_wait_selfcheck(unsigned long long limit_ns, void* stream) {
+    uint32_t timed_out = 0;
+    const int rc = grim::launch_wait_selfcheck(limit_ns, (cudaStream_t)stream, &timed_out);
+    if (rc != GRIM_OK) return rc;
+    return timed_out ? GRIM_ETIMEOUT : GRIM_OK;
+}
+
 int grim_release_scratch(void) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return GRIM_ECUDA;

@@ -118,6 +118,10 @@ int launch_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read
 // (looked up once per device, with that device current).
 int scan_noalloc_scratch(void** ptr, size_t* bytes);
 
+// The full scan's bounded mbarrier wait run for limit_ns on a barrier that
+// nothing completes; *timed_out (host) = 1 when it gave up as designed.
+int launch_wait_selfcheck(unsigned long long limit_ns, cudaStream_t s, uint32_t* timed_out);
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 

@@ -139,16 +139,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait: false when the CTA is aborting or the time limit expired
 // (then the abort flag is raised for every role of the CTA).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = now_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (now_ns() - t0 > kWaitLimitNs) {
+        if (now_ns() - t0 > limit_ns) {
             *abort_flag = 1;
             return false;
         }
+    }
+}
+
+// The bounded wait above on a barrier that nothing completes: out = 1 when
+// it gave up with the abort flag raised, 0 otherwise.
+__global__ void wait_selfcheck_kernel(unsigned long long limit_ns, uint32_t* out) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool done = mbar_wait(&bar, 0, &abort_flag, limit_ns);
+        *out = (!done && abort_flag) ? 1u : 0u;
     }
 }
 
@@ -838,6 +856,22 @@ int launch_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read
         case 5: return launch_scan_q<5>(bank, reads, read_offsets, n_reads, E, bin_begin, bin_end, out, scratch, s);
         default: return GRIM_ENOTSUP;
     }
+}
+
+int launch_wait_selfcheck(unsigned long long limit_ns, cudaStream_t s, uint32_t* timed_out) {
+    if (limit_ns < 1000000ull || limit_ns > kWaitLimitNs) return GRIM_EINVAL;
+    uint32_t* out = nullptr;
+    GRIM_CUDA_TRY(scratch_alloc((void**)&out, 4, s));
+    wait_selfcheck_kernel<<<1, 32, 0, s>>>(limit_ns, out);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(timed_out, out, 4, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e);
+        return GRIM_ECUDA;
+    }
+    return GRIM_OK;
 }
 
 }  // namespace grim

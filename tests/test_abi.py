@@ -85,6 +85,9 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert lib.grim_bank_save(None, b"/nonexistent", None) == grim.GRIM_EINVAL
     assert lib.grim_bank_load(None, None, ctypes.byref(h)) == grim.GRIM_EINVAL
     assert lib.grim_strerror(grim.GRIM_EIO) != lib.grim_strerror(12345)
+    # the bounded-wait diagnostic takes a limit of 1 ms .. 2 s
+    assert lib.grim_wait_selfcheck(999_999, None) == grim.GRIM_EINVAL
+    assert lib.grim_wait_selfcheck(2_000_000_001, None) == grim.GRIM_EINVAL
 
 
 def test_no_oracle_in_product_path():

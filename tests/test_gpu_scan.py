@@ -200,3 +200,20 @@ def test_scan_3gbp_batch_sampled(oracle):
             passes = oracle.sum_one(row(b), w.q, read) >= T
             assert passes == ((int(r) * w.n_bins + b) in got), (r, b)
     bank.free()
+
+
+def test_bounded_wait_gives_up_and_the_context_survives(oracle):
+    # the scan's mbarrier wait on a barrier that nothing completes: it must
+    # give up after its limit with GRIM_ETIMEOUT, not hang, and leave the
+    # context usable (a scan right after still matches the oracle)
+    import time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    assert grim.grim_wait_selfcheck(100_000_000) == grim.GRIM_ETIMEOUT
+    dt = time.perf_counter() - t0
+    assert 0.1 <= dt < 5.0, dt
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    codes = synth.ref_iid(50_000, 6)
+    bases, offs = make_reads(codes, 64, rng, lmax=150)
+    check_scan(oracle, codes, 5, 128, 100, bases, offs, np.full(64, 3, np.uint16))
