@@ -16,19 +16,22 @@
 //      base, first base highest), two shuffles bring it the next 8, and its
 //      4 tokens are shifts and masks of that 12-base window (the q-gram
 //      window of Sec. 3.2 step 1);
-//   2. each token is added to the read's bit-sliced count planes in shared
-//      memory with a carry chain of atomicXor (bit p flips; a bit that was
-//      set carries into plane p+1);
+//   2. each token is counted in a byte counter in shared memory (one
+//      atomic add; reads of more than 255 tokens instead add it to the
+//      bit-sliced planes with a carry chain of atomicXor), and the count
+//      planes are cut out of the counters with masks and shifts;
 //   3. every lane keeps its slice of the planes in registers (reads with up
 //      to two planes) or reads it from shared memory (more planes);
 //   4. candidate rows stream through the warp as 16-byte vectors,
 //      lanes_per_row lanes per row (4 lanes x 32 bytes for q=5: 8 rows per
 //      warp step); each row is requested three steps before it is scored,
 //      its id taken from a prefetched window of 32 candidate ids; rows are
-//      ANDed with the planes, popcounted, reduced with xor-shuffles and
-//      compared with the threshold (steps 3-5);
-//   5. the first lane of each row stores its pass byte (and sum); the eight
-//      rows of a step land in eight consecutive bytes.
+//      ANDed with the planes and popcounted, and the lanes' shares of the
+//      window's 32 rows are combined by shuffles as the steps finish
+//      (steps 3-4);
+//   5. every lane then holds one whole sum of the window, compares it with
+//      the threshold and stores its pass byte (and sum): 32 bytes of one
+//      window land together (step 5).
 #include "grim_internal.cuh"
 #include "tokens.cuh"
 
@@ -149,6 +152,37 @@ __device__ __forceinline__ void stream_start(Stream<Q>& st, const uint32_t* __re
     }
 }
 
+// Partial sums of one id window: lane s of a row group holds, for every
+// step t of the window, its share of row (t, g); the kLPB lanes of a group
+// together hold the kLPB steps.  Steps are combined pairwise as they finish,
+// like a binary counter: two step groups that differ in bit l of the step
+// index meet across lane bit l, the lane with that bit clear keeping the
+// lower group and the other the upper, each adding its partner's share.
+// After the last step, lane s holds the whole sum of step s: one shuffle
+// per step instead of log2(kLPB), and one row per lane to store.
+template <int N>
+struct StepReducer {
+    static constexpr int kLevels = N >= 16 ? 4 : N >= 8 ? 3 : N >= 4 ? 2 : N >= 2 ? 1 : 0;
+    static_assert((1 << kLevels) == N, "steps per window must be a power of two");
+    uint32_t stk[kLevels > 0 ? kLevels : 1];
+    uint32_t total = 0;
+    // T: the step index (a constant once the window loop is unrolled)
+    __device__ __forceinline__ void add(int T, uint32_t v, int s) {
+#pragma unroll
+        for (int l = 0; l < kLevels; l++) {
+            if (((T >> l) & 1) == 0) {
+                stk[l] = v;
+                return;
+            }
+            const uint32_t lo = stk[l], hi = v;
+            const bool upper = (s >> l) & 1;
+            const uint32_t send = upper ? lo : hi;
+            v = (upper ? hi : lo) + __shfl_xor_sync(kFull, send, 1 << l);
+        }
+        total = v;
+    }
+};
+
 // Score the read's candidates.  NP > 0: NP planes held in registers;
 // NP == 0: P planes read from shared memory.  cands / pass / sums point at
 // the read's first candidate.
@@ -167,53 +201,57 @@ __device__ __forceinline__ void score_read(Stream<Q>& st, const uint4* __restric
 #pragma unroll
             for (int u = 0; u < G::kVPL; u++) pl[p][u] = planes[p * G::kRowVecs + s + u * G::kLPB];
     }
+    static_assert(S::kWinSteps == G::kLPB, "one step of the window per lane of a row group");
     for (int w0 = 0; w0 < n; w0 += 32) {
         const uint32_t win_after = window_id(cands, w0 + 64 + lane, n);  // two windows ahead
+        StepReducer<S::kWinSteps> red;
 #pragma unroll
         for (int t = 0; t < S::kWinSteps; t++) {
             const int c0 = w0 + t * G::kBPS;
-            if (c0 >= n) break;  // warp-uniform
-            // request the rows kAhead steps ahead (window position t + kAhead)
-            {
-                const int ahead = t + S::kAhead;
-                const int idx = (ahead % S::kWinSteps) * G::kBPS + g;
-                const uint32_t src = ahead < S::kWinSteps ? st.win_cur : st.win_next;
-                const uint32_t id = __shfl_sync(kFull, src, idx);
-                fetch_row<Q>(st.r[(t + S::kAhead) % S::kBufs], id, bank, n_bins32, s);
-            }
-            // score this step's rows
-            const uint4 (&v)[G::kVPL] = st.r[t % S::kBufs];
             uint32_t part = 0;
-            if constexpr (NP > 0 && Q >= 6 && G::kVPL == 2) {
-                part = row_sum_csa<NP>(v, pl);
-            } else if (NP > 0) {
-#pragma unroll
-                for (int p = 0; p < (NP > 0 ? NP : 1); p++) {
-                    uint32_t q = 0;
-#pragma unroll
-                    for (int u = 0; u < G::kVPL; u++) q += and_popc(v[u], pl[p][u]);
-                    part += q << p;
+            if (c0 < n) {  // warp-uniform
+                // request the rows kAhead steps ahead (window position t + kAhead)
+                {
+                    const int ahead = t + S::kAhead;
+                    const int idx = (ahead % S::kWinSteps) * G::kBPS + g;
+                    const uint32_t src = ahead < S::kWinSteps ? st.win_cur : st.win_next;
+                    const uint32_t id = __shfl_sync(kFull, src, idx);
+                    fetch_row<Q>(st.r[(t + S::kAhead) % S::kBufs], id, bank, n_bins32, s);
                 }
-            } else {
-                for (int p = 0; p < P; p++) {
-                    uint32_t q = 0;
+                // score this step's rows
+                const uint4 (&v)[G::kVPL] = st.r[t % S::kBufs];
+                if constexpr (NP > 0 && Q >= 6 && G::kVPL == 2) {
+                    part = row_sum_csa<NP>(v, pl);
+                } else if (NP > 0) {
 #pragma unroll
-                    for (int u = 0; u < G::kVPL; u++)
-                        q += and_popc(v[u], planes[p * G::kRowVecs + s + u * G::kLPB]);
-                    part += q << p;
+                    for (int p = 0; p < (NP > 0 ? NP : 1); p++) {
+                        uint32_t q = 0;
+#pragma unroll
+                        for (int u = 0; u < G::kVPL; u++) q += and_popc(v[u], pl[p][u]);
+                        part += q << p;
+                    }
+                } else {
+                    for (int p = 0; p < P; p++) {
+                        uint32_t q = 0;
+#pragma unroll
+                        for (int u = 0; u < G::kVPL; u++)
+                            q += and_popc(v[u], planes[p * G::kRowVecs + s + u * G::kLPB]);
+                        part += q << p;
+                    }
                 }
             }
-#pragma unroll
-            for (int o = G::kLPB / 2; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-            const int c = c0 + g;
-            const uint32_t id = __shfl_sync(kFull, st.win_cur, (t * G::kBPS + g) & 31);
-            if (s == 0 && c < n) {
-                const bool in_range = id < n_bins32;
-                if (!in_range) flags |= GRIM_FLAG_BAD_BIN;
-                const uint32_t sum = in_range ? part : 0u;
-                pass[c] = (in_range && (int)sum >= T) ? 1 : 0;
-                if (sums) sums[c] = (uint16_t)sum;
-            }
+            red.add(t, part, s);
+        }
+        // this lane's row: step s, group g
+        const int j = s * G::kBPS + g;
+        const int c = w0 + j;
+        const uint32_t id = __shfl_sync(kFull, st.win_cur, j);
+        if (c < n) {
+            const bool in_range = id < n_bins32;
+            if (!in_range) flags |= GRIM_FLAG_BAD_BIN;
+            const uint32_t sum = in_range ? red.total : 0u;
+            pass[c] = (in_range && (int)sum >= T) ? 1 : 0;
+            if (sums) sums[c] = (uint16_t)sum;
         }
         st.win_cur = st.win_next;
         st.win_next = win_after;
@@ -231,6 +269,52 @@ __device__ __forceinline__ void write_constant(int64_t co, int64_t ce, const uin
         pass[c] = (in_range && pass0) ? 1 : 0;
         if (sums) sums[c] = 0;
     }
+}
+
+// Reads with at most 255 token positions count their tokens in bytes: one
+// shared atomic add per token, no carries.  The counters sit in the upper
+// half of the warp's plane area (planes 8-15, which such reads never use)
+// in a transposed order: the counter of token t is byte (t / 8) % 4 of
+// counter word k = t % 8 of group w = t / 32, and word k of group w lies at
+// 16-byte vector (k / 4) * RW + w, slot k % 4.  Bit 8 b + k of plane word w
+// then is bit p of byte b of counter word k, so a plane word is eight
+// masked shifts of the group's counter words, with no bit shuffling.
+template <int Q>
+__device__ __forceinline__ uint32_t counter_word(uint32_t tok) {
+    constexpr uint32_t RW = GatherGeo<Q>::kRowWords;
+    return 8 * RW + (tok & 4u) * RW + ((tok >> 5) << 2) + (tok & 3u);
+}
+
+// Count planes 0 .. used-1 from the byte counters of the warp's reads, which
+// are zeroed on the way; returns used (the bit length of the largest count).
+// Whole warp, after a __syncwarp that follows the counting.
+template <int Q>
+__device__ __forceinline__ int planes_from_counters(uint32_t* __restrict__ planes, int lane) {
+    constexpr int RW = GatherGeo<Q>::kRowWords;
+    uint4* cnt = reinterpret_cast<uint4*>(planes + 8 * RW);
+    uint32_t any = 0;  // OR of every count: its bit length is the largest count's
+    for (int w = lane; w < RW; w += 32) {
+        const uint4 a = cnt[w], b = cnt[RW + w];
+        any |= a.x | a.y | a.z | a.w | b.x | b.y | b.z | b.w;
+    }
+    any |= any >> 16;
+    any |= any >> 8;
+    const int used = 32 - __clz((int)__reduce_or_sync(kFull, any & 0xFFu));
+    for (int w = lane; w < RW; w += 32) {
+        const uint4 a = cnt[w], b = cnt[RW + w];
+        cnt[w] = make_uint4(0u, 0u, 0u, 0u);
+        cnt[RW + w] = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t c[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int p = 0; p < 8; p++) {
+            if (p >= used) break;  // warp-uniform
+            uint32_t u = 0;
+#pragma unroll
+            for (int k = 0; k < 8; k++) u |= ((c[k] >> p) & 0x01010101u) << k;
+            planes[p * RW + w] = u;
+        }
+    }
+    return used;
 }
 
 // Shared-memory set-up of a gather CTA: zeroed count planes.
@@ -284,24 +368,32 @@ __device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restric
 
     // 1-2. tokens into bit-sliced count planes
     uint32_t bad_base = 0;
-    int top = -1;  // highest plane this lane set
-    for_each_token4<Q>(rd, L, lane, bad_base, [&](uint32_t tok) {
-        const uint32_t w = tok >> 5, m = 1u << (tok & 31);
-        int p = 0;
-        while (p < kPlanes) {
-            const uint32_t old = atomicXor(&planes[p * RW + w], m);
-            if (!(old & m)) break;
-            ++p;
-        }
-        top = p > top ? p : top;
-    });
-    const int used = (int)__reduce_max_sync(kFull, (unsigned)(top + 1));
+    int used;
+    const int n_tok = L - Q + 1 > 0 ? L - Q + 1 : 0;
+    if (n_tok <= 255) {  // byte counters, then the planes from them
+        for_each_token4<Q>(rd, L, lane, bad_base,
+                           [&](uint32_t tok) { atomicAdd(&planes[counter_word<Q>(tok)], 1u << (tok & 0x18u)); });
+        __syncwarp();
+        used = planes_from_counters<Q>(planes, lane);
+    } else {  // longer reads: a carry chain of atomicXor per token
+        int top = -1;  // highest plane this lane set
+        for_each_token4<Q>(rd, L, lane, bad_base, [&](uint32_t tok) {
+            const uint32_t w = tok >> 5, m = 1u << (tok & 31);
+            int p = 0;
+            while (p < kPlanes) {
+                const uint32_t old = atomicXor(&planes[p * RW + w], m);
+                if (!(old & m)) break;
+                ++p;
+            }
+            top = p > top ? p : top;
+        });
+        used = (int)__reduce_max_sync(kFull, (unsigned)(top + 1));
+    }
     if (__any_sync(kFull, bad_base)) {
         flags |= GRIM_FLAG_BAD_BASE;
         bad_read = true;
     }
     __syncwarp();
-    const int n_tok = L - Q + 1 > 0 ? L - Q + 1 : 0;
     const int T = n_tok - Q * e;
 
     // 3-5. score the candidates
