@@ -21,7 +21,8 @@
 //      bit-sliced planes with a carry chain of atomicXor), and the count
 //      planes are cut out of the counters with masks and shifts;
 //   3. every lane keeps its slice of the planes in registers (reads with up
-//      to two planes) or reads it from shared memory (more planes);
+//      to three planes, two for q = 6) or reads it from shared memory (more
+//      planes);
 //   4. candidate rows stream through the warp as 16-byte vectors,
 //      lanes_per_row lanes per row (4 lanes x 32 bytes for q=5: 8 rows per
 //      warp step); each row is requested three steps before it is scored,
@@ -220,7 +221,7 @@ __device__ __forceinline__ void score_read(Stream<Q>& st, const uint4* __restric
                 }
                 // score this step's rows
                 const uint4 (&v)[G::kVPL] = st.r[t % S::kBufs];
-                if constexpr (NP > 0 && Q >= 6 && G::kVPL == 2) {
+                if constexpr (NP > 0 && NP <= 2 && Q >= 6 && G::kVPL == 2) {
                     part = row_sum_csa<NP>(v, pl);
                 } else if (NP > 0) {
 #pragma unroll
@@ -328,20 +329,16 @@ __device__ __forceinline__ void gather_cta_setup(uint4* smem, int warps) {
 
 // The whole filter for read r, by one warp (steps 0-5 above).  The warp's
 // count planes are zero on entry and left zero on exit.
+// ro, re: the read's bases; co, ce: its candidates; e: its edit budget.
 template <int Q>
-__device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restrict__ bank, int64_t n_bins,
+__device__ __forceinline__ void gather_read(int64_t ro, int64_t re, int64_t co, int64_t ce, int e,
+                                            const uint32_t* __restrict__ bank, int64_t n_bins,
                                             const uint8_t* __restrict__ reads,
-                                            const int64_t* __restrict__ read_offsets,
-                                            const uint32_t* __restrict__ cand_bins,
-                                            const int64_t* __restrict__ cand_offsets,
-                                            const uint16_t* __restrict__ E, uint8_t* __restrict__ pass,
+                                            const uint32_t* __restrict__ cand_bins, uint8_t* __restrict__ pass,
                                             uint16_t* __restrict__ sums, uint32_t* __restrict__ planes, int lane,
                                             uint32_t& flags) {
     constexpr int RW = GatherGeo<Q>::kRowWords;
     const uint4* planes4 = reinterpret_cast<const uint4*>(planes);
-    const int64_t ro = read_offsets[r], re = read_offsets[r + 1];
-    const int64_t co = cand_offsets[r], ce = cand_offsets[r + 1];
-    const int e = E[r];
     if (ce < co) {  // nothing sensible to write for this read
         flags |= GRIM_FLAG_BAD_OFFSETS;
         return;
@@ -405,6 +402,9 @@ __device__ __forceinline__ void gather_read(int64_t r, const uint32_t* __restric
                              lane, flags);
         else if (used == 2)
             score_read<Q, 2>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+                             lane, flags);
+        else if (Q <= 5 && used == 3)  // for q = 6 three planes stay in shared memory
+            score_read<Q, 3>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
                              lane, flags);
         else
             score_read<Q, 0>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
@@ -506,8 +506,8 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
         if ((int64_t)r0 >= r_end) break;
         const int64_t r1 = (int64_t)r0 + claim < r_end ? (int64_t)r0 + claim : r_end;
         for (int64_t r = (int64_t)r0; r < r1; r++)
-            gather_read<Q>(r, bank, n_bins, reads, read_offsets, cand_bins, cand_offsets, E, pass, sums, planes, lane,
-                           flags);
+            gather_read<Q>(read_offsets[r], read_offsets[r + 1], cand_offsets[r], cand_offsets[r + 1], E[r], bank,
+                           n_bins, reads, cand_bins, pass, sums, planes, lane, flags);
     }
     flags = __reduce_or_sync(kFull, flags);
     if (lane == 0 && flags) atomicOr(status, flags);
