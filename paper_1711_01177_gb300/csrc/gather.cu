@@ -12,9 +12,9 @@
 // One warp per read (grid-stride over reads):
 //   0. the first candidate rows are requested before anything else, so
 //      their latency hides behind the token work;
-//   1. each lane packs 4 consecutive bases of a 128-base block (2 bits per
-//      base, first base highest), two shuffles bring it the next 8, and its
-//      4 tokens are shifts and masks of that 12-base window (the q-gram
+//   1. each lane packs 5 consecutive bases of a 160-base block (2 bits per
+//      base, first base highest), a shuffle brings it the next 5, and its
+//      5 tokens are shifts and masks of that 10-base window (the q-gram
 //      window of Sec. 3.2 step 1);
 //   2. each token is counted in a byte counter in shared memory (one
 //      atomic add; reads of more than 255 tokens instead add it to the
@@ -368,13 +368,13 @@ __device__ __forceinline__ void gather_read(int64_t ro, int64_t re, int64_t co, 
     int used;
     const int n_tok = L - Q + 1 > 0 ? L - Q + 1 : 0;
     if (n_tok <= 255) {  // byte counters, then the planes from them
-        for_each_token4<Q>(rd, L, lane, bad_base,
+        for_each_token5<Q>(rd, L, lane, bad_base,
                            [&](uint32_t tok) { atomicAdd(&planes[counter_word<Q>(tok)], 1u << (tok & 0x18u)); });
         __syncwarp();
         used = planes_from_counters<Q>(planes, lane);
     } else {  // longer reads: a carry chain of atomicXor per token
         int top = -1;  // highest plane this lane set
-        for_each_token4<Q>(rd, L, lane, bad_base, [&](uint32_t tok) {
+        for_each_token5<Q>(rd, L, lane, bad_base, [&](uint32_t tok) {
             const uint32_t w = tok >> 5, m = 1u << (tok & 31);
             int p = 0;
             while (p < kPlanes) {

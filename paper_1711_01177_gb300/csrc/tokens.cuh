@@ -103,4 +103,43 @@ __device__ __forceinline__ void for_each_token4(const uint8_t* __restrict__ rd, 
     }
 }
 
+// Calls f(token) on the lane that owns each token position i (i + Q <= L),
+// lane l owning positions 160 b + 5 l .. 160 b + 5 l + 4 of block b: one
+// block covers a read of up to 164 bases, with 5 token slots per lane.  Each
+// lane packs its 5 bases, 2 bits each with the first base highest; one
+// shuffle brings the next lane's 5 (lane 31 takes them from the next block,
+// loaded one block ahead); the 20-bit window of 10 bases then holds the
+// lane's 5 tokens, each a shift and a mask (Q <= 6).  Whole warp, L
+// warp-uniform.  bad_base collects codes > 3 (the tokens then use the
+// code's low two bits; the caller rejects the read).
+template <int Q, typename F>
+__device__ __forceinline__ void for_each_token5(const uint8_t* __restrict__ rd, int L, int lane, uint32_t& bad_base,
+                                                F&& f) {
+    static_assert(Q >= 1 && Q <= 6, "window of 10 bases");
+    constexpr uint32_t kMask = (1u << (2 * Q)) - 1;
+    auto pack = [&](int p0) -> uint32_t {
+        uint32_t v = 0;
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            const int i = p0 + k;
+            const uint32_t c = i < L ? (uint32_t)__ldg(rd + i) : 0u;
+            bad_base |= (uint32_t)(c > 3u);
+            v = (v << 2) | (c & 3u);
+        }
+        return v;
+    };
+    if (L <= 0) return;
+    uint32_t cur = pack(5 * lane);
+    for (int b0 = 0; b0 < L; b0 += 160) {
+        const uint32_t nxt = b0 + 160 < L ? pack(b0 + 160 + 5 * lane) : 0u;  // warp-uniform condition
+        const uint32_t nb = __shfl_sync(kFull, lane == 0 ? nxt : cur, (lane + 1) & 31);
+        const uint32_t w = (cur << 10) | nb;  // bases p .. p + 9 of the read, p = b0 + 5 lane
+        const int p = b0 + 5 * lane;
+#pragma unroll
+        for (int k = 0; k < 5; k++)
+            if (p + k + Q <= L) f((w >> (2 * (10 - k - Q))) & kMask);
+        cur = nxt;
+    }
+}
+
 }  // namespace grim
