@@ -17,9 +17,9 @@
 //      5 tokens are shifts and masks of that 10-base window (the q-gram
 //      window of Sec. 3.2 step 1);
 //   2. each token is counted in a byte counter in shared memory (one
-//      atomic add; reads of more than 255 tokens instead add it to the
-//      bit-sliced planes with a carry chain of atomicXor), and the count
-//      planes are cut out of the counters with masks and shifts;
+//      atomic add), and the count planes are cut out of the counters with
+//      masks and shifts; for q = 6 and for reads of more than 255 tokens it
+//      is added to the bit-sliced planes by a carry chain of atomicXor;
 //   3. every lane keeps its slice of the planes in registers (reads with up
 //      to three planes, two for q = 6) or reads it from shared memory (more
 //      planes);
@@ -272,7 +272,7 @@ __device__ __forceinline__ void write_constant(int64_t co, int64_t ce, const uin
     }
 }
 
-// Reads with at most 255 token positions count their tokens in bytes: one
+// Reads with at most 255 token positions (q <= 5) count their tokens in bytes: one
 // shared atomic add per token, no carries.  The counters sit in the upper
 // half of the warp's plane area (planes 8-15, which such reads never use)
 // in a transposed order: the counter of token t is byte (t / 8) % 4 of
@@ -367,12 +367,14 @@ __device__ __forceinline__ void gather_read(int64_t ro, int64_t re, int64_t co, 
     uint32_t bad_base = 0;
     int used;
     const int n_tok = L - Q + 1 > 0 ? L - Q + 1 : 0;
-    if (n_tok <= 255) {  // byte counters, then the planes from them
+    // byte counters, then the planes from them (q <= 5); for q = 6 the 4096
+    // counters cost more to cut into planes than the carries they save
+    if (Q <= 5 && n_tok <= 255) {
         for_each_token5<Q>(rd, L, lane, bad_base,
                            [&](uint32_t tok) { atomicAdd(&planes[counter_word<Q>(tok)], 1u << (tok & 0x18u)); });
         __syncwarp();
         used = planes_from_counters<Q>(planes, lane);
-    } else {  // longer reads: a carry chain of atomicXor per token
+    } else {  // q = 6 and longer reads: a carry chain of atomicXor per token
         int top = -1;  // highest plane this lane set
         for_each_token5<Q>(rd, L, lane, bad_base, [&](uint32_t tok) {
             const uint32_t w = tok >> 5, m = 1u << (tok & 31);
