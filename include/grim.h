@@ -387,6 +387,21 @@ int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* c
                 int64_t seg_stride, int64_t capacity, int64_t* n_loc, void* stream);
 
 /*
+ * Edit budgets from an error rate (Sec. 3.4: the threshold tolerates E
+ * edits, E the read length times the error rate; Sec. 6.1 uses a rate of
+ * 0.05): E[r] = floor(num * L_r / den), or the ceiling when round_up != 0,
+ * in exact integer arithmetic, with L_r = read_offsets[r+1] -
+ * read_offsets[r] (a negative length gives 0, a length above
+ * GRIM_MAX_READ_LEN counts as GRIM_MAX_READ_LEN + 1 — the filter rejects
+ * such reads — and results above 65535 are saturated).
+ * read_offsets: device i64 [n_reads + 1]; E: device u16
+ * [n_reads], written.  num >= 0 and den >= 1, else GRIM_EINVAL.  Enqueues
+ * on `stream`.
+ */
+int grim_fill_E_rate(const int64_t* read_offsets, int64_t n_reads, int32_t num, int32_t den, int32_t round_up,
+                     uint16_t* E, void* stream);
+
+/*
  * The seed location filter bitmask of Sec. 3.3 at one bit per location:
  * bit i % 32 of bits[i / 32] is 1 iff pass[i] != 0 (device u8 [n] in,
  * device u32 [ceil(n / 32)] out; the unused high bits of the last word are

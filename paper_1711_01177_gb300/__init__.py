@@ -36,6 +36,7 @@ SIGNATURES = {
     "grim_last_cuda_error": (_I32, []),
     "grim_release_scratch": (_I32, []),
     "grim_wait_selfcheck": (_I32, [ctypes.c_ulonglong, _P]),
+    "grim_fill_E_rate": (_I32, [_P, _I64, _I32, _I32, _I32, _P, _P]),
     "grim_build_bank": (_I32, [_P, _I64, _I32, _I32, _I32, _P, ctypes.POINTER(_P)]),
     "grim_bank_info": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "grim_bank_status": (_I32, [_P, _P, ctypes.POINTER(_U32)]),
@@ -485,6 +486,20 @@ def grim_bank_load(path: str, stream=None) -> Bank:
     h = ctypes.c_void_p()
     _check(load().grim_bank_load(os.fsencode(path), _stream_ptr(stream), ctypes.byref(h)), "grim_bank_load")
     return Bank(h)
+
+
+def grim_fill_E_rate(read_offsets: torch.Tensor, num: int = 5, den: int = 100, round_up: bool = False,
+                     E: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Per-read edit budgets floor(num * L / den) (ceil with round_up), as
+    int16 holding u16 (Sec. 3.4, Sec. 6.1)."""
+    n = read_offsets.numel() - 1
+    if n < 0:
+        raise ValueError("read_offsets needs n_reads + 1 entries")
+    if E is None:
+        E = torch.empty(max(n, 1), dtype=torch.int16, device=read_offsets.device)
+    _check(load().grim_fill_E_rate(_dev_ptr(read_offsets, "read_offsets", 8), n, num, den, int(bool(round_up)),
+                                   _dev_ptr(E, "E", 2), _stream_ptr(stream)), "grim_fill_E_rate")
+    return E[:n]
 
 
 def grim_pack_mask(pass_: torch.Tensor, bits: torch.Tensor | None = None, stream=None) -> torch.Tensor:

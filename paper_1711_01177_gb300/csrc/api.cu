@@ -116,9 +116,36 @@ void delete_bank(grim_bank* bank) {
     delete bank;
 }
 
+namespace {
+
+// E[r] = floor (or ceil) of num * L_r / den, saturated at 65535; L_r < 0 gives 0.
+__global__ void fill_E_rate_kernel(const int64_t* __restrict__ read_offsets, int64_t n, int64_t num, int64_t den,
+                                   bool round_up, uint16_t* __restrict__ E) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t L = __ldg(read_offsets + r + 1) - __ldg(read_offsets + r);
+        L = L < 0 ? 0 : (L > GRIM_MAX_READ_LEN + 1 ? GRIM_MAX_READ_LEN + 1 : L);  // num * L < 2^48
+        const int64_t e = (num * L + (round_up ? den - 1 : 0)) / den;
+        E[r] = (uint16_t)(e > 65535 ? 65535 : e);
+    }
+}
+
+}  // namespace
 }  // namespace grim
 
 extern "C" {
+
+int grim_fill_E_rate(const int64_t* read_offsets, int64_t n_reads, int32_t num, int32_t den, int32_t round_up,
+                     uint16_t* E, void* stream) {
+    if (n_reads < 0 || num < 0 || den < 1) return GRIM_EINVAL;
+    if (n_reads == 0) return GRIM_OK;
+    if (!read_offsets || !E) return GRIM_EINVAL;
+    const int64_t need = (n_reads + 255) / 256;
+    const int64_t cap = (int64_t)grim::sm_count() * 8;
+    grim::fill_E_rate_kernel<<<(unsigned)(need < cap ? need : cap), 256, 0, (cudaStream_t)stream>>>(
+        read_offsets, n_reads, num, den, round_up != 0, E);
+    GRIM_CUDA_TRY(cudaGetLastError());
+    return GRIM_OK;
+}
 
 const char* grim_strerror(int status) {
     switch (status) {

@@ -85,6 +85,10 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert lib.grim_bank_save(None, b"/nonexistent", None) == grim.GRIM_EINVAL
     assert lib.grim_bank_load(None, None, ctypes.byref(h)) == grim.GRIM_EINVAL
     assert lib.grim_strerror(grim.GRIM_EIO) != lib.grim_strerror(12345)
+    assert lib.grim_fill_E_rate(fake, 5, 5, 0, 0, fake, None) == grim.GRIM_EINVAL  # den >= 1
+    assert lib.grim_fill_E_rate(fake, 5, -1, 100, 0, fake, None) == grim.GRIM_EINVAL  # num >= 0
+    assert lib.grim_fill_E_rate(None, 5, 5, 100, 0, fake, None) == grim.GRIM_EINVAL
+    assert lib.grim_fill_E_rate(None, 0, 5, 100, 0, None, None) == grim.GRIM_OK  # nothing to do
     # the bounded-wait diagnostic takes a limit of 1 ms .. 2 s
     assert lib.grim_wait_selfcheck(999_999, None) == grim.GRIM_EINVAL
     assert lib.grim_wait_selfcheck(2_000_000_001, None) == grim.GRIM_EINVAL

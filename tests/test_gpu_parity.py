@@ -132,6 +132,65 @@ def test_filter_low_complexity_and_long_reads(oracle):
     bank.free()
 
 
+@pytest.mark.parametrize("q", [1, 2, 3, 4, 5, 6])
+def test_filter_count_path_boundaries(oracle, q):
+    """The token-count paths at their edges: reads of 255 token positions
+    (byte counters, one of them reaching 255: eight planes) and of 256 (the
+    carry chain), lengths around the 160-base blocks of the token roller,
+    and random reads with one run giving a top count of 2 .. 8 (one to four
+    planes, the register paths and the shared-memory path)."""
+    rng = np.random.default_rng(700 + q)
+    n = 30_000
+    codes = synth.ref_iid(n, 70 + q)
+    codes[8000:8400] = 0  # poly-A
+    codes[12000:12400] = np.tile([0, 1], 200)  # (AC)n
+    r2 = synth.pack2bit(codes)
+    bank = gpu_bank(r2, n, q, 256, 120)
+    reads_l = []
+    for L in (q + 253, q + 254, q + 255, q + 256):  # 254 .. 257 token positions
+        reads_l += [np.zeros(L, np.uint8), np.tile([0, 1], L)[:L].astype(np.uint8), codes[7900:7900 + L].copy()]
+    for L in (155, 159, 160, 161, 163, 164, 165, 166, 319, 320, 321, 324, 325):
+        st = int(rng.integers(0, n - L))
+        reads_l.append(codes[st:st + L].copy())
+    for run in range(q + 1, q + 8):  # a poly-A run of `run` bases: top count run - q + 1
+        st = int(rng.integers(0, n - 150))
+        r = codes[st:st + 150].copy()
+        r[40:40 + run] = 0
+        reads_l.append(r)
+    offs = np.concatenate([[0], np.cumsum([len(x) for x in reads_l])]).astype(np.int64)
+    bases = np.concatenate(reads_l).astype(np.uint8)
+    nr = len(reads_l)
+    cb = np.tile(np.arange(bank.n_bins, dtype=np.uint32), nr)
+    co = np.arange(0, (nr + 1) * bank.n_bins, bank.n_bins, dtype=np.int64)
+    E = rng.integers(0, 20, nr).astype(np.uint16)
+    p, s, st, flags = run_filter(bank, bases, offs, cb, co, E)
+    assert st == grim.GRIM_OK and flags == 0
+    ob = oracle.build_bank(r2, n, q, 256, 120)
+    op, os_ = oracle.filter(ob, q, bases, offs, cb, co, E)
+    assert np.array_equal(s, os_.astype(np.uint16))
+    assert np.array_equal(p, op)
+    assert p.any() and not p.all()
+    bank.free()
+
+
+def test_fill_E_rate_is_the_integer_rule():
+    """E = floor(num L / den) (or the ceiling), saturated, 0 for a negative
+    length: checked against Python integers and the input generator's rule."""
+    rng = np.random.default_rng(5)
+    lens = rng.integers(0, 400, 5000)
+    lens[:6] = [0, 1, 19, 20, 21, 150]
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    offs_d = dev(offs)
+    for num, den, up in ((5, 100, False), (5, 100, True), (1, 3, False), (7, 1, True), (0, 9, False)):
+        E = host(grim.grim_fill_E_rate(offs_d, num, den, up), np.uint16)
+        want = [min(65535, (num * int(L) + (den - 1 if up else 0)) // den) for L in lens]
+        assert E.tolist() == want, (num, den, up)
+    assert np.array_equal(host(grim.grim_fill_E_rate(offs_d), np.uint16), synth.E_rate(offs))
+    odd = dev(np.array([0, 100, 50, 50 + 10_000_000], np.int64))  # decreasing, then very long
+    assert host(grim.grim_fill_E_rate(odd, 5, 100), np.uint16).tolist() == [5, 0, 3276]
+    assert host(grim.grim_fill_E_rate(odd, 60_000, 1), np.uint16).tolist() == [65535, 0, 65535]
+
+
 def test_filter_empty_inputs(oracle):
     w = synth.gather_iid(ref_len=50_000, n_reads=64, k=4)
     bank = gpu_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
