@@ -169,7 +169,7 @@ def test_filter_count_path_boundaries(oracle, q):
     op, os_ = oracle.filter(ob, q, bases, offs, cb, co, E)
     assert np.array_equal(s, os_.astype(np.uint16))
     assert np.array_equal(p, op)
-    assert p.any() and not p.all()
+    assert p.any() and (q == 1 or not p.all())  # at q = 1 every bin holds all four tokens
     bank.free()
 
 
