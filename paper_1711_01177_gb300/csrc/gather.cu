@@ -9,7 +9,7 @@
 // exact integer arithmetic over whole 32-bit words instead of one bit test
 // per token.  Reads of 100-150 bases need two or three planes.
 //
-// One warp per read (grid-stride over reads):
+// One warp per read (warps claim reads; the launch at the end of the file):
 //   0. the first candidate rows are requested before anything else, so
 //      their latency hides behind the token work;
 //   1. each lane packs 5 consecutive bases of a 160-base block (2 bits per

@@ -1,11 +1,12 @@
-// Warp-level q-gram token roller shared by the gather and full-scan kernels
-// (Sec. 3.2 step 1: every token of the read).
+// Warp-level q-gram token rollers (Sec. 3.2 step 1: every token of the read).
 //
-// A warp reads a read 32 bases at a time.  Two ballots per 32 bases give the
-// low and high bits of every base code; a funnel shift lines up the q bases
-// starting at a lane's position; a table of 4^q entries (built once per CTA
-// in shared memory) maps those 2q bits to the token value, first base most
-// significant.
+// for_each_token (full-scan preparation): a warp reads a read 32 bases at a
+// time; two ballots per 32 bases give the low and high bits of every base
+// code; a funnel shift lines up the q bases starting at a lane's position;
+// a table of 4^q entries (built once per CTA in shared memory) maps those 2q
+// bits to the token value, first base most significant.
+// for_each_token5 (gather): each lane packs 5 bases and takes the next 5 from
+// its neighbour; its 5 tokens are shifts and masks of that 10-base window.
 #pragma once
 
 #include "grim_internal.cuh"
@@ -62,44 +63,6 @@ __device__ __forceinline__ void for_each_token(const uint8_t* __restrict__ rd, i
             lo_c = lo_n;
             hi_c = hi_n;
         }
-    }
-}
-
-// Calls f(token) on the lane that owns each token position i (i + Q <= L),
-// lane l owning positions 128 b + 4 l .. 128 b + 4 l + 3 of block b.  Each
-// lane packs its 4 bases, 2 bits each with the first base highest; two
-// shuffles bring the next 8 bases (lanes 30 and 31 take them from the next
-// block, loaded one block ahead); the 24-bit window of 12 bases then holds
-// the lane's 4 tokens, each a shift and a mask (Q <= 6).  Whole warp, L
-// warp-uniform.  bad_base collects codes > 3 (the tokens then use the
-// code's low two bits; the caller rejects the read).
-template <int Q, typename F>
-__device__ __forceinline__ void for_each_token4(const uint8_t* __restrict__ rd, int L, int lane, uint32_t& bad_base,
-                                                F&& f) {
-    static_assert(Q >= 1 && Q <= 6, "window of 12 bases");
-    constexpr uint32_t kMask = (1u << (2 * Q)) - 1;
-    auto pack = [&](int p0) -> uint32_t {
-        uint32_t v = 0;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int i = p0 + k;
-            const uint32_t c = i < L ? (uint32_t)__ldg(rd + i) : 0u;
-            bad_base |= (uint32_t)(c > 3u);
-            v = (v << 2) | (c & 3u);
-        }
-        return v;
-    };
-    if (L <= 0) return;
-    uint32_t cur = pack(4 * lane);
-    for (int b0 = 0; b0 < L; b0 += 128) {
-        const uint32_t nxt = b0 + 128 < L ? pack(b0 + 128 + 4 * lane) : 0u;  // warp-uniform condition
-        const uint32_t d1 = __shfl_sync(kFull, lane == 0 ? nxt : cur, (lane + 1) & 31);
-        const uint32_t d2 = __shfl_sync(kFull, lane < 2 ? nxt : cur, (lane + 2) & 31);
-        const uint32_t w = (cur << 16) | (d1 << 8) | d2;  // bases 4l .. 4l + 11 of the block
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            if (b0 + 4 * lane + k + Q <= L) f((w >> (24 - 2 * (k + Q))) & kMask);
-        cur = nxt;
     }
 }
 
