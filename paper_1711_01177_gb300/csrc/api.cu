@@ -18,6 +18,12 @@ int check_device(const grim_bank* bank) {
     return dev == bank->device ? GRIM_OK : GRIM_EINVAL;
 }
 
+int device_slot() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+    return dev;
+}
+
 int sm_count() {
     static int cached[64] = {0};
     int dev = 0;

@@ -161,11 +161,13 @@ static int launch_q(const uint8_t* ref2bit, grim_bank* bank, cudaStream_t s) {
     const int64_t stage = 4 * (span / 16 + 3);
     if (stage <= kBuildStageBytes) {
         const size_t smem = smem_rows + (size_t)((stage + 15) & ~15LL);
-        static bool attr = false;
-        if (!attr && smem > 48 * 1024) {
+        static bool attr[64] = {};  // per device
+        const int slot = device_slot();
+        if (slot < 0) return GRIM_ENOTSUP;
+        if (!attr[slot] && smem > 48 * 1024) {
             GRIM_CUDA_TRY(cudaFuncSetAttribute(bank_build_staged_kernel<Q>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
+            attr[slot] = true;
         }
         bank_build_staged_kernel<Q><<<(unsigned)blocks, kBuildThreads, smem, s>>>(
             ref2bit, bank->len, bank->bin_len, bank->overlap, bank->n_bins, bins_per_cta, bank->bits);

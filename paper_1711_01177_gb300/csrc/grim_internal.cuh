@@ -122,6 +122,10 @@ int scan_noalloc_scratch(void** ptr, size_t* bytes);
 // nothing completes; *timed_out (host) = 1 when it gave up as designed.
 int launch_wait_selfcheck(unsigned long long limit_ns, cudaStream_t s, uint32_t* timed_out);
 
+// The current device as an index into per-device caches (kernel attributes
+// and occupancy are per device), or -1 when there is none below 64.
+int device_slot();
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 

@@ -784,10 +784,12 @@ static int launch_scan_q(const grim_bank* bank, const uint8_t* reads, const int6
     }
     {
         constexpr size_t smem = ScanSmem<Q>::kAlloc;
-        static bool attr = false;
-        if (!attr) {
+        static bool attr[64] = {};  // per device
+        const int slot = device_slot();
+        if (slot < 0) return GRIM_ENOTSUP;
+        if (!attr[slot]) {
             GRIM_CUDA_TRY(cudaFuncSetAttribute(scan_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
+            attr[slot] = true;
         }
         ScanParams P;
         P.bank = bank->bits;
