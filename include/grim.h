@@ -167,15 +167,17 @@ int grim_filter(const grim_bank* bank, const uint8_t* reads, const int64_t* read
  * read_offsets, cand_bins, cand_offsets, E in; pass out), with the meanings
  * of grim_filter.  The reads are processed in chunks of chunk_reads (<= 0:
  * an eighth of the reads, at least 65,536, the last eighth in four
- * quarters): each chunk's inputs are copied
- * in and its pass bytes copied out on two streams of the library's, while
- * the filter runs on `stream`, so that the copies of one chunk overlap the
- * filtering of another.  Page-locked host buffers let the copies overlap;
- * pageable ones work but are copied synchronously.  Synchronises `stream`
- * (pass is complete on return).  Device memory: two chunk slots from the
- * library's pool.  A chunk whose end offset (read or candidate) lies below
- * its start offset gives GRIM_EINVAL before any copy; other decreasing
- * offsets are flagged on the device as for grim_filter.
+ * quarters): each chunk's inputs are copied in and its pass bytes copied
+ * out on two streams of the library's, while the filter runs on `stream`,
+ * so that the copies of one chunk overlap the filtering of another.  The
+ * two copy streams and their events are created by the first call on a
+ * device and kept for later ones (a call made while another host thread
+ * uses them creates its own).  Page-locked host buffers let the copies
+ * overlap; pageable ones work but are copied synchronously.  Synchronises
+ * `stream` (pass is complete on return).  Device memory: two chunk slots
+ * from the library's pool.  A chunk whose end offset (read or candidate)
+ * lies below its start offset gives GRIM_EINVAL before any copy; other
+ * decreasing offsets are flagged on the device as for grim_filter.
  */
 int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                      const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,

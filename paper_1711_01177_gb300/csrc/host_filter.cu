@@ -13,6 +13,7 @@
 //     buffer; record "out(slot)".
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "grim_internal.cuh"
@@ -38,6 +39,30 @@ struct HostSlot {
     uint8_t* pass = nullptr;
     cudaEvent_t in = nullptr, done = nullptr, out = nullptr;
 };
+
+// The copy streams and events of one call.  Creating and destroying them
+// costs tens of microseconds at both ends of every call, so each device
+// keeps one set for reuse; a call that finds it in use (another host thread)
+// makes its own.
+struct CopyKit {
+    cudaStream_t si = nullptr, so = nullptr;
+    cudaEvent_t ev[7] = {};  // in, done, out of both slots; "ready"
+    cudaError_t create() {
+        cudaError_t e = cudaStreamCreateWithFlags(&si, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&so, cudaStreamNonBlocking);
+        for (int i = 0; i < 7 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        return e;
+    }
+    void destroy() {
+        for (cudaEvent_t& v : ev)
+            if (v) cudaEventDestroy(v), v = nullptr;
+        if (si) cudaStreamDestroy(si), si = nullptr;
+        if (so) cudaStreamDestroy(so), so = nullptr;
+    }
+};
+
+std::mutex g_kit_mu[64];
+CopyKit g_kit[64];
 
 }  // namespace
 }  // namespace grim
@@ -79,9 +104,22 @@ int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t*
         max_bases = nb > max_bases ? nb : max_bases;
         max_cands = nc > max_cands ? nc : max_cands;
     }
-    cudaStream_t sf = (cudaStream_t)stream, si = nullptr, so = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&si, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&so, cudaStreamNonBlocking);
+    cudaStream_t sf = (cudaStream_t)stream;
+    // this device's cached streams and events when free, else a set of our own
+    const int slot_dev = grim::device_slot();
+    std::unique_lock<std::mutex> kit_lock;
+    grim::CopyKit own, *kit = &own;
+    cudaError_t e = cudaSuccess;
+    if (slot_dev >= 0) {
+        kit_lock = std::unique_lock<std::mutex>(grim::g_kit_mu[slot_dev], std::try_to_lock);
+        if (kit_lock.owns_lock()) {
+            kit = &grim::g_kit[slot_dev];
+            if (!kit->si) e = kit->create();
+            if (e != cudaSuccess) kit->destroy();
+        }
+    }
+    if (kit == &own) e = own.create();
+    cudaStream_t si = kit->si, so = kit->so;
     grim::HostSlot slot[2];
     int64_t *ro_all = nullptr, *co_all = nullptr;
     uint16_t* E_all = nullptr;
@@ -95,12 +133,11 @@ int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t*
         if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.co, (size_t)(max_nr + 1) * 8, sf);
         if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.cb, (size_t)max_cands * 4, sf);
         if (e == cudaSuccess) e = grim::scratch_alloc((void**)&s.pass, (size_t)max_cands, sf);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.in, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.out, cudaEventDisableTiming);
+        s.in = kit->ev[3 * i];
+        s.done = kit->ev[3 * i + 1];
+        s.out = kit->ev[3 * i + 2];
     }
-    cudaEvent_t ready = nullptr;  // the slots' memory exists on the filter stream
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    cudaEvent_t ready = kit->ev[6];  // the slots' memory exists on the filter stream
     if (e == cudaSuccess) e = cudaEventRecord(ready, sf);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(si, ready, 0);
     // every read's offsets and E, once
@@ -135,12 +172,13 @@ int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t*
         if (e == cudaSuccess && nc > 0) e = cudaMemcpyAsync(pass + co0, s.pass, (size_t)nc, cudaMemcpyDeviceToHost, so);
         if (e == cudaSuccess) e = cudaEventRecord(s.out, so);
     }
-    // the caller's stream completes once every copy out has
-    for (int i = 0; i < 2; i++)
-        if (slot[i].out && e == cudaSuccess) e = cudaStreamWaitEvent(sf, slot[i].out, 0);
-    cudaError_t e2 = cudaStreamSynchronize(so);
+    // the caller's stream completes once every copy out has (a slot's "out"
+    // event is recorded only when a chunk used the slot)
+    for (int64_t i = 0; i < 2 && i < n_chunks; i++)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sf, slot[i].out, 0);
+    cudaError_t e2 = so ? cudaStreamSynchronize(so) : cudaSuccess;
     if (e == cudaSuccess) e = e2;
-    e2 = cudaStreamSynchronize(si);
+    e2 = si ? cudaStreamSynchronize(si) : cudaSuccess;
     if (e == cudaSuccess) e = e2;
     for (int i = 0; i < 2; i++) {
         grim::HostSlot& s = slot[i];
@@ -153,14 +191,8 @@ int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t*
     if (E_all) cudaFreeAsync(E_all, sf);
     e2 = cudaStreamSynchronize(sf);
     if (e == cudaSuccess) e = e2;
-    for (int i = 0; i < 2; i++) {
-        if (slot[i].in) cudaEventDestroy(slot[i].in);
-        if (slot[i].done) cudaEventDestroy(slot[i].done);
-        if (slot[i].out) cudaEventDestroy(slot[i].out);
-    }
-    if (ready) cudaEventDestroy(ready);
-    if (si) cudaStreamDestroy(si);
-    if (so) cudaStreamDestroy(so);
+    // the cached set stays for the next call unless something failed
+    if (kit == &own || e != cudaSuccess) kit->destroy();
     if (e != cudaSuccess) {
         grim::set_last_cuda_error(e);
         return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;

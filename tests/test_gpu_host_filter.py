@@ -74,3 +74,33 @@ def test_host_filter_rejects_a_chunk_whose_offsets_run_backwards(work):
         grim.grim_filter_host(bank, host(w.bases, False), host(off, False), host(w.cand_bins, False),
                               host(w.cand_offsets, False), host(w.E, False), pass_out=out, chunk_reads=1000)
     assert e.value.status == grim.GRIM_EINVAL
+
+
+def test_host_filter_from_two_threads(work):
+    """Two host threads at once, each on its own stream: one call takes the
+    device's cached copy streams, the other makes its own; both give the
+    oracle's bytes, and repeated calls reuse the cached set."""
+    import threading
+    w, op, bank = work
+    ins = [host(w.bases, True), host(w.read_offsets, True), host(w.cand_bins, True),
+           host(w.cand_offsets, True), host(w.E, True)]
+    outs = [torch.full((w.n_checks,), 0xAA, dtype=torch.uint8).pin_memory() for _ in range(4)]
+    errors = []
+
+    def run(k):
+        try:
+            s = torch.cuda.Stream()
+            for rep in range(2):
+                grim.grim_filter_host(bank, *ins, pass_out=outs[2 * k + rep], chunk_reads=997, stream=s)
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    th = [threading.Thread(target=run, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
+    assert grim.grim_bank_status(bank) == (grim.GRIM_OK, 0)
+    for o in outs:
+        assert np.array_equal(o.numpy(), op)
