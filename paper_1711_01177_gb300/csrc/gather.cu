@@ -25,7 +25,8 @@
 //      planes);
 //   4. candidate rows stream through the warp as 16-byte vectors,
 //      lanes_per_row lanes per row (4 lanes x 32 bytes for q=5: 8 rows per
-//      warp step); each row is requested three steps before it is scored,
+//      warp step); each row is requested one step (q <= 5, with 4 CTAs of
+//      64 registers per SM) or three steps (q = 6) before it is scored,
 //      its id taken from a prefetched window of 32 candidate ids; rows are
 //      ANDed with the planes and popcounted, and the lanes' shares of the
 //      window's 32 rows are combined by shuffles as the steps finish
@@ -115,7 +116,9 @@ template <int Q>
 struct Stream {
     using G = GatherGeo<Q>;
     static constexpr int kWinSteps = 32 / G::kBPS;       // steps per id window
-    static constexpr int kBufs = kWinSteps >= 4 ? 4 : kWinSteps;  // row buffers; divides kWinSteps
+    // row buffers (a divisor of kWinSteps): two for q <= 5, whose smaller
+    // register budget lets 4 CTAs share an SM; four for q = 6
+    static constexpr int kBufs = (Q <= 5 && kWinSteps >= 2) ? 2 : (kWinSteps >= 4 ? 4 : kWinSteps);
     static constexpr int kAhead = kBufs - 1;                      // steps a row is requested early
     static_assert(kWinSteps % kBufs == 0, "buffer rotation must repeat every window");
     uint32_t win_cur, win_next;  // candidate ids c = base + lane, base + 32 + lane
@@ -468,7 +471,7 @@ __device__ __forceinline__ int64_t cost_share(int64_t total, int64_t i, int64_t 
 //    which also absorbs speed differences between SMs; the batched filter
 //    resets it before each launch of its graph.
 template <int Q, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 24 / WARPS)
+__global__ void __launch_bounds__(WARPS * 32, (Q >= 6 ? 24 : 32) / WARPS)
 gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* __restrict__ reads,
               const int64_t* __restrict__ read_offsets, int64_t n_reads, const uint32_t* __restrict__ cand_bins,
               const int64_t* __restrict__ cand_offsets, const uint16_t* __restrict__ E,
