@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--sub-steps", type=int, default=3, help="timed steps of the sub-measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="--impl reference: target CPU time of the whole run (warm-up + timed steps)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched sub-measurement")
     ap.add_argument("--no-full-scan", action="store_true", help="skip the full-scan sub-measurement")
     ap.add_argument("--no-mixed", action="store_true", help="skip the dispatcher (mixed) sub-measurement")
@@ -682,7 +684,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    per_step = min(20.0, max(0.05, args.ref_seconds / max(1, args.steps + args.warmup)))
     o = oracle.Oracle()
     if args.workload == "fullscan":
         import synth
