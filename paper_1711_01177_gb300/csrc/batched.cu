@@ -195,7 +195,8 @@ int grim_autotune(const grim_bank* bank, const uint8_t* reads, const int64_t* re
     GRIM_CUDA_TRY(cudaMemcpyAsync(&bounds[0], cand_offsets, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     GRIM_CUDA_TRY(cudaMemcpyAsync(&bounds[1], cand_offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     GRIM_CUDA_TRY(cudaStreamSynchronize(s));
-    if (best_ms > 0 && bounds[1] > bounds[0]) grim::record_gather_rate(bank, (bounds[1] - bounds[0]) / (best_ms * 1e-3));
+    if (best_ms > 0 && bounds[1] > bounds[0])
+        grim::record_gather_rate(bank, (bounds[1] - bounds[0]) / (best_ms * 1e-3));
     best.use_graph = 1;
     *out = best;
     std::lock_guard<std::mutex> lock(g_tune_mu);

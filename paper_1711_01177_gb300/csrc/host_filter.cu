@@ -153,7 +153,8 @@ int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t*
         const int64_t ro0 = read_offsets[r0], co0 = cand_offsets[r0];
         const int64_t nb = read_offsets[r1] - ro0, nc = cand_offsets[r1] - co0;
         if (c >= 2) e = cudaStreamWaitEvent(si, s.done, 0);  // chunk c - 2 no longer reads the slot
-        if (e == cudaSuccess && nb > 0) e = cudaMemcpyAsync(s.reads, reads + ro0, (size_t)nb, cudaMemcpyHostToDevice, si);
+        if (e == cudaSuccess && nb > 0)
+            e = cudaMemcpyAsync(s.reads, reads + ro0, (size_t)nb, cudaMemcpyHostToDevice, si);
         if (e == cudaSuccess && nc > 0)
             e = cudaMemcpyAsync(s.cb, cand_bins + co0, (size_t)nc * 4, cudaMemcpyHostToDevice, si);
         if (e == cudaSuccess) e = cudaEventRecord(s.in, si);
