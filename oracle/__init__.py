@@ -43,6 +43,7 @@ def _bind(lib):
         "oracle_filter": (I32, [P, I64, I32, P, P, I64, P, P, P, P, P]),
         "oracle_scan": (I64, [P, I64, I32, P, P, I64, P, I64, I64, I64, P, P, P]),
         "oracle_bin_row": (I32, [P, I64, I32, I32, I32, I64, P]),
+        "oracle_filter_rows": (I32, [P, I64, I32, I32, I32, P, P, I64, P, P, P, P, P]),
         "oracle_sellers": (I64, [P, I64, P, I64]),
         "oracle_seed_candidates": (I64, [P, I64, I32, P, P, I64, I32, I64, I32, I64, P, P]),
         "oracle_locate": (I64, [P, P, P, I64, P, I64, I32, I32, I64, P, P, P, P, P, I64]),
@@ -150,6 +151,24 @@ class Oracle:
         cnt2 = self.lib.oracle_scan(*args, cnt, _p(pr), _p(pb), _p(ps))
         assert cnt2 == cnt
         return pr, pb, ps
+
+    def filter_rows(self, ref2bit: np.ndarray, length: int, q: int, bin_len: int, overlap: int, reads: np.ndarray,
+                    read_offsets: np.ndarray, cand_bins: np.ndarray, cand_offsets: np.ndarray, E: np.ndarray):
+        """filter() with every candidate's bitvector rebuilt from the reference
+        (no bank).  Returns (pass u8, sums u32) aligned with cand_bins."""
+        n = len(read_offsets) - 1
+        nc = int(cand_offsets[-1]) - int(cand_offsets[0]) if n > 0 else 0
+        co = np.ascontiguousarray(cand_offsets, dtype=np.int64) - int(cand_offsets[0])
+        ro = np.ascontiguousarray(read_offsets, dtype=np.int64) - int(read_offsets[0])
+        pass_ = np.empty(nc, dtype=np.uint8)
+        sums = np.empty(nc, dtype=np.uint32)
+        rc = self.lib.oracle_filter_rows(_p(np.ascontiguousarray(ref2bit, dtype=np.uint8)), length, q, bin_len,
+                                         overlap, _p(np.ascontiguousarray(reads, dtype=np.uint8)), _p(ro), n,
+                                         _p(np.ascontiguousarray(cand_bins, dtype=np.uint32)), _p(co),
+                                         _p(np.ascontiguousarray(E, dtype=np.uint16)), _p(pass_), _p(sums))
+        if rc != 0:
+            raise ValueError(f"oracle_filter_rows: {rc}")
+        return pass_, sums
 
     def bin_row(self, ref2bit: np.ndarray, length: int, q: int, bin_len: int, overlap: int, b: int) -> np.ndarray:
         row = np.empty(4 ** q, dtype=np.uint8)

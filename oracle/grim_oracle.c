@@ -218,6 +218,41 @@ int oracle_bin_row(const uint8_t* ref2bit, int64_t len, int q, int bin_len, int 
 }
 
 /*
+ * oracle_filter for a candidate list without a bank: every candidate's
+ * bitvector is rebuilt from the reference by oracle_bin_row (Sec. 3.1) and
+ * handed to oracle_filter as a one-bin bank (Sec. 3.2 steps 1-5).  For
+ * genome-scale references, whose byte-per-bit bank would not fit in memory.
+ * Returns ORACLE_EDATA on a code > 3 or a bin id >= n_bins, ORACLE_EINVAL /
+ * ORACLE_ENOMEM otherwise on failure.
+ */
+int oracle_filter_rows(const uint8_t* ref2bit, int64_t len, int q, int bin_len, int overlap,
+                       const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
+                       const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E,
+                       uint8_t* pass, uint32_t* sums) {
+    if (len <= 0 || q < 1 || q > 8 || bin_len <= 0 || overlap < 0) return ORACLE_EINVAL;
+    int64_t n_bins = oracle_n_bins(len, bin_len);
+    uint8_t* row = (uint8_t*)malloc((size_t)oracle_bits_per_bin(q));
+    if (!row) return ORACLE_ENOMEM;
+    int rc = ORACLE_OK;
+    const uint32_t bin0 = 0;
+    for (int64_t r = 0; r < n_reads && rc == ORACLE_OK; r++) {
+        const uint8_t* read = reads + read_offsets[r];
+        const int64_t one_read[2] = {0, read_offsets[r + 1] - read_offsets[r]};
+        const int64_t one_cand[2] = {0, 1};
+        for (int64_t c = cand_offsets[r]; c < cand_offsets[r + 1] && rc == ORACLE_OK; c++) {
+            if (cand_bins[c] >= n_bins) {
+                rc = ORACLE_EDATA;
+                break;
+            }
+            oracle_bin_row(ref2bit, len, q, bin_len, overlap, cand_bins[c], row);
+            rc = oracle_filter(row, 1, q, read, one_read, 1, &bin0, one_cand, E + r, pass + c, sums ? sums + c : 0);
+        }
+    }
+    free(row);
+    return rc;
+}
+
+/*
  * Sellers' semi-global edit distance: the fewest substitutions, insertions
  * and deletions that turn the read into some substring of text.  Used by
  * the tests to pin the zero-miss property the paper claims (Sec. 3.2:

@@ -168,6 +168,15 @@ def test_filter_matches_brute_force(oracle):
             n_tok = max(L - q + 1, 0)
             assert pass_[c] == int(s >= n_tok - q * int(E[r]))
     assert sums.max() > 0 and pass_.sum() > 0 and pass_.sum() < len(pass_)
+    # the bank-free form rebuilds each candidate's row from the reference:
+    # the same bytes, also for a slice of reads with its own offsets
+    r2 = synth.pack2bit(codes)
+    p2, s2 = oracle.filter_rows(r2, n, q, bl, ov, reads, offs, cb, co, E)
+    assert np.array_equal(p2, pass_) and np.array_equal(s2, sums)
+    a, z = 5, 20
+    p3, s3 = oracle.filter_rows(r2, n, q, bl, ov, reads[offs[a]:offs[z]], offs[a:z + 1], cb[co[a]:co[z]],
+                                co[a:z + 1], E[a:z])
+    assert np.array_equal(p3, pass_[co[a]:co[z]]) and np.array_equal(s3, sums[co[a]:co[z]])
 
 
 def test_aaaaa_example(oracle):
