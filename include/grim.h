@@ -86,6 +86,61 @@ const char* grim_strerror(int status);
 int grim_last_cuda_error(void);
 
 /*
+ * Host-side fault injection, so that callers and tests can walk the
+ * library's error paths (GRIM_ENOMEM, GRIM_ECUDA and the clean-up behind
+ * them) without making the GPU fail.  The paper has no counterpart.
+ *   kind GRIM_FAULT_ALLOC:  the nth device or page-locked host allocation
+ *        the library makes from now on fails as if memory were exhausted:
+ *        nothing is allocated and the call making it returns GRIM_ENOMEM
+ *        (grim_last_cuda_error() = cudaErrorMemoryAllocation).
+ *   kind GRIM_FAULT_LAUNCH: the nth kernel launch from now on is made with
+ *        an empty grid, which the CUDA runtime rejects before anything runs
+ *        on the device; the call returns GRIM_ECUDA
+ *        (grim_last_cuda_error() = cudaErrorInvalidConfiguration).
+ *   kind GRIM_FAULT_NONE:   disarm.
+ * One fault is armed at a time (a new one replaces it); events on every
+ * host thread count towards it; it fires once and disarms itself.  nth >= 1
+ * (else GRIM_EINVAL).  The environment variable GRIM_FAULT=alloc:N or
+ * launch:N arms the same fault when the library is first used.
+ * grim_fault_pending returns the armed kind (GRIM_FAULT_NONE once it has
+ * fired) and, in *left (nullable), how many more events until it fires.
+ * Neither call touches the GPU.
+ */
+/*
+ * Roofline denominators measured on the current device: the rates the
+ * benchmark divides its achieved figures by.  The paper has no counterpart.
+ *   GRIM_PEAK_L2_READ        work = bytes of a buffer that fits the L2 (a
+ *                            multiple of 16, <= 64 MiB), read 40 times with
+ *                            16-byte L2-only loads by every SM; *units =
+ *                            bytes read.
+ *   GRIM_PEAK_E4M3           one CTA per SM issues `work` dense tcgen05 MMAs
+ *                            of 128 x 256 x 32 (kind::f8f6f4, e4m3), both
+ *                            operands in shared memory; *units = flops.
+ *   GRIM_PEAK_MXF4           the same for kind::mxf4 (e2m1, K = 64, unit
+ *                            block scales).
+ *   GRIM_PEAK_MXF4_TMEM_A, GRIM_PEAK_E4M3_TMEM_A   the same with A in tensor
+ *                            memory (the full scan's arrangement).
+ *   GRIM_PEAK_INT8_MMA_SYNC  `work` trips of 8 legacy mma.sync m16n8k32 s8 per
+ *                            warp, 32 warps per SM; *units = integer ops.
+ * *ms = CUDA-event time of the timed launch on `stream`, after one warm-up
+ * launch.  Synchronises `stream`; scratch from the library's pool.
+ * GRIM_ETIMEOUT if an MMA pipeline wait ran out (bounded, 2 s).
+ */
+#define GRIM_PEAK_L2_READ 1
+#define GRIM_PEAK_E4M3 2
+#define GRIM_PEAK_MXF4 3
+#define GRIM_PEAK_MXF4_TMEM_A 4
+#define GRIM_PEAK_E4M3_TMEM_A 5
+#define GRIM_PEAK_INT8_MMA_SYNC 6
+int grim_peak(int kind, int64_t work, double* units, float* ms, void* stream);
+
+#define GRIM_FAULT_NONE 0
+#define GRIM_FAULT_ALLOC 1
+#define GRIM_FAULT_LAUNCH 2
+int grim_fault_inject(int kind, int64_t nth);
+int grim_fault_pending(int64_t* left);
+
+/*
  * Build the bank: the existence bitvector of every bin (Sec. 3.1, Fig. 2;
  * generated once per reference).
  *   ref2bit  device, (len+3)/4 bytes: base k in bits 2*(k%4) of byte k/4.
@@ -107,17 +162,35 @@ int grim_last_cuda_error(void);
 int grim_build_bank(const uint8_t* ref2bit, int64_t len, int q, int bin_len, int overlap, void* stream,
                     grim_bank** out);
 
-/* Geometry and device address of a bank (any output pointer may be NULL). */
+/*
+ * Recompute every row of an existing bank from a reference of the bank's
+ * length (Sec. 3.1): the build of grim_build_bank without its allocation -
+ * for a reference edited in place, or to time the build kernel alone.
+ * ref2bit as for grim_build_bank, (len + 3) / 4 bytes with len the bank's.
+ * Enqueues on `stream`; allocates nothing.
+ */
+int grim_build_bank_into(grim_bank* bank, const uint8_t* ref2bit, void* stream);
+
+/* Geometry and device address of a bank (any output pointer may be NULL):
+ * the bin partition and bitvector layout that grim_build_bank made from
+ * Sec. 3.1 / Fig. 2 (bins of bin_len bases plus overlap, one 4^q-bit
+ * existence bitvector each).  The query itself has no counterpart in the
+ * paper. */
 int grim_bank_info(const grim_bank* bank, int64_t* len, int64_t* n_bins, int* q, int* bin_len, int* overlap,
                    int64_t* row_words, const uint32_t** bits);
 
 /* Synchronise `stream`, then read and clear the bank's device status word.
  * *flags (nullable) receives the GRIM_FLAG_* bits raised since the last
  * call by any call that used this bank.  Returns GRIM_EDATA if a data flag
- * is set, GRIM_EOVERFLOW / GRIM_ETIMEOUT for those flags, else GRIM_OK. */
+ * is set, GRIM_EOVERFLOW / GRIM_ETIMEOUT for those flags, else GRIM_OK.
+ * The paper has no counterpart: its filter assumes valid input (Sec. 3.2
+ * is silent on codes other than A, C, G, T), and this call is how the
+ * device-side checks of this library report what they found. */
 int grim_bank_status(grim_bank* bank, void* stream, uint32_t* flags);
 
-/* Free the bank (synchronises the device first). NULL is a no-op. */
+/* Free the bank (synchronises the device first). NULL is a no-op.  The
+ * paper has no counterpart (its bitvectors live in the memory for as long
+ * as the reference is mapped against, Sec. 3.1 / 4.2). */
 int grim_bank_free(grim_bank* bank);
 
 /*
@@ -195,7 +268,9 @@ typedef struct grim_tune {
 } grim_tune;
 
 /*
- * Batched gather filter: the same outputs as grim_filter, computed by one
+ * Batched gather filter: the five steps of Sec. 3.2 / Fig. 3 for every
+ * (read, candidate bin) pair, as in grim_filter, with the same outputs,
+ * computed by one
  * launch per batch of `batch_reads` reads in which every warp claims reads
  * from a device work counter, so reads of uneven length and uneven
  * candidate lists balance across the GPU.  With use_graph, the call's
@@ -206,7 +281,9 @@ typedef struct grim_tune {
  * defaults with use_graph = 1.  The graph cache is host state of the bank:
  * calls on one bank from several host threads must be serialised.  The
  * work counters live in the bank: batched calls on one bank that overlap
- * on the GPU without a graph of their own must be serialised.
+ * on the GPU without a graph of their own must be serialised.  The
+ * batching, the work counter and the graph have no counterpart in the
+ * paper, whose filter logic checks one read at a time (Sec. 4.2).
  */
 int grim_filter_batched(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                         const uint32_t* cand_bins, const int64_t* cand_offsets, const uint16_t* E, uint8_t* pass,
@@ -290,9 +367,9 @@ int grim_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_o
  * (64 MiB) compiled into the library: every GPU on which the library is
  * loaded holds it until the process exits.  A call needing more is
  * rejected with GRIM_ESCRATCH before anything is enqueued; the need is
- * 256 + sum over c = 0, 1, 2 of ceil(n_reads / (128 >> c)) * 128 * K bytes
- * (K = max(128, 4^q)) plus two small index arrays per c, which allows at
- * most 9,312 reads per call at q = 5, 36,928 at q = 4, 72,928 at q <= 3.
+ * 256 + sum over c = 0 .. 3 of ceil(n_reads / (128 >> c)) * 128 * K / 2
+ * bytes (K = max(256, 4^q)) plus two small index arrays per c, which allows
+ * at most 8,688 reads per call at q = 5 and 34,368 at q <= 4.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any
  * stream capture.  Every call uses the same array and finds the previous
@@ -300,6 +377,11 @@ int grim_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_o
  * calls whose work overlaps on the GPU - on different streams or from
  * different host threads - race on it: the caller must serialise them.
  */
+/* The tcgen05 MMA kind the full scan runs on ("f8f6f4": e4m3 operands, or
+ * "mxf4": e2m1 operands with unit block scales); static storage.  The paper
+ * has no counterpart. */
+const char* grim_scan_mma_kind(void);
+
 #define GRIM_SCAN_NOALLOC_SCRATCH_BYTES (64ull << 20)
 int grim_scan_noalloc(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                       const uint16_t* E, int64_t bin_begin, int64_t bin_end, uint32_t* pair_read, uint32_t* pair_bin,

@@ -39,6 +39,8 @@ SIGNATURES = {
     "grim_fill_E_rate": (_I32, [_P, _I64, _I32, _I32, _I32, _P, _P]),
     "grim_build_bank": (_I32, [_P, _I64, _I32, _I32, _I32, _P, ctypes.POINTER(_P)]),
     "grim_bank_info": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "grim_build_bank_into": (_I32, [_P, _P, _P]),
+    "grim_scan_mma_kind": (ctypes.c_char_p, []),
     "grim_bank_status": (_I32, [_P, _P, ctypes.POINTER(_U32)]),
     "grim_bank_free": (_I32, [_P]),
     "grim_filter": (_I32, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
@@ -60,7 +62,13 @@ SIGNATURES = {
     "grim_verify": (_I32, [_P, _P, _P, _P, _I64, _P, _P, _I64, _P, _P]),
     "grim_map": (_I32, [_P, _P, _P, _P, _P, _I64, _P, _I32, _I64, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P, _P]),
     "grim_verify_stats": (_I32, [_P, _P, _P, _P, _I64, _I64, _P, _P]),
+    "grim_fault_inject": (_I32, [_I32, _I64]),
+    "grim_peak": (_I32, [_I32, _I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), _P]),
+    "grim_fault_pending": (_I32, [ctypes.POINTER(_I64)]),
 }
+GRIM_FAULT_NONE, GRIM_FAULT_ALLOC, GRIM_FAULT_LAUNCH = 0, 1, 2
+(GRIM_PEAK_L2_READ, GRIM_PEAK_E4M3, GRIM_PEAK_MXF4, GRIM_PEAK_MXF4_TMEM_A, GRIM_PEAK_E4M3_TMEM_A,
+ GRIM_PEAK_INT8_MMA_SYNC) = range(1, 7)
 GRIM_FORM_GATHER, GRIM_FORM_SCAN = 0, 1
 
 
@@ -108,6 +116,28 @@ def load(path: str | None = None):
 def grim_wait_selfcheck(limit_ns: int, stream=None) -> int:
     """Status of the bounded-wait diagnostic (GRIM_ETIMEOUT when it works)."""
     return load().grim_wait_selfcheck(limit_ns, _stream_ptr(stream))
+
+
+def grim_fault_inject(kind: int, nth: int = 1) -> None:
+    """Arm the library's host-side fault injection: the nth allocation
+    (GRIM_FAULT_ALLOC) or kernel launch (GRIM_FAULT_LAUNCH) from now on
+    fails; GRIM_FAULT_NONE disarms."""
+    _check(load().grim_fault_inject(kind, nth), "grim_fault_inject")
+
+
+def grim_fault_pending() -> tuple[int, int]:
+    """(armed kind, events left before it fires); (GRIM_FAULT_NONE, 0) once fired."""
+    left = ctypes.c_int64(0)
+    kind = load().grim_fault_pending(ctypes.byref(left))
+    return kind, left.value
+
+
+def grim_peak(kind: int, work: int, stream=None) -> tuple[float, float]:
+    """(units, ms) of one timed peak launch: bytes (GRIM_PEAK_L2_READ) or
+    flops / ops (the tensor kinds) and its CUDA-event time."""
+    u, t = ctypes.c_double(), ctypes.c_float()
+    _check(load().grim_peak(kind, work, ctypes.byref(u), ctypes.byref(t), _stream_ptr(stream)), "grim_peak")
+    return u.value, t.value
 
 
 def grim_release_scratch() -> None:
@@ -198,6 +228,18 @@ def grim_build_bank(ref2bit: torch.Tensor, length: int, q: int, bin_len: int, ov
     _check(load().grim_build_bank(_dev_ptr(ref2bit, "ref2bit", 1), length, q, bin_len, overlap, _stream_ptr(stream),
                                   ctypes.byref(h)), "grim_build_bank")
     return Bank(h)
+
+
+def grim_build_bank_into(bank: Bank, ref2bit: torch.Tensor, stream=None) -> None:
+    """Recompute the bank's rows from a reference of its length (no allocation)."""
+    _check(load().grim_build_bank_into(bank.handle, _dev_ptr(ref2bit, "ref2bit", 1), _stream_ptr(stream)),
+           "grim_build_bank_into")
+
+
+def grim_scan_kind() -> str:
+    """The full scan's operand type as named in the peaks: "e4m3" or "mxf4"."""
+    k = load().grim_scan_mma_kind().decode()
+    return "e4m3" if k == "f8f6f4" else k
 
 
 def grim_bank_status(bank: Bank, stream=None):

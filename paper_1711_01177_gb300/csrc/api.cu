@@ -2,6 +2,9 @@
 // the library's scratch pool.
 #include <string.h>
 
+#include <stdlib.h>
+
+#include <atomic>
 #include <mutex>
 
 #include "grim_internal.cuh"
@@ -25,15 +28,15 @@ int device_slot() {
 }
 
 int sm_count() {
-    static int cached[64] = {0};
+    static DeviceCache cached[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (cached[dev] == 0) {
-        int n = 0;
+    int n = cached[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-        cached[dev] = n;
+        cached[dev].store(n, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return n;
 }
 
 // Working memory of the entry points comes from one stream-ordered pool per
@@ -62,7 +65,47 @@ static cudaMemPool_t scratch_pool(int dev) {
     return g_pool[dev];
 }
 
+// Fault injection: one armed fault at a time, counted down by the matching
+// events (allocations or kernel launches) of every thread; it fires once.
+// GRIM_FAULT=alloc:N or launch:N in the environment arms it when the
+// library is first used.
+static std::atomic<int> g_fault_kind{-1};  // -1: environment not read yet
+static std::atomic<long long> g_fault_left{0};
+
+static void fault_env_once() {
+    int expect = -1;
+    if (g_fault_kind.load() != -1) return;
+    int kind = GRIM_FAULT_NONE;
+    long long n = 0;
+    const char* v = getenv("GRIM_FAULT");
+    if (v) {
+        if (!strncmp(v, "alloc:", 6)) kind = GRIM_FAULT_ALLOC, n = atoll(v + 6);
+        else if (!strncmp(v, "launch:", 7)) kind = GRIM_FAULT_LAUNCH, n = atoll(v + 7);
+        if (n < 1) kind = GRIM_FAULT_NONE, n = 0;
+    }
+    g_fault_left.store(n);
+    g_fault_kind.compare_exchange_strong(expect, kind);
+}
+
+static bool fault_hit(int kind) {
+    fault_env_once();
+    if (g_fault_kind.load(std::memory_order_relaxed) != kind) return false;
+    const long long left = g_fault_left.fetch_sub(1) - 1;
+    if (left != 0) return false;
+    int k = kind;
+    g_fault_kind.compare_exchange_strong(k, GRIM_FAULT_NONE);  // fired: disarm
+    return true;
+}
+
+bool fault_alloc_now() { return fault_hit(GRIM_FAULT_ALLOC); }
+
+unsigned fault_grid(unsigned blocks) { return fault_hit(GRIM_FAULT_LAUNCH) ? 0u : blocks; }
+
 cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
+    if (fault_alloc_now()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -93,7 +136,8 @@ int new_bank(int64_t len, int q, int bin_len, int overlap, cudaStream_t s, grim_
     const size_t bytes = (size_t)n_bins * (size_t)rw * 4;
     const size_t tail = ((bytes + 255) & ~(size_t)255);  // status word, then the work counters
     void* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, tail + 256 + 8 * (1 + kGraphCache));
+    cudaError_t e = fault_alloc_now() ? cudaErrorMemoryAllocation
+                                      : cudaMalloc(&mem, tail + 256 + 8 * (1 + kGraphCache));
     if (e != cudaSuccess) {
         set_last_cuda_error(e);
         delete bank;
@@ -147,7 +191,7 @@ int grim_fill_E_rate(const int64_t* read_offsets, int64_t n_reads, int32_t num, 
     if (!read_offsets || !E) return GRIM_EINVAL;
     const int64_t need = (n_reads + 255) / 256;
     const int64_t cap = (int64_t)grim::sm_count() * 8;
-    grim::fill_E_rate_kernel<<<(unsigned)(need < cap ? need : cap), 256, 0, (cudaStream_t)stream>>>(
+    grim::fill_E_rate_kernel<<<grim::fault_grid((unsigned)(need < cap ? need : cap)), 256, 0, (cudaStream_t)stream>>>(
         read_offsets, n_reads, num, den, round_up != 0, E);
     GRIM_CUDA_TRY(cudaGetLastError());
     return GRIM_OK;
@@ -170,6 +214,27 @@ const char* grim_strerror(int status) {
 }
 
 int grim_last_cuda_error(void) { return grim::g_last_cuda_error; }
+
+int grim_fault_inject(int kind, int64_t nth) {
+    grim::fault_env_once();
+    if (kind == GRIM_FAULT_NONE) {
+        grim::g_fault_kind.store(GRIM_FAULT_NONE);
+        grim::g_fault_left.store(0);
+        return GRIM_OK;
+    }
+    if ((kind != GRIM_FAULT_ALLOC && kind != GRIM_FAULT_LAUNCH) || nth < 1) return GRIM_EINVAL;
+    grim::g_fault_kind.store(GRIM_FAULT_NONE);  // no event counts against a half-armed fault
+    grim::g_fault_left.store(nth);
+    grim::g_fault_kind.store(kind);
+    return GRIM_OK;
+}
+
+int grim_fault_pending(int64_t* left) {
+    grim::fault_env_once();
+    const int kind = grim::g_fault_kind.load();
+    if (left) *left = kind == GRIM_FAULT_NONE ? 0 : (int64_t)grim::g_fault_left.load();
+    return kind;
+}
 
 int grim_wait_selfcheck(unsigned long long limit_ns, void* stream) {
     uint32_t timed_out = 0;
@@ -208,6 +273,13 @@ int grim_build_bank(const uint8_t* ref2bit, int64_t len, int q, int bin_len, int
     }
     *out = bank;
     return GRIM_OK;
+}
+
+int grim_build_bank_into(grim_bank* bank, const uint8_t* ref2bit, void* stream) {
+    if (!bank || !ref2bit) return GRIM_EINVAL;
+    const int rc = grim::check_device(bank);
+    if (rc != GRIM_OK) return rc;
+    return grim::launch_bank_build(ref2bit, bank, (cudaStream_t)stream);
 }
 
 int grim_bank_info(const grim_bank* bank, int64_t* len, int64_t* n_bins, int* q, int* bin_len, int* overlap,

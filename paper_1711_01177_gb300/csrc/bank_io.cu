@@ -89,7 +89,8 @@ int grim_bank_save(const grim_bank* bank, const char* path, void* stream) {
     if (!f) return GRIM_EIO;
     unsigned char* stage = nullptr;
     cudaError_t e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&stage, grim::kChunk);
+    if (e == cudaSuccess)
+        e = grim::fault_alloc_now() ? cudaErrorMemoryAllocation : cudaMallocHost((void**)&stage, grim::kChunk);
     uint64_t sum = grim::checksum_init(h.payload);
     bool io_ok = fwrite(&h, sizeof(h), 1, f) == 1;  // checksum rewritten at the end
     const unsigned char* src = reinterpret_cast<const unsigned char*>(bank->bits);
@@ -109,7 +110,7 @@ int grim_bank_save(const grim_bank* bank, const char* path, void* stream) {
     if (stage) cudaFreeHost(stage);
     if (e != cudaSuccess) {
         grim::set_last_cuda_error(e);
-        return GRIM_ECUDA;
+        return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
     }
     return io_ok ? GRIM_OK : GRIM_EIO;
 }
@@ -143,7 +144,8 @@ int grim_bank_load(const char* path, void* stream, grim_bank** out) {
         return rc;
     }
     unsigned char* stage = nullptr;
-    cudaError_t e = cudaMallocHost((void**)&stage, grim::kChunk);
+    cudaError_t e =
+        grim::fault_alloc_now() ? cudaErrorMemoryAllocation : cudaMallocHost((void**)&stage, grim::kChunk);
     uint64_t sum = grim::checksum_init(h.payload);
     unsigned char* dst = reinterpret_cast<unsigned char*>(bank->bits);
     for (uint64_t done = 0; e == cudaSuccess && ok && done < h.payload; done += grim::kChunk) {
@@ -162,7 +164,7 @@ int grim_bank_load(const char* path, void* stream, grim_bank** out) {
         grim::delete_bank(bank);
         if (e != cudaSuccess) {
             grim::set_last_cuda_error(e);
-            return GRIM_ECUDA;
+            return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
         }
         return GRIM_EIO;
     }
@@ -178,7 +180,7 @@ int grim_pack_mask(const uint8_t* pass, int64_t n, uint32_t* bits, void* stream)
     const int64_t words = (n + 31) / 32;
     const int64_t need = (words + 255) / 256;
     const int64_t cap = (int64_t)grim::sm_count() * 16;
-    grim::pack_mask_kernel<<<(unsigned)(need < cap ? need : cap), 256, 0, s>>>(pass, n, ((uintptr_t)pass & 15) == 0,
+    grim::pack_mask_kernel<<<grim::fault_grid((unsigned)(need < cap ? need : cap)), 256, 0, s>>>(pass, n, ((uintptr_t)pass & 15) == 0,
                                                                              bits);
     GRIM_CUDA_TRY(cudaGetLastError());
     return GRIM_OK;

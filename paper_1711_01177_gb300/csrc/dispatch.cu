@@ -163,10 +163,10 @@ int grim_filter_auto(const grim_bank* bank, const uint8_t* reads, const int64_t*
                 cudaMemsetAsync(table, 0xFF, table_n * 8, s);
                 const int64_t ib = (np + grim::kJoinThreads - 1) / grim::kJoinThreads;
                 if (np > 0)
-                    grim::join_insert_kernel<<<(unsigned)(ib < 65535 ? ib : 65535), grim::kJoinThreads, 0, s>>>(
+                    grim::join_insert_kernel<<<grim::fault_grid((unsigned)(ib < 65535 ? ib : 65535)), grim::kJoinThreads, 0, s>>>(
                         pr, pb, np, 0, table, table_n - 1);
                 const int64_t lb = (n * 32 + grim::kJoinThreads - 1) / grim::kJoinThreads;
-                grim::join_lookup_kernel<<<(unsigned)(lb < 65535 ? lb : 65535), grim::kJoinThreads, 0, s>>>(
+                grim::join_lookup_kernel<<<grim::fault_grid((unsigned)(lb < 65535 ? lb : 65535)), grim::kJoinThreads, 0, s>>>(
                     cand_offsets + r0, n, 0, cand_bins, bank->n_bins, table, table_n - 1, pass, bank->status);
                 cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess) {

@@ -524,25 +524,25 @@ template <int Q, int WARPS>
 static int launch_range(const grim_bank* bank, const GatherArgs& a, int64_t r0, int64_t n, int per_sm, int claim,
                         unsigned long long* counter, cudaStream_t s) {
     constexpr size_t smem = gather_smem_bytes<Q>(WARPS);
-    static int max_blocks_of[64] = {};  // per device, like the attribute
+    static DeviceCache max_blocks_of[64];  // per device, like the attribute
     const int slot = device_slot();
     if (slot < 0) return GRIM_ENOTSUP;
-    if (max_blocks_of[slot] == 0) {
+    if (max_blocks_of[slot].load() == 0) {
         if (smem > 48 * 1024)
             GRIM_CUDA_TRY(
                 cudaFuncSetAttribute(gather_kernel<Q, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int b = 0;
         GRIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gather_kernel<Q, WARPS>, WARPS * 32, smem));
-        max_blocks_of[slot] = b > 0 ? b : 1;
+        max_blocks_of[slot].store(b > 0 ? b : 1);
     }
-    const int max_blocks = max_blocks_of[slot];
+    const int max_blocks = max_blocks_of[slot].load();
     if (per_sm <= 0 || per_sm > max_blocks) per_sm = max_blocks;
     if (claim <= 0) claim = 1;
     int64_t blocks = (int64_t)sm_count() * per_sm;
     const int64_t need = (n + (int64_t)WARPS * claim - 1) / ((int64_t)WARPS * claim);  // a claim per warp at least
     if (need < blocks) blocks = need;
     if (counter) GRIM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
-    gather_kernel<Q, WARPS><<<(unsigned)blocks, WARPS * 32, smem, s>>>(
+    gather_kernel<Q, WARPS><<<grim::fault_grid((unsigned)blocks), WARPS * 32, smem, s>>>(
         bank->bits, bank->n_bins, a.reads, a.read_offsets + r0, n, a.cand_bins, a.cand_offsets + r0, a.E + r0,
         a.pass, a.sums, bank->status, claim, counter);
     GRIM_CUDA_TRY(cudaGetLastError());

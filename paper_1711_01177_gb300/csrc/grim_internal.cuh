@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "grim.h"
@@ -68,6 +69,16 @@ inline int64_t row_words_for(int q) {
 // device (freed with cudaFreeAsync; kept cached until grim_release_scratch).
 cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s);
 
+// Host-side fault injection (grim_fault_inject).  fault_alloc_now(): true
+// when the allocation about to be made is the one armed to fail (the caller
+// then allocates nothing and reports cudaErrorMemoryAllocation).
+// fault_grid(blocks): the grid size of the launch about to be made -
+// `blocks`, or 0 when this launch is the one armed to fail; the runtime
+// rejects a zero grid (cudaErrorInvalidConfiguration) before anything runs
+// on the device, so the launch's error check takes its real failure path.
+bool fault_alloc_now();
+unsigned fault_grid(unsigned blocks);
+
 // Records the CUDA error of a failing call for grim_last_cuda_error.
 void set_last_cuda_error(cudaError_t e);
 
@@ -128,6 +139,12 @@ int device_slot();
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
+
+// Per-device caches of kernel attributes and occupancy are arrays of these:
+// several host threads may make their first call on one device at the same
+// time, so each entry is atomic (the work behind it is idempotent, and a
+// thread that finds 0 simply repeats it).
+using DeviceCache = std::atomic<int>;
 
 }  // namespace grim
 

@@ -6,32 +6,36 @@
 // on the tcgen05 tensor cores, exactly.
 //
 // Exactness.  sm_103a has no integer tcgen05 kind, so the contraction runs
-// on kind::f8f6f4 with e4m3 operands and f32 accumulation.  A = bank bits as
-// e4m3 0 / 2^-6.  B = the read's token counts split in base-16 digits
-// (count = sum_d 16^d * digit_d, digit_d in [0, 15], each digit exact in
-// e4m3); every digit of every read is its own B row, so one MMA yields
-// sum_t bit * digit_d for all (read, digit) rows at once, and the epilogue
-// recombines Sum = 64 * sum_d 16^d * acc_d.  Every product is 0 or a small
-// integer and every partial sum is below 2^24, so f32 accumulation is exact
-// and the pass decision is bit-identical to counting tokens one by one.
-// Reads whose counts stay below 16 (nearly all) take one row; reads with
-// counts up to 255 take two, longer repeats four; the prep kernel packs
-// reads into tiles of 128 rows by digit class (128 x 1, 64 x 2, 32 x 4).
+// on kind::mxf4: e2m1 operands (four-bit floats, two per byte), unit block
+// scales, f32 accumulation.  Token t = 32i + 4j + s of a row takes the K
+// position 32i + 8s + j, so that one bank word x (tokens 32i .. 32i+31)
+// becomes four A words by masking alone: x & 0x11111111 (slot s = 0, a set
+// bit reads as e2m1 0.5), x & 0x22222222 (s = 1, 1.0), x & 0x44444444
+// (s = 2, 2.0) and (x >> 1) & 0x44444444 (s = 3, 2.0).  B = the read's token
+// counts in base-4 digits (count = sum_d 4^d * digit_d, digit_d in 0..3),
+// each scaled by the inverse of its slot's A value (2 d, d, d / 2, d / 2 -
+// all exact in e2m1), so every product is the digit itself; every digit of
+// every read is its own B row, and the epilogue recombines
+// Sum = sum_d 4^d * acc_d.  Every partial sum is a small integer, so the f32
+// accumulation is exact and the pass decision is bit-identical to counting
+// tokens one by one.  Reads whose counts stay below 4 (nearly all) take one
+// row; counts up to 15, 255 and 65,535 take 2, 4 and 8; the prep kernel packs
+// reads into tiles of 128 rows by digit class (128 x 1, 64 x 2, 32 x 4, 16 x 8).
 //
 // Data flow per CTA (persistent, one per SM; a work item = one read tile x
 // one run of bin tiles):
-//   B   : the read tile's 128 digit rows x K bytes, staged once per work item
-//         in shared memory in the 128-byte-swizzled K-major layout;
+//   B   : the read tile's 128 digit rows x K/2 bytes, staged once per work
+//         item in shared memory in the 128-byte-swizzled K-major layout;
 //   bank: tiles of 128 bin rows stream through a 4-deep shared-memory ring
 //         by 1-D TMA bulk copies (warp 0);
 //   A   : warps 2-9 (one thread per bin = per TMEM lane; two groups of four
-//         warps taking alternate K chunks) expand 128 bits of their bin's row
-//         into 128 e4m3 bytes and store them straight into tensor memory (2
-//         stages of 128 columns = 512 tokens, 16 MMAs per stage) - the
-//         expanded operand never touches shared memory;
-//   MMA : warp 1 issues M=128 (bins) x N=128 (rows) x K=32 tcgen05.mma with A
-//         from TMEM, B from shared memory, accumulating in TMEM (two 128-column
-//         accumulators);
+//         warps taking alternate K chunks) mask 512 bits of their bin's row
+//         into 512 e2m1 values and store them straight into tensor memory
+//         (3 stages of 64 columns, 8 MMAs per stage) - the expanded operand
+//         never touches shared memory;
+//   MMA : warp 1 issues M=128 (bins) x N=128 (rows) x K=64 tcgen05.mma with A
+//         from TMEM, B from shared memory and the unit scale factors from
+//         TMEM, accumulating in TMEM (two 128-column accumulators);
 //   out : warps 10-13 read the accumulators with tcgen05.ld, recombine digits,
 //         compare with each read's threshold and append the rare passing
 //         (read, bin, sum) triples with warp-aggregated atomics.
@@ -40,6 +44,7 @@
 #include <mutex>
 
 #include "grim_internal.cuh"
+#include "tcgen05.cuh"
 #include "tokens.cuh"
 
 namespace grim {
@@ -58,37 +63,40 @@ constexpr int kEpilogueWarp0 = 10;  // epilogue warps 10..13
 constexpr int kBinTile = 128;       // bins per MMA tile (M, TMEM lanes)
 constexpr int kRowsTile = 128;      // B rows per read tile (N)
 constexpr int kBankStages = 4;
-constexpr int kAStages = 2;          // one per expander group
-constexpr int kACols = 128;         // TMEM columns per A stage (up to 512 K bytes)
+constexpr int kAStages = 3;         // A stages in tensor memory, filled by alternate expander groups
 constexpr int kAccCol = 0;          // two accumulators: columns [0, 256)
-constexpr int kACol = 256;          // A stages: columns [256, 512)
+constexpr int kSfCol = 256;         // unit scale factors of A and B: columns [256, 288)
+constexpr int kACol = 288;          // A stages: 3 x 64 columns from 288
 constexpr int kTmemCols = 512;
 constexpr int kPrepWarps = 8;
-constexpr int kNumClasses = 3;      // digit classes: 1, 2, 4 digits
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr int kNumClasses = 4;      // digit classes: 1, 2, 4, 8 base-4 digits
+constexpr int kMmaK = 64;           // e2m1 K elements per MMA (32 bytes of a row)
 
-__host__ __device__ constexpr int class_digits(int c) { return c == 0 ? 1 : (c == 1 ? 2 : 4); }
-__host__ __device__ constexpr int class_reads(int c) { return kRowsTile / class_digits(c); }
+__host__ __device__ constexpr int class_digits(int c) { return 1 << c; }
+__host__ __device__ constexpr int class_reads(int c) { return kRowsTile >> c; }
 
 template <int Q>
 struct ScanGeo {
     static constexpr int kRowWords = Geo<Q>::kRowWords;
     static constexpr int kRowBytes = kRowWords * 4;
-    static constexpr int kK = (1 << (2 * Q)) < 128 ? 128 : (1 << (2 * Q));  // padded token count
+    static constexpr int kK = (1 << (2 * Q)) < 256 ? 256 : (1 << (2 * Q));  // padded token count
+    static constexpr int kKBytes = kK / 2;                                   // a B row: two e2m1 per byte
     static constexpr int kChunkTok = kK >= 512 ? 512 : kK;                   // tokens per A stage
-    static constexpr int kVecPerChunk = kChunkTok / 128;                      // 16-byte row slices per stage
-    static constexpr int kMmaPerChunk = kChunkTok / 32;                       // K=32 MMAs per stage
+    static constexpr int kACols = kChunkTok / 8;                              // TMEM columns per A stage
+    static constexpr int kWordsPerChunk = kChunkTok / 32;                     // bank words per A stage
+    static constexpr int kMmaPerChunk = kChunkTok / kMmaK;                    // MMAs per A stage
     static constexpr int kChunks = kK / kChunkTok;
-    static constexpr int kBBytes = kRowsTile * kK;                            // staged B tile
+    static constexpr int kBBytes = kRowsTile * kKBytes;                       // staged B tile
     static constexpr int kBankTileBytes = kBinTile * kRowBytes;
-    static_assert(kRowBytes * 8 == kK, "a bank row holds exactly the padded K bits");
+    static_assert(kRowBytes * 8 <= kK, "a bank row fits the padded K");
+    static_assert(kKBytes % 128 == 0 && kACols <= 64, "B rows are whole 128-byte swizzle atoms");
 };
 
 // Scratch written by the prep kernel and read by the scan kernel.
 struct ScanScratch {
-    int32_t* class_count;  // [3] reads per digit class
+    int32_t* class_count;  // [4] reads per digit class
     int32_t* work;         // [1] work-item counter
-    uint8_t* rows[kNumClasses];   // digit rows, tiles of 128 rows x K bytes
+    uint8_t* rows[kNumClasses];   // digit rows, tiles of 128 rows x K/2 bytes (e2m1)
     int32_t* T[kNumClasses];      // thresholds per slot (INT_MAX: never passes)
     uint32_t* rid[kNumClasses];   // read index per slot
 };
@@ -102,56 +110,7 @@ struct ScanOut {
     uint32_t* read_pass;         // nullable, per read
 };
 
-// ------------------------------------------------------------ PTX helpers
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long now_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: false when the CTA is aborting or the time limit expired
-// (then the abort flag is raised for every role of the CTA).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          unsigned long long limit_ns = kWaitLimitNs) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = now_ns();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (now_ns() - t0 > limit_ns) {
-            *abort_flag = 1;
-            return false;
-        }
-    }
-}
+// ------------------------------------------------------------ bounded-wait self-check
 
 // The bounded wait above on a barrier that nothing completes: out = 1 when
 // it gave up with the abort flag raised, 0 otherwise.
@@ -170,120 +129,27 @@ __global__ void wait_selfcheck_kernel(unsigned long long limit_ns, uint32_t* out
     }
 }
 
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
+
+// e2m1 code of a base-4 digit d in token slot s (t % 4): the B value is the
+// digit divided by the slot's A value (0.5, 1, 2, 2), i.e. 2d, d, d/2, d/2:
+// codes {0, 4, 6, 7}, {0, 2, 4, 5}, {0, 1, 2, 3} (e2m1: 0, .5, 1, 1.5, 2, 3, 4, 6).
+__device__ __forceinline__ uint32_t e2m1_digit(uint32_t s, uint32_t d) {
+    constexpr unsigned long long kTab = 0x321054207640ull;  // nibble 4 * (4 * min(s, 2) + d)
+    return (uint32_t)(kTab >> (16 * (s < 2 ? s : 2) + 4 * d)) & 0xFu;
 }
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(
-            taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
-        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]),
-        "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]),
-        "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// D[tmem] (+)= A[tmem] x B[smem], kind::f8f6f4.
-__device__ __forceinline__ void mma_f8f6f4_tmemA(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
-                                                 uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_addr(bar))
-                 : "memory");
-}
-
-// Shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);   // start address
-    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
-    d |= (uint64_t)1 << 46;                   // descriptor version
-    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: f32 accumulate, A and B e4m3, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_f8(int M, int N) {
-    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// e4m3 bit pattern of an integer 0..15 (B digits)
-__device__ __forceinline__ uint32_t e4m3_small_int(uint32_t k) {
-    if (k == 0) return 0;
-    const uint32_t e = 31 - __clz(k);
-    const uint32_t m = ((k << 3) >> e) & 7u;
-    return ((e + 7u) << 3) | m;
-}
-
-// A operand: a set bit is e4m3 0x08 = 2^-6 (the smallest normal), a clear bit
-// 0.  Products with the B digits (0..15) and all partial sums (multiples of
-// 2^-6 below 2^8) are exact in f32; the epilogue scales back by 64.
-// Four bits n (bit i -> byte i): n * 0x01020408 puts bit i at bit 8i + 3 with
-// no overlapping copies, the mask keeps exactly those bits.
-__device__ __forceinline__ uint32_t expand_nibble(uint32_t n) { return (n * 0x01020408u) & 0x08080808u; }
-
-// 32 bits of a row -> 8 columns of A (4 tokens per column, token t in byte t%4).
-__device__ __forceinline__ void expand_word(uint32_t w, uint32_t* v) {
-    const uint32_t lo = w & 0x0F0F0F0Fu, hi = (w >> 4) & 0x0F0F0F0Fu;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        v[2 * k] = expand_nibble(__byte_perm(lo, 0u, 0x4440u | k));
-        v[2 * k + 1] = expand_nibble(__byte_perm(hi, 0u, 0x4440u | k));
-    }
+// A operand: bank word x (tokens 32i .. 32i+31) -> four e2m1 words, slot s
+// of token 32i + 4j + s in nibble j of word s.
+__device__ __forceinline__ void expand_word_fp4(uint32_t x, uint32_t* v) {
+    v[0] = x & 0x11111111u;
+    v[1] = x & 0x22222222u;
+    v[2] = x & 0x44444444u;
+    v[3] = (x >> 1) & 0x44444444u;
 }
 
 // ------------------------------------------------------------ prep kernel
 
-// Per read: token counts -> digit class -> digit rows (e4m3), threshold and
+// Per read: token counts -> digit class -> digit rows (e2m1), threshold and
 // read index at the read's slot in its class.
 template <int Q>
 __global__ void __launch_bounds__(kPrepWarps * 32)
@@ -300,7 +166,7 @@ scan_prep_kernel(const uint8_t* __restrict__ reads, const int64_t* __restrict__ 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t* counts = counts_all + warp * kCountWords;
-    constexpr int kTPL = G::kK / 32;  // tokens (bytes of a row) per lane
+    constexpr int kGroups = G::kK / 32;  // 32-token groups of a row: lane i < kGroups writes group i
     uint32_t flags = 0;
     const int64_t stride = (int64_t)gridDim.x * kPrepWarps;
     for (int64_t r = (int64_t)blockIdx.x * kPrepWarps + warp; r < n_reads; r += stride) {
@@ -325,38 +191,33 @@ scan_prep_kernel(const uint8_t* __restrict__ reads, const int64_t* __restrict__ 
             bad = true;
         }
         __syncwarp();
-        // this lane's tokens [lane*kTPL, (lane+1)*kTPL)
+        // this lane's tokens: group 32 * lane .. 32 * lane + 31 (lanes past
+        // the row's groups hold none)
+        uint32_t cnt[32];
         uint32_t mx = 0;
 #pragma unroll
-        for (int j = 0; j < kTPL; j++) {
-            const int t = lane * kTPL + j;
-            const uint32_t cnt = (counts[t >> 1] >> (16 * (t & 1))) & 0xFFFFu;
-            mx = cnt > mx ? cnt : mx;
+        for (int u = 0; u < 32; u++) {
+            const int t = 32 * lane + u;
+            cnt[u] = (lane < kGroups && !bad) ? (counts[t >> 1] >> (16 * (t & 1))) & 0xFFFFu : 0u;
+            mx = cnt[u] > mx ? cnt[u] : mx;
         }
         mx = __reduce_max_sync(kFull, mx);
-        const int cls = bad ? 0 : (mx <= 15u ? 0 : (mx <= 255u ? 1 : 2));
+        const int cls = mx <= 3u ? 0 : (mx <= 15u ? 1 : (mx <= 255u ? 2 : 3));
         int slot = 0;
         if (lane == 0) slot = atomicAdd(&sc.class_count[cls], 1);
         slot = __shfl_sync(kFull, slot, 0);
         const int nD = class_digits(cls), nR = class_reads(cls);
         const int tile = slot / nR, n = slot % nR;
-        uint8_t* tile_rows = sc.rows[cls] + (size_t)tile * kRowsTile * G::kK;
+        uint8_t* tile_rows = sc.rows[cls] + (size_t)tile * G::kBBytes;
         for (int d = 0; d < nD; d++) {
-            uint32_t packed[kTPL / 4 > 0 ? kTPL / 4 : 1];
+            // word s of the group: token 32 * lane + 4j + s in nibble j
+            uint4 packed = make_uint4(0, 0, 0, 0);
+            uint32_t* pw = reinterpret_cast<uint32_t*>(&packed);
 #pragma unroll
-            for (int w = 0; w < (kTPL / 4 > 0 ? kTPL / 4 : 1); w++) {
-                uint32_t word = 0;
-#pragma unroll
-                for (int b = 0; b < 4; b++) {
-                    const int t = lane * kTPL + 4 * w + b;
-                    const uint32_t cnt = bad ? 0u : ((counts[t >> 1] >> (16 * (t & 1))) & 0xFFFFu);
-                    word |= e4m3_small_int((cnt >> (4 * d)) & 15u) << (8 * b);
-                }
-                packed[w] = word;
-            }
-            uint32_t* dst = reinterpret_cast<uint32_t*>(tile_rows + (size_t)(d * nR + n) * G::kK + lane * kTPL);
-#pragma unroll
-            for (int w = 0; w < (kTPL / 4 > 0 ? kTPL / 4 : 1); w++) dst[w] = packed[w];
+            for (int u = 0; u < 32; u++)
+                pw[u & 3] |= e2m1_digit(u & 3, (cnt[u] >> (2 * d)) & 3u) << (4 * (u >> 2));
+            if (lane < kGroups)
+                *reinterpret_cast<uint4*>(tile_rows + (size_t)(d * nR + n) * G::kKBytes + 16 * lane) = packed;
         }
         if (lane == 0) {
             const int n_tok = L - Q + 1 > 0 ? L - Q + 1 : 0;
@@ -429,10 +290,10 @@ __device__ __forceinline__ void scan_emit(const ScanParams& P, const int* sums, 
     }
 }
 
-// Epilogue of one work item for reads with D base-16 digits (N = 128 / D
+// Epilogue of one work item for reads with D base-4 digits (N = 128 / D
 // reads per tile): thread = bin row = TMEM lane of its warp's quadrant.
-// Accumulator column d*N + n holds 2^-6 * (digit-d sum of read n); the
-// columns are read 64 at a time.
+// Accumulator column d*N + n holds the digit-d sum of read n (an exact
+// integer in f32); Sum = sum_d 4^d * column d*N + n.
 template <int D>
 __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem, uint64_t* acc_full,
                                               uint64_t* acc_empty, volatile int* abort_flag,
@@ -440,6 +301,8 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
                                               const uint32_t* __restrict__ sRid, int valid_reads, int64_t bt0,
                                               int64_t bt1, uint32_t& acc_cnt) {
     constexpr int N = kRowsTile / D;
+    constexpr int G = N < 32 ? N : 32;  // reads per group
+    constexpr int DPL = 32 / G;         // digits per 32-column load
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quad = warp & 3;
     const int m = quad * 32 + lane;
@@ -452,7 +315,7 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
         const int64_t b = P.bin_begin + bt * kBinTile + m;
         const bool bin_ok = b < P.bin_end;
         if (D == 1) {
-            // one digit: compare 2^-6 * Sum with T / 64 in f32 (both exact)
+            // one digit: the accumulator is the sum; compare it with T in f32
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 uint32_t v[64];
@@ -470,38 +333,37 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
                 if (__any_sync(kFull, bin_ok && any)) {
                     int sums[64];
 #pragma unroll
-                    for (int i = 0; i < 64; i++) sums[i] = (int)(__uint_as_float(v[i]) * 64.0f);
+                    for (int i = 0; i < 64; i++) sums[i] = (int)__uint_as_float(v[i]);
                     scan_emit<64>(P, sums, 64 * h, valid_reads, sT, sRid, b, bin_ok, lane);
                 }
             }
         } else {
-            // D digits: groups of 32 reads, two digit columns per load round
+            // D digits: groups of G reads, DPL digit columns per 32-column load
 #pragma unroll
-            for (int g = 0; g < N / 32; g++) {
-                int acc[32];
+            for (int g = 0; g < N / G; g++) {
+                int acc[G];
 #pragma unroll
-                for (int i = 0; i < 32; i++) acc[i] = 0;
+                for (int i = 0; i < G; i++) acc[i] = 0;
 #pragma unroll
-                for (int d = 0; d < D; d += 2) {
-                    uint32_t v[64];
-                    tmem_ld32(col0 + d * N + 32 * g, v);
-                    tmem_ld32(col0 + (d + 1) * N + 32 * g, v + 32);
+                for (int d = 0; d < D; d += DPL) {
+                    uint32_t v[32];
+                    tmem_ld32(col0 + d * N + G * g, v);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int i = 0; i < 32; i++)
-                        acc[i] += ((int)(__uint_as_float(v[i]) * 64.0f) << (4 * d)) +
-                                  ((int)(__uint_as_float(v[32 + i]) * 64.0f) << (4 * (d + 1)));
+                    for (int e = 0; e < DPL; e++)
+#pragma unroll
+                        for (int i = 0; i < G; i++) acc[i] += (int)__uint_as_float(v[e * G + i]) << (2 * (d + e));
                 }
-                if (g == N / 32 - 1) {
+                if (g == N / G - 1) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acc_empty[buf]);
                 }
                 uint32_t any = 0;
 #pragma unroll
-                for (int i = 0; i < 32; i++) any |= (uint32_t)(acc[i] >= sT[32 * g + i]);
+                for (int i = 0; i < G; i++) any |= (uint32_t)(acc[i] >= sT[G * g + i]);
                 if (__any_sync(kFull, bin_ok && any))
-                    scan_emit<32>(P, acc, 32 * g, valid_reads, sT, sRid, b, bin_ok, lane);
+                    scan_emit<G>(P, acc, G * g, valid_reads, sT, sRid, b, bin_ok, lane);
             }
         }
         acc_cnt++;
@@ -557,6 +419,17 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    if (warp >= kEpilogueWarp0) {
+        // unit scale factors (ue8m0 127 = 1.0 in every byte) for A and B
+        uint32_t v[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) v[i] = 0x7F7F7F7Fu;
+        tmem_st32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + kSfCol, v);
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     // work decomposition: classes' tile counts come from the prep kernel
     int n_tiles[kNumClasses];
@@ -569,7 +442,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
     const int64_t n_btiles = (P.bin_end - P.bin_begin + kBinTile - 1) / kBinTile;
     const int64_t n_chunks = (n_btiles + P.btiles_per_item - 1) / P.btiles_per_item;
     const int64_t n_items = (int64_t)total_tiles * n_chunks;
-    constexpr uint32_t kIdesc = idesc_f8(kBinTile, kRowsTile);
+    constexpr uint32_t kIdesc = idesc_mxf4(kBinTile, kRowsTile);
 
     // running pipeline counters (each role uses its own)
     uint32_t bank_cnt = 0, a_cnt = 0, acc_cnt = 0;
@@ -591,7 +464,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
         // stage the read tile's digit rows (swizzled K-major), thresholds, read ids
         {
             const uint4* src = reinterpret_cast<const uint4*>(P.sc.rows[cls] + (size_t)tile * G::kBBytes);
-            constexpr int kChunksPerRow = G::kK / 16;
+            constexpr int kChunksPerRow = G::kKBytes / 16;
             for (int i = threadIdx.x; i < kRowsTile * kChunksPerRow; i += kScanThreads) {
                 const int row = i / kChunksPerRow, j = i % kChunksPerRow;
                 const int kb = j >> 3, cj = j & 7;
@@ -600,8 +473,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
             }
             for (int n = threadIdx.x; n < kRowsTile; n += kScanThreads) {
                 sT[n] = n < valid_reads ? P.sc.T[cls][tile * nR + n] : 0x7fffffff;
-                // T / 64 exactly (|T| < 2^24); "never passes" is +inf
-                sTf[n] = sT[n] == 0x7fffffff ? __int_as_float(0x7f800000) : (float)sT[n] * (1.0f / 64.0f);
+                // T exactly in f32 (|T| < 2^24); "never passes" is +inf
+                sTf[n] = sT[n] == 0x7fffffff ? __int_as_float(0x7f800000) : (float)sT[n];
                 sRid[n] = n < valid_reads ? P.sc.rid[cls][tile * nR + n] : 0u;
             }
             if (threadIdx.x == 0) {
@@ -645,11 +518,13 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
                         tc_fence_after();
 #pragma unroll
                         for (int kk = 0; kk < G::kMmaPerChunk; kk++) {
-                            const uint32_t a_tmem = tmem + kACol + sa * kACols + kk * 8;
-                            const int kb = c * G::kVecPerChunk + (kk >> 2);  // 128-byte K block of B
+                            const uint32_t a_tmem = tmem + kACol + sa * G::kACols + kk * 8;
+                            const int kg = c * G::kMmaPerChunk + kk;  // MMA index within the row
+                            const int kb = kg >> 2;                   // 128-byte K block of B (4 MMAs)
                             const uint64_t bdesc =
-                                smem_desc_sw128(smem_addr(sB) + kb * (kRowsTile * 128) + (kk & 3) * 32);
-                            mma_f8f6f4_tmemA(d_tmem, a_tmem, bdesc, kIdesc, (c | kk) != 0);
+                                smem_desc_sw128(smem_addr(sB) + kb * (kRowsTile * 128) + (kg & 3) * 32);
+                            mma_mxf4_tmemA(d_tmem, a_tmem, bdesc, kIdesc, tmem + kSfCol, tmem + kSfCol,
+                                           (c | kk) != 0);
                         }
                         mma_commit(&a_empty[sa]);
                         a_cnt++;
@@ -677,23 +552,32 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
                 for (int c = 0; c < G::kChunks; c++, a_cnt++) {
                     if ((a_cnt & 1u) != group) continue;
                     const uint32_t sa = a_cnt % kAStages, pha = (a_cnt / kAStages) & 1;
-                    uint4 bits[G::kVecPerChunk];
+                    // this stage's bank words (rows shorter than the padded K read as 0)
+                    constexpr int kVec = G::kWordsPerChunk / 4;
+                    uint4 bits[kVec];
 #pragma unroll
-                    for (int u = 0; u < G::kVecPerChunk; u++)
-                        bits[u] = (m < rows) ? myrow[c * G::kVecPerChunk + u] : make_uint4(0, 0, 0, 0);
+                    for (int u = 0; u < kVec; u++) {
+                        const int wv = c * kVec + u;  // 16-byte vector of the row
+                        bits[u] = (m < rows && 4 * wv < G::kRowWords) ? myrow[wv] : make_uint4(0, 0, 0, 0);
+                    }
                     if (!__all_sync(kFull, mbar_wait(&a_empty[sa], pha ^ 1, abort_flag))) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
 #pragma unroll
-                    for (int u = 0; u < G::kVecPerChunk; u++) {
+                    for (int u = 0; u < kVec; u += 2) {
+                        // 8 bank words -> 32 columns (4 per word)
                         uint32_t v[32];
-                        expand_word(bits[u].x, v);
-                        expand_word(bits[u].y, v + 8);
-                        expand_word(bits[u].z, v + 16);
-                        expand_word(bits[u].w, v + 24);
-                        tmem_st32(tmem + lane_base + kACol + sa * kACols + u * 32, v);
+                        expand_word_fp4(bits[u].x, v);
+                        expand_word_fp4(bits[u].y, v + 4);
+                        expand_word_fp4(bits[u].z, v + 8);
+                        expand_word_fp4(bits[u].w, v + 12);
+                        expand_word_fp4(bits[u + 1].x, v + 16);
+                        expand_word_fp4(bits[u + 1].y, v + 20);
+                        expand_word_fp4(bits[u + 1].z, v + 24);
+                        expand_word_fp4(bits[u + 1].w, v + 28);
+                        tmem_st32(tmem + lane_base + kACol + sa * G::kACols + u * 16, v);
                     }
                     tmem_wait_st();
                     tc_fence_before();
@@ -714,8 +598,11 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
             else if (cls_now == 1)
                 scan_epilogue<2>(P, tmem, acc_full, acc_empty, abort_flag, sT, sTf, sRid, *s_valid, bt0, bt1,
                                  acc_cnt);
-            else
+            else if (cls_now == 2)
                 scan_epilogue<4>(P, tmem, acc_full, acc_empty, abort_flag, sT, sTf, sRid, *s_valid, bt0, bt1,
+                                 acc_cnt);
+            else
+                scan_epilogue<8>(P, tmem, acc_full, acc_empty, abort_flag, sT, sTf, sRid, *s_valid, bt0, bt1,
                                  acc_cnt);
         }
         __syncthreads();  // the item is drained before B is overwritten
@@ -778,18 +665,18 @@ static int launch_scan_q(const grim_bank* bank, const uint8_t* reads, const int6
         const int64_t need = (n_reads + kPrepWarps - 1) / kPrepWarps;
         const int64_t cap = (int64_t)sm_count() * 16;
         const int64_t blocks = need < cap ? need : cap;
-        scan_prep_kernel<Q><<<(unsigned)blocks, kPrepWarps * 32, smem, s>>>(reads, read_offsets, n_reads, E, sc,
+        scan_prep_kernel<Q><<<grim::fault_grid((unsigned)blocks), kPrepWarps * 32, smem, s>>>(reads, read_offsets, n_reads, E, sc,
                                                                             bank->status);
         GRIM_CUDA_TRY(cudaGetLastError());
     }
     {
         constexpr size_t smem = ScanSmem<Q>::kAlloc;
-        static bool attr[64] = {};  // per device
+        static DeviceCache attr[64];  // per device
         const int slot = device_slot();
         if (slot < 0) return GRIM_ENOTSUP;
-        if (!attr[slot]) {
+        if (!attr[slot].load()) {
             GRIM_CUDA_TRY(cudaFuncSetAttribute(scan_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr[slot] = true;
+            attr[slot].store(1);
         }
         ScanParams P;
         P.bank = bank->bits;
@@ -805,11 +692,17 @@ static int launch_scan_q(const grim_bank* bank, const uint8_t* reads, const int6
         P.sc = sc;
         P.out = out;
         P.status = bank->status;
-        scan_kernel<Q><<<sm_count(), kScanThreads, smem, s>>>(P);
+        scan_kernel<Q><<<grim::fault_grid(sm_count()), kScanThreads, smem, s>>>(P);
         GRIM_CUDA_TRY(cudaGetLastError());
     }
     return GRIM_OK;
 }
+
+}  // namespace grim
+
+extern "C" const char* grim_scan_mma_kind(void) { return "mxf4"; }
+
+namespace grim {
 
 int scan_noalloc_scratch(void** ptr, size_t* bytes) {
     static std::mutex mu;
@@ -829,11 +722,11 @@ int scan_noalloc_scratch(void** ptr, size_t* bytes) {
 }
 
 size_t scan_scratch_bytes(int q, int64_t n_reads) {
-    const int64_t K = (int64_t(1) << (2 * q)) < 128 ? 128 : (int64_t(1) << (2 * q));
+    const int64_t K = (int64_t(1) << (2 * q)) < 256 ? 256 : (int64_t(1) << (2 * q));  // e2m1: K / 2 bytes a row
     size_t total = 256;
     for (int c = 0; c < kNumClasses; c++) {
         const int64_t tiles = (n_reads + class_reads(c) - 1) / class_reads(c);
-        total += (size_t)tiles * kRowsTile * K;
+        total += (size_t)tiles * kRowsTile * (K / 2);
         total += 2 * (((size_t)tiles * class_reads(c) * 4 + 255) & ~(size_t)255);
     }
     return total;

@@ -135,16 +135,16 @@ __global__ void scan_tiles_kernel(const T* in, T* out, int64_t n, const T* __res
 template <typename T>
 int exclusive_scan(const T* in, T* out, int64_t n, T init, cudaStream_t s, const T* init_dev = nullptr) {
     if (n == 0) {
-        set_value_kernel<T><<<1, 1, 0, s>>>(out, init, init_dev);
+        set_value_kernel<T><<<grim::fault_grid(1), 1, 0, s>>>(out, init, init_dev);
         GRIM_CUDA_TRY(cudaGetLastError());
         return GRIM_OK;
     }
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     T* sums = nullptr;
     GRIM_CUDA_TRY(grim::scratch_alloc((void**)&sums, (size_t)tiles * sizeof(T), s));
-    tile_sums_kernel<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
-    scan_sums_kernel<T><<<1, 1024, 0, s>>>(sums, tiles, init, init_dev);
-    scan_tiles_kernel<T><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
+    tile_sums_kernel<T><<<grim::fault_grid((unsigned)tiles), kScanThreads, 0, s>>>(in, n, sums);
+    scan_sums_kernel<T><<<grim::fault_grid(1), 1024, 0, s>>>(sums, tiles, init, init_dev);
+    scan_tiles_kernel<T><<<grim::fault_grid((unsigned)tiles), kScanThreads, 0, s>>>(in, out, n, sums);
     const cudaError_t e = cudaGetLastError();
     cudaFreeAsync(sums, s);
     if (e != cudaSuccess) {
@@ -652,20 +652,23 @@ int grim_seed_index_build(const uint8_t* ref2bit, int64_t len, int k, void* stre
         return GRIM_ECUDA;
     }
     uint32_t* cursor = nullptr;
-    cudaError_t e = cudaMalloc((void**)&idx->offsets, (size_t)(nk + 1) * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&idx->positions, (size_t)npos * 4);
+    cudaError_t e = grim::fault_alloc_now() ? cudaErrorMemoryAllocation
+                                            : cudaMalloc((void**)&idx->offsets, (size_t)(nk + 1) * 4);
+    if (e == cudaSuccess)
+        e = grim::fault_alloc_now() ? cudaErrorMemoryAllocation
+                                    : cudaMalloc((void**)&idx->positions, (size_t)npos * 4);
     if (e == cudaSuccess) e = grim::scratch_alloc((void**)&cursor, (size_t)nk * 4, s);
     int rc = GRIM_OK;
     if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, (size_t)nk * 4, s);
     if (e == cudaSuccess) {
         const int blocks = grim::sm_count() * 8;
-        grim::seed_index_kernel<false><<<blocks, 256, 0, s>>>(ref2bit, npos, k, cursor, nullptr);
+        grim::seed_index_kernel<false><<<grim::fault_grid(blocks), 256, 0, s>>>(ref2bit, npos, k, cursor, nullptr);
         e = cudaGetLastError();
         if (e == cudaSuccess) rc = grim::exclusive_scan<uint32_t>(cursor, idx->offsets, nk, 0u, s);
         if (e == cudaSuccess && rc == GRIM_OK)
             e = cudaMemcpyAsync(cursor, idx->offsets, (size_t)nk * 4, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess && rc == GRIM_OK) {
-            grim::seed_index_kernel<true><<<blocks, 256, 0, s>>>(ref2bit, npos, k, cursor, idx->positions);
+            grim::seed_index_kernel<true><<<grim::fault_grid(blocks), 256, 0, s>>>(ref2bit, npos, k, cursor, idx->positions);
             e = cudaGetLastError();
         }
     }
@@ -725,7 +728,7 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
     GRIM_CUDA_TRY(grim::scratch_alloc((void**)&hit_off, (size_t)(n_reads + 1) * 8, s));
     GRIM_CUDA_TRY(grim::scratch_alloc((void**)&info, 64, s));  // batch bounds
     int rc = GRIM_OK;
-    grim::seed_hits_kernel<<<blocks, threads, 0, s>>>(idx->offsets, idx->k, reads, read_offsets, n_reads, hit_off);
+    grim::seed_hits_kernel<<<grim::fault_grid(blocks), threads, 0, s>>>(idx->offsets, idx->k, reads, read_offsets, n_reads, hit_off);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(hit_off, hit_off, n_reads, 0, s);
 
@@ -733,11 +736,11 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
     int bits = 0;
     while (bits < 32 && ((n_bins - 1) >> bits) != 0) bits++;
     const int passes = 2 * ((bits + 2 * grim::kRadixBits - 1) / (2 * grim::kRadixBits));
-    static bool smem_set[64] = {};
-    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
+    static grim::DeviceCache smem_set[64];
+    if (dev >= 0 && dev < 64 && !smem_set[dev].load()) {
         GRIM_CUDA_TRY(cudaFuncSetAttribute(grim::seed_dedupe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)grim::kDedupSmemBytes));
-        smem_set[dev] = true;
+        smem_set[dev].store(1);
     }
     const int64_t kBudget = int64_t(1) << 28;     // votes per batch
     const int64_t kMaxReads = int64_t(1) << 20;   // reads per batch
@@ -751,13 +754,13 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
         const int64_t max_nb = n_reads < kMaxReads ? n_reads : kMaxReads;
         e = grim::scratch_alloc((void**)&kept, (size_t)max_nb * 8, s);
         if (e == cudaSuccess) {
-            grim::set_value_kernel<int64_t><<<1, 1, 0, s>>>(cand_offsets, 0, nullptr);
+            grim::set_value_kernel<int64_t><<<grim::fault_grid(1), 1, 0, s>>>(cand_offsets, 0, nullptr);
             e = cudaGetLastError();
         }
     }
     for (int64_t r0 = 0; r0 < n_reads && e == cudaSuccess && rc == GRIM_OK;) {
         int64_t b[4];
-        grim::batch_end_kernel<<<1, 1, 0, s>>>(hit_off, n_reads, r0, kBudget, kMaxReads, info);
+        grim::batch_end_kernel<<<grim::fault_grid(1), 1, 0, s>>>(hit_off, n_reads, r0, kBudget, kMaxReads, info);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(b, info, sizeof(b), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -778,16 +781,16 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
         const int64_t wb = (nb * 32 + threads - 1) / threads;
         const unsigned bb = (unsigned)(wb < 65535 ? wb : 65535);
         if (votes > 0)
-            grim::seed_expand_kernel<<<bb, threads, 0, s>>>(idx->offsets, idx->positions, idx->k, reads,
+            grim::seed_expand_kernel<<<grim::fault_grid(bb), threads, 0, s>>>(idx->offsets, idx->positions, idx->k, reads,
                                                              read_offsets + r0, nb, hit_off + r0, h0,
                                                              (uint32_t)bin_len, (uint32_t)(n_bins - 1), H);
-        grim::seed_dedupe_kernel<<<(unsigned)nb, grim::kDedupThreads, grim::kDedupSmemBytes, s>>>(
+        grim::seed_dedupe_kernel<<<grim::fault_grid((unsigned)nb), grim::kDedupThreads, grim::kDedupSmemBytes, s>>>(
             hit_off + r0, h0, cap, passes, H, S, kept);
         e = cudaGetLastError();
         // offsets continue from the previous batch's total in cand_offsets[r0]
         if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(kept, cand_offsets + r0, nb, 0, s, cand_offsets + r0);
         if (e == cudaSuccess && rc == GRIM_OK) {
-            grim::seed_copy_kernel<<<bb, threads, 0, s>>>(H, hit_off + r0, h0, cand_offsets + r0, nb, cand_bins,
+            grim::seed_copy_kernel<<<grim::fault_grid(bb), threads, 0, s>>>(H, hit_off + r0, h0, cand_offsets + r0, nb, cand_bins,
                                                           capacity);
             e = cudaGetLastError();
         }
@@ -828,19 +831,19 @@ int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* c
     int64_t* counts = nullptr;
     GRIM_CUDA_TRY(grim::scratch_alloc((void**)&counts, (size_t)(tiles + 1) * 8, s));
     const bool aligned = ((uintptr_t)pass & 15) == 0;
-    grim::locate_count_kernel<<<(unsigned)tiles, grim::kScanThreads, 0, s>>>(pass, n_cands, aligned, counts);
+    grim::locate_count_kernel<<<grim::fault_grid((unsigned)tiles), grim::kScanThreads, 0, s>>>(pass, n_cands, aligned, counts);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(counts, counts, tiles, 0, s);
     if (e == cudaSuccess && rc == GRIM_OK)
         e = cudaMemcpyAsync(n_loc, counts + tiles, 8, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && rc == GRIM_OK) {
-        grim::locate_write_kernel<<<(unsigned)tiles, grim::kScanThreads, 0, s>>>(
+        grim::locate_write_kernel<<<grim::fault_grid((unsigned)tiles), grim::kScanThreads, 0, s>>>(
             pass, aligned, cand_bins, cand_offsets, n_reads, n_cands, counts, bank->len, bank->n_bins, bank->bin_len,
             bank->overlap, capacity, loc_read, loc_bin, loc_begin, loc_end, bank->status);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && rc == GRIM_OK && segments && capacity > 0) {
-        grim::locate_segments_kernel<<<grim::sm_count() * 8, 256, 0, s>>>(ref2bit, n_loc, capacity, loc_begin,
+        grim::locate_segments_kernel<<<grim::fault_grid(grim::sm_count() * 8), 256, 0, s>>>(ref2bit, n_loc, capacity, loc_begin,
                                                                           loc_end, segments, seg_stride);
         e = cudaGetLastError();
     }

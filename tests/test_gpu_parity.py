@@ -42,7 +42,13 @@ def run_filter(bank, bases, offs, cb, co, E):
 @pytest.mark.parametrize("q,bin_len,overlap,n", [
     (1, 7, 0, 50), (2, 7, 3, 61), (3, 32, 10, 5000), (4, 50, 25, 7777), (5, 256, 100, 200_003),
     (6, 256, 300, 100_001), (5, 100, 0, 12_345), (5, 1000, 5, 3000), (4, 17, 0, 4), (5, 16, 16, 3),
-    (6, 3, 40, 999), (5, 256, 100, 1), (3, 300_000, 7, 1_000_000)])
+    (6, 3, 40, 999), (5, 256, 100, 1), (3, 300_000, 7, 1_000_000),
+    # geometries of the lane-per-core kernel: whole following cores in a
+    # span (J >= 1), no prefix (e = 0), the largest bins, CTA boundaries
+    (5, 256, 300, 400_000), (5, 256, 4, 300_001), (4, 64, 700, 100_000), (5, 1024, 100, 500_000),
+    (5, 2048, 100, 500_000), (5, 512, 100, 1_000_003),
+    (5, 256, 100, 195_840), (3, 48, 2, 9_999), (1, 16, 0, 1000), (5, 16, 4000, 50_000), (2, 32, 45, 7_001),
+    (5, 256, 100, 2_000_003)])
 def test_bank_matches_oracle(oracle, q, bin_len, overlap, n):
     codes = synth.ref_with_repeats(n, q + n, 0.3 if n > 20_000 else 0.0, n_fam=20, fam_min=100, fam_max=2000)
     r2 = synth.pack2bit(codes)
@@ -52,6 +58,21 @@ def test_bank_matches_oracle(oracle, q, bin_len, overlap, n):
     want = pack_rows(oracle.build_bank(r2, n, q, bin_len, overlap), bank.row_words)
     got = bank.bits().cpu().numpy().view(np.uint32)
     assert np.array_equal(got, want)
+    bank.free()
+
+
+def test_bank_from_unaligned_reference(oracle):
+    """A reference buffer that does not start on a 4-byte boundary takes the
+    byte-wise build; the rows are the same."""
+    n = 300_001
+    codes = synth.ref_with_repeats(n, 77, 0.3, n_fam=20, fam_min=100, fam_max=2000)
+    r2 = synth.pack2bit(codes)
+    buf = torch.zeros(len(r2) + 1, dtype=torch.uint8, device="cuda")
+    buf[1:] = dev(r2)
+    bank = grim.grim_build_bank(buf[1:], n, 5, 256, 100)
+    assert grim.grim_bank_status(bank) == (grim.GRIM_OK, 0)
+    want = pack_rows(oracle.build_bank(r2, n, 5, 256, 100), bank.row_words)
+    assert np.array_equal(bank.bits().cpu().numpy().view(np.uint32), want)
     bank.free()
 
 

@@ -83,7 +83,8 @@ def test_scan_plain_workload_sizes(oracle):
 
 
 def test_scan_heavy_reads_use_more_digits(oracle):
-    """Token counts > 15 and > 255 (two and four base-16 digits)."""
+    """Token counts above 3, 15 and 255 (2, 4 and 8 base-4 digits: every
+    digit class of the full scan's B rows)."""
     rng = np.random.default_rng(7)
     codes = synth.ref_iid(30_000, 5)
     codes[3000:3400] = 0                      # poly-A
