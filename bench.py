@@ -1,27 +1,35 @@
 """Benchmark of the seed-location filter on GB300.
 
-Three forms of the hot path, each on its synthetic workload:
-  gather   (default line): 100 Mbp repeat-rich reference (70% i.i.d. ACGT +
-           30% planted repeat families at 10-20% divergence), q=5, 256 bp
-           bins + 150 bp overlap; 1M reads of 150 bp (4% substitutions, 1%
-           indels), E=7; candidates = bins of all exact 12-mer seed hits from
-           a CPU index, capped at 1,000 per read.  One step = one grim_filter
-           over the whole batch.
-  batched: 100 Mbp repeat-rich reference, q=6, 256 + 300 bp; 2M reads of
-           50-300 bp (3% + 1%), E = floor(0.05 L); true bin + log-uniform
-           1-5,000 candidates.  One step = one grim_filter_batched (one
-           cost-balanced launch per 262,144 reads, replayed CUDA graph,
-           autotuned launch shape).
-  fullscan: 3.1 Gbp repeat-rich reference, q=5, 256 + 100 bp (12.1M bins);
-           a batch of 65,536 reads of 100 bp, E=5, every bin scored on the
-           tensor cores.  One step = one grim_scan.
-The bank is built once per reference beforehand (the paper also leaves
-bitvector generation out of its runtime, Sec. 6.1) and timed on its own.
-`--workload` picks the form of the JSON line; the other two are measured
-after it and reported as sub-objects unless disabled.
+Five synthetic workloads, each timed with the form of the hot path it is
+meant for (inputs resident in HBM, L2 flushed between timed steps):
+  1 plain gather, 1 Mbp: i.i.d. reference, q=5, 256 bp bins + 100 bp
+           overlap; 10,000 reads of 100 bp (3% substitutions, 1% indels),
+           E=5; the true bin + 31 uniform candidates.  Step: grim_filter.
+  2 gather at scale, 100 Mbp: 70% i.i.d. + 30% planted repeat families at
+           10-20% divergence, q=5, 256 + 150 bp; 1M reads of 150 bp (4% + 1%),
+           E=7; bins of all exact 12-mer seed hits, capped at 1,000.
+           Step: grim_filter.
+  3 full scan, 3.1 Gbp: same mixture, q=5, 256 + 100 bp (12.1M bins); a
+           batch of 65,536 reads of 100 bp, E=5, every bin scored on the
+           tensor cores.  Step: grim_scan.
+  4 batching, 100 Mbp, q=6, 256 + 300 bp; 2M reads of 50-300 bp (3% + 1%),
+           E = floor(0.05 L); true bin + log-uniform 1-5,000 candidates.
+           Step: grim_filter_batched (one launch per 262,144 reads in a
+           replayed CUDA graph, autotuned launch shape).
+  5 human-scale mixed, 3.1 Gbp, 40% repeats at 5-20% divergence, q=5,
+           256 + 100 bp; 10M reads of 100 bp, E=5; 12-mer seed candidates
+           built on the GPU, capped at 10,000.  Step: grim_filter_auto (the
+           per-batch choice between the gather form and the full scan).
+The default JSON line is workload 5 (the largest single-GPU configuration);
+the other four are measured after it and summarised in the `configs` key,
+the line's last.  The bank is built once per reference beforehand (the paper
+also leaves bitvector generation out of its runtime, Sec. 6.1) and timed on
+its own.  Roofline denominators: the measured HBM copy bandwidth
+(MEASURED_PEAKS.json) and, measured here by the library's own kernels, the
+L2 read bandwidth and the dense tensor rates (grim_peak).
 
-Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle on a
-bounded sample of the same workload instead.
+--impl reference times the CPU oracle on bounded samples of the same
+workload instead, on every host core.
 """
 from __future__ import annotations
 
@@ -32,6 +40,7 @@ import os
 import subprocess
 import sys
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -41,12 +50,16 @@ sys.path.insert(0, ROOT)
 METRIC = "(read,bin) checks/s & reads/s at E=0.05·L; frac of HBM/INT8 roofline vs plain"
 UNIT = "checks/s"
 L2_FLUSH_BYTES = 256 << 20
+CONFIG_OF_FORM = {"plain": "1", "gather": "2", "fullscan": "3", "batched": "4", "mixed": "5"}
+SUMMARY_KEY = {"plain": "1_plain_1Mbp", "gather": "2_gather_100Mbp", "fullscan": "3_fullscan_3.1Gbp",
+               "batched": "4_batched_q6_100Mbp", "mixed": "5_mixed_3.1Gbp"}
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch, from
-# an ncu capture, valid only for the kernel source it was taken on.
+# dram__bytes_read.sum + dram__bytes_write.sum of one gather launch, from an
+# ncu capture, valid only for the kernel source it was taken on:
+# {source hash: {form: {"bytes": per launch, "reads": reads per launch}}}
 TRAFFIC_BY_SOURCE: dict[str, dict] = {
     # gather_kernel<5,8>, 1M reads, 74.8M checks: 660.20 MB read + 74.78 MB written
-    "0b92bfcdafdb14db": {"bytes": 734_982_656, "reads": 1_000_000},
+    "0b92bfcdafdb14db": {"gather": {"bytes": 734_982_656, "reads": 1_000_000}},
 }
 
 
@@ -56,23 +69,25 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gather", choices=["gather", "batched", "fullscan", "mixed"])
+    ap.add_argument("--workload", default="mixed", choices=["plain", "gather", "batched", "fullscan", "mixed"])
+    ap.add_argument("--plain-ref-bp", type=int, default=1_000_000)
+    ap.add_argument("--plain-reads", type=int, default=10_000)
     ap.add_argument("--reads", type=int, default=1_000_000, help="gather: reads per GPU (weak scaling)")
-    ap.add_argument("--ref-bp", type=int, default=100_000_000, help="gather: reference length")
+    ap.add_argument("--ref-bp", type=int, default=100_000_000, help="gather / batched: reference length")
     ap.add_argument("--batched-reads", type=int, default=2_000_000)
-    ap.add_argument("--scan-ref-bp", type=int, default=3_100_000_000)
+    ap.add_argument("--scan-ref-bp", type=int, default=3_100_000_000, help="full scan / mixed: reference length")
     ap.add_argument("--scan-reads", type=int, default=65_536)
-    ap.add_argument("--sub-steps", type=int, default=3, help="timed steps of the sub-measurements")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--ref-seconds", type=float, default=150.0,
-                    help="--impl reference: target CPU time of the whole run (warm-up + timed steps)")
-    ap.add_argument("--no-batched", action="store_true", help="skip the batched sub-measurement")
-    ap.add_argument("--no-full-scan", action="store_true", help="skip the full-scan sub-measurement")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the dispatcher (mixed) sub-measurement")
     ap.add_argument("--mixed-reads", type=int, default=10_000_000)
+    ap.add_argument("--sub-steps", type=int, default=3, help="timed steps of the other workloads")
+    ap.add_argument("--only", action="store_true", help="measure the --workload line alone")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=3.0, help="CPU time of each oracle sample leg")
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="--impl reference: target wall time of the whole run (warm-up + timed steps)")
     ap.add_argument("--no-q-sweep", action="store_true", help="skip the token-size sweep (q = 4, 5, 6)")
     ap.add_argument("--q-sweep-reads", type=int, default=262_144)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="workload 5: skip the verification metrics and the overlapped pipeline")
     return ap.parse_args()
 
 
@@ -81,23 +96,11 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def load_peaks():
+def load_hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
-        d = json.load(open(p))
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
-
-
-def load_fp8_peak():
-    """Dense e4m3 tensor peak: the measured bf16 cuBLAS peak x the nominal
-    fp8 / bf16 ratio (4.5 / 2.25 PFLOP/s); burst and sustained."""
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        d = json.load(open(p))
-        return (float(d["bf16_tflops"]) * 2.0, float(d.get("bf16_tflops_sustained", d["bf16_tflops"])) * 2.0,
-                "measured bf16 x 2")
-    return 1900.0 * 2.0, 1700.0 * 2.0, "fallback bf16 x 2"
+        return float(json.load(open(p))["hbm_gbs"]), "measured hbm_gbs (MEASURED_PEAKS.json)"
+    return 6800.0, "fallback hbm 6.8 TB/s"
 
 
 def source_sha(files=("gather.cu", "grim_internal.cuh", "tokens.cuh")):
@@ -105,6 +108,26 @@ def source_sha(files=("gather.cu", "grim_internal.cuh", "tokens.cuh")):
     for f in files:
         h.update(open(os.path.join(ROOT, "paper_1711_01177_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def sig(x, n=4):
+    """x rounded to n significant digits (compact JSON)."""
+    if x is None or not isinstance(x, (int, float)) or x == 0 or not np.isfinite(x):
+        return x
+    return float(f"{x:.{n}g}")
+
+
+def cpu_info():
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count() or 1}
 
 
 class ClockSampler:
@@ -156,71 +179,139 @@ class ClockSampler:
 
 # --------------------------------------------------------------- workloads
 
-def make_gather(args, rank):
+def make_workload(form, args, rank, cand_reads=0):
     import synth
-    return synth.gather_seeds(ref_len=args.ref_bp, n_reads=args.reads, read_seed=synth.SEED_READS + 1000 * rank)
+    rs = synth.SEED_READS + 1000 * rank
+    if form == "plain":
+        return synth.gather_iid(ref_len=args.plain_ref_bp, n_reads=args.plain_reads)
+    if form == "gather":
+        return synth.gather_seeds(ref_len=args.ref_bp, n_reads=args.reads, read_seed=rs)
+    if form == "batched":
+        return synth.batched_varlen(ref_len=args.ref_bp, n_reads=args.batched_reads, read_seed=rs)
+    if form == "fullscan":
+        return synth.fullscan(ref_len=args.scan_ref_bp, n_reads=args.scan_reads, read_seed=rs)
+    # candidates come from the GPU seed table; cand_reads > 0 also builds CPU
+    # lists for the first reads (the oracle's sample)
+    return synth.mixed_seeds(ref_len=args.scan_ref_bp, n_reads=args.mixed_reads, read_seed=rs, cand_reads=cand_reads)
 
 
-def make_batched(args, rank):
-    import synth
-    return synth.batched_varlen(n_reads=args.batched_reads, read_seed=synth.SEED_READS + 1000 * rank)
-
-
-def make_fullscan(args, rank):
-    import synth
-    return synth.fullscan(ref_len=args.scan_ref_bp, n_reads=args.scan_reads,
-                          read_seed=synth.SEED_READS + 1000 * rank)
-
-
-def make_mixed(args, rank, cand_reads=0):
-    """Candidates come from the GPU seed table; cand_reads > 0 also builds
-    CPU lists for the first reads (the oracle's sample)."""
-    import synth
-    return synth.mixed_seeds(ref_len=args.scan_ref_bp, n_reads=args.mixed_reads,
-                             read_seed=synth.SEED_READS + 1000 * rank, cand_reads=cand_reads)
-
-
-def describe(form, w):
+def describe(form, w, world=1):
+    """The workload's defining parameters (identical for both arms)."""
     L = np.diff(w.read_offsets)
     base = {"ref_bp": w.ref_len, "q": w.q, "bin_len": w.bin_len, "overlap": w.overlap, "n_bins": w.n_bins,
             "reads_per_gpu": w.n_reads, "read_len": [int(L.min()), int(L.max())],
             "E": [int(w.E.min()), int(w.E.max())], "sub": w.meta["sub"], "indel": w.meta["indel"],
             "repeat_frac": w.meta["repeat_frac"],
-            "l2": "flushed between timed steps (256 MiB write, outside the events)"}
+            "l2": "flushed between timed steps (256 MiB write, outside the events)",
+            "parallelism": f"replicas x{world} (read batches per GPU, no collective)"}
     rep = f"{int(w.meta['repeat_frac'] * 100)}% repeats"
-    if form == "gather":
-        c = np.diff(w.cand_offsets)
-        base.update(workload=f"gather, {w.ref_len / 1e6:g} Mbp repeat-rich reference ({rep}), q={w.q}, "
-                             f"{w.n_reads} x {int(L[0])} bp reads/GPU, 12-mer seed candidates (cap 1000)",
-                    checks_per_gpu_step=w.n_checks, cands_per_read_mean=round(float(c.mean()), 2),
-                    cands_per_read_max=int(c.max()))
+    if form == "plain":
+        wl = (f"plain gather, {w.ref_len / 1e6:g} Mbp i.i.d. reference, q={w.q}, {w.n_reads} x {int(L[0])} bp "
+              f"reads/GPU, true bin + 31 uniform candidates")
+    elif form == "gather":
+        wl = (f"gather, {w.ref_len / 1e6:g} Mbp repeat-rich reference ({rep}), q={w.q}, {w.n_reads} x {int(L[0])} "
+              f"bp reads/GPU, 12-mer seed candidates (cap 1000)")
     elif form == "batched":
-        base.update(workload=f"batched gather, {w.ref_len / 1e6:g} Mbp repeat-rich reference ({rep}), q={w.q}, "
-                             f"{w.n_reads} reads of {int(L.min())}-{int(L.max())} bp/GPU, E=floor(0.05 L), "
-                             f"log-uniform 1-5000 candidates (mean {w.n_checks / w.n_reads:.0f})",
-                    checks_per_gpu_step=w.n_checks)
+        wl = (f"batched gather, {w.ref_len / 1e6:g} Mbp repeat-rich reference ({rep}), q={w.q}, {w.n_reads} reads "
+              f"of {int(L.min())}-{int(L.max())} bp/GPU, E=floor(0.05 L), log-uniform 1-5000 candidates")
     elif form == "mixed":
-        base.update(workload=f"dispatcher, {w.ref_len / 1e9:g} Gbp reference ({rep} at 5-20% divergence), q={w.q}, "
-                             f"{w.n_reads} x {int(L[0])} bp reads/GPU, 12-mer seed candidates (cap 10000), "
-                             f"gather vs full scan chosen per batch")
-        if w.cand_offsets is not None and len(w.cand_offsets) == w.n_reads + 1:
-            c = np.diff(w.cand_offsets)
-            base.update(checks_per_gpu_step=w.n_checks, cands_per_read_mean=round(float(c.mean()), 2),
-                        cands_per_read_max=int(c.max()))
+        wl = (f"dispatcher, {w.ref_len / 1e9:g} Gbp reference ({rep} at 5-20% divergence), q={w.q}, {w.n_reads} x "
+              f"{int(L[0])} bp reads/GPU, 12-mer seed candidates from the GPU seed table (cap 10000), gather vs full "
+              f"scan chosen per batch")
     else:
-        base.update(workload=f"full scan, {w.ref_len / 1e9:g} Gbp repeat-rich reference ({rep}), q={w.q}, "
-                             f"{w.n_bins} bins, batch of {w.n_reads} x {int(L[0])} bp reads/GPU, every bin",
-                    checks_per_gpu_step=w.n_reads * w.n_bins)
+        wl = (f"full scan, {w.ref_len / 1e9:g} Gbp repeat-rich reference ({rep}), q={w.q}, {w.n_bins} bins, batch "
+              f"of {w.n_reads} x {int(L[0])} bp reads/GPU, every bin")
+    base["workload"] = wl
     return base
 
 
-def gather_bytes(w, row_bytes):
+def gather_bytes(n_checks, w, row_bytes):
     """Bytes one gather pass must move: per check the bin row, the candidate
     id and the pass byte; per read its bases, two offsets and E."""
-    return w.n_checks * (row_bytes + 4 + 1) + int(w.read_offsets[-1]) + (w.n_reads + 1) * 16 + w.n_reads * 2
+    return n_checks * (row_bytes + 4 + 1) + int(w.read_offsets[-1]) + (w.n_reads + 1) * 16 + w.n_reads * 2
 
 
-# --------------------------------------------------------------- one form
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_rate(run_chunk, n_max, seconds, threads):
+    """run_chunk(a, b) runs the oracle on units [a, b) and returns the checks
+    done; the oracle's C calls release the GIL, so a thread pool runs them on
+    `threads` cores.  Calibrated on a small prefix, the sample is sized for
+    about `seconds` of wall time and cut into chunks that the threads take in
+    turn.  Returns (checks/s, units used, checks, seconds)."""
+    n0 = min(n_max, 8)
+    t = time.perf_counter()
+    run_chunk(0, n0)
+    per = max((time.perf_counter() - t) / n0, 1e-7)
+    n = int(min(n_max, max(threads, seconds * threads / per)))
+    edges = np.unique(np.linspace(0, n, min(n, 8 * threads) + 1).astype(np.int64))
+    t = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        done = sum(ex.map(lambda ab: run_chunk(int(ab[0]), int(ab[1])), zip(edges[:-1], edges[1:])))
+    dt = time.perf_counter() - t
+    return done / dt, n, done, dt
+
+
+def oracle_sampler(form, w, sample_reads=16_384):
+    """(run_chunk, n_max, what) for the oracle on this workload: read ranges
+    [a, b) through the byte-per-bit bank (built beforehand, untimed), or, at
+    genome scale, with each candidate's bitvector rebuilt from the reference
+    (oracle_filter_rows), or the full scan over the first 20,000 bins."""
+    import oracle
+    import synth
+    o = oracle.Oracle()
+    ro, bases = w.read_offsets, w.bases
+    if form == "fullscan":
+        nb = 20_000
+        prefix = nb * w.bin_len + w.overlap
+        ob = o.build_bank(synth.pack2bit(w.codes[:prefix]), prefix, w.q, w.bin_len, w.overlap)[:nb]
+
+        def run(a, b):
+            o.scan(ob, w.q, bases[ro[a]:ro[b]], ro[a:b + 1] - ro[a], w.E[a:b])
+            return (b - a) * nb
+
+        return run, w.n_reads, f"reads x the first {nb} bins"
+    if form == "mixed":
+        if w.cand_offsets is None or len(w.cand_offsets) - 1 < min(sample_reads, w.n_reads):
+            m = min(sample_reads, w.n_reads)
+            sub_off = ro[:m + 1]
+            idx = synth.seed_index_for_reads(w.codes, bases[:sub_off[-1]], sub_off, w.meta["seed_k"])
+            cb, co = synth.cands_seeds(idx, bases[:sub_off[-1]], sub_off, w.bin_len, w.n_bins, w.meta["cap"],
+                                       w.meta["seed_k"])
+            del idx
+        else:
+            cb, co = w.cand_bins, w.cand_offsets
+
+        def run(a, b):
+            o.filter_rows(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap, bases[ro[a]:ro[b]], ro[a:b + 1],
+                          cb[co[a]:co[b]], co[a:b + 1], w.E[a:b])
+            return int(co[b] - co[a])
+
+        return run, len(co) - 1, "reads (CPU seed candidates), each candidate's bitvector rebuilt from the reference"
+    ob = o.build_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
+    cb, co = w.cand_bins, w.cand_offsets
+
+    def run(a, b):
+        o.filter(ob, w.q, bases[ro[a]:ro[b]], ro[a:b + 1] - ro[a], cb[co[a]:co[b]], co[a:b + 1] - co[a], w.E[a:b])
+        return int(co[b] - co[a])
+
+    return run, w.n_reads, "reads, oracle bank prebuilt (not timed)"
+
+
+def cpu_baseline(form, w, seconds):
+    """The oracle on a bounded sample of the same workload: single-threaded,
+    then on every host core."""
+    run, n_max, what = oracle_sampler(form, w)
+    info = cpu_info()
+    v1, n1, c1, t1 = oracle_rate(run, n_max, seconds, 1)
+    vn, nn, cn, tn = oracle_rate(run, n_max, seconds, info["nproc"])
+    return {"value": vn, "unit": UNIT, "cores": info["nproc"], "kind": "oracle",
+            "sample": f"first {nn} {what}: {cn} checks in {tn:.1f} s on {info['nproc']} threads; single thread: "
+                      f"first {n1}, {c1} checks in {t1:.1f} s",
+            "single_thread": v1, "cpu_model": info["cpu_model"], "nproc": info["nproc"]}
+
+
+# --------------------------------------------------------------- GPU context
 
 def max_over_ranks(x, world):
     """The largest x over all ranks (the job's time is its slowest rank's)."""
@@ -263,7 +354,7 @@ class Ctx:
             import torch.distributed as dist
             dist.barrier()
 
-    def timed(self, fn, steps, warmup, clocks=False):
+    def timed(self, fn, steps, warmup, clocks=True):
         """Per-step CUDA-event times on the launching stream, L2 flushed
         between steps outside the events; returns (list of ms, clock summary)."""
         import torch
@@ -292,110 +383,318 @@ class Ctx:
         return [a.elapsed_time(b) for a, b in ev], (sampler.summary() if sampler else None)
 
 
-def run_form(form, args, ctx, primary):
-    """Measure one form; returns its JSON dict (contract keys if primary)."""
-    import torch
-
+def measure_peaks(ctx):
+    """Roofline denominators: the driver's HBM copy figure and, measured
+    here by the library's kernels, the L2 read bandwidth, the dense tensor
+    rates (burst: one launch of a few ms; sustained: launches back to back
+    for about a second) and the legacy mma.sync INT8 rate."""
     import paper_1711_01177_gb300 as grim
-    w = {"gather": make_gather, "batched": make_batched, "fullscan": make_fullscan,
-         "mixed": make_mixed}[form](args, ctx.rank)
-    dev, s = ctx.dev, ctx.stream
-    steps = args.steps if primary else args.sub_steps
-    warmup = args.warmup if primary else 2
+    hbm, hbm_src = load_hbm_peak()
+    out = {"hbm_gbs": hbm, "hbm_source": hbm_src}
 
-    ref_d = dev(w.ref2bit)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    def best(kind, work, n=3):
+        r = [grim.grim_peak(kind, work, stream=ctx.stream) for _ in range(n)]
+        return max(u / (ms / 1e3) for u, ms in r)
+
+    out["l2_read_gbs"] = best(grim.GRIM_PEAK_L2_READ, 32 << 20) / 1e9
+    for name, kind, work in (("e4m3", grim.GRIM_PEAK_E4M3, 65536), ("mxf4", grim.GRIM_PEAK_MXF4, 131072),
+                             ("e4m3_tmem_a", grim.GRIM_PEAK_E4M3_TMEM_A, 65536),
+                             ("mxf4_tmem_a", grim.GRIM_PEAK_MXF4_TMEM_A, 131072)):
+        out[f"{name}_tflops"] = best(kind, work) / 1e12
+    # sustained: the full scan's kind for about a second, the last launches
+    t0, rates = time.perf_counter(), []
+    while time.perf_counter() - t0 < 1.0:
+        u, ms = grim.grim_peak(grim.GRIM_PEAK_MXF4_TMEM_A, 1 << 20, stream=ctx.stream)
+        rates.append(u / (ms / 1e3))
+    out["mxf4_tmem_a_tflops_sustained"] = float(np.median(rates[len(rates) // 2:])) / 1e12
+    out["int8_mma_sync_tops"] = best(grim.GRIM_PEAK_INT8_MMA_SYNC, 4000) / 1e12
+    out["how"] = ("grim_peak: L2 = 32 MiB read 40x with ld.global.cg.v4 on every SM; tensor = one CTA per SM "
+                  "issuing dense tcgen05.mma 128x256 (e4m3 K=32 / mxf4 e2m1 K=64, unit scales) back to back, "
+                  "operands in shared (or A in tensor) memory; best of 3 launches; int8 = mma.sync m16n8k32 s8")
+    return {k: (sig(v) if isinstance(v, float) else v) for k, v in out.items()}
+
+
+# --------------------------------------------------------------- one form
+
+def build_bank_timed(grim, ctx, w):
+    """Builds the bank once; the build kernel's time is taken on a second
+    build into the same bank (grim_build_bank_into), which allocates nothing."""
+    import torch
+    s = ctx.stream
+    ref_d = ctx.dev(w.ref2bit)
     with torch.cuda.stream(s):
-        e0.record(s)
         bank = grim.grim_build_bank(ref_d, w.ref_len, w.q, w.bin_len, w.overlap, stream=s)
-        e1.record(s)
-    s.synchronize()
-    bank_ms = e0.elapsed_time(e1)
+    ms, _ = ctx.timed(lambda: grim.grim_build_bank_into(bank, ref_d, stream=s), 3, 1, clocks=False)
     st, flags = grim.grim_bank_status(bank, s)
     assert st == grim.GRIM_OK, (st, flags)
     row = bank.row_words * 4
-    bank_info = {"ms": bank_ms, "mbp_per_s": w.ref_len / 1e6 / (bank_ms / 1e3),
-                 "gb_per_s": (bank.n_bins * row + len(w.ref2bit)) / 1e9 / (bank_ms / 1e3),
-                 "bank_bytes": bank.n_bins * row}
+    alg = bank.n_bins * row + len(w.ref2bit)
+    m = float(np.median(ms))
+    hbm, _ = load_hbm_peak()
+    info = {"ms": sig(m), "mbp_per_s": sig(w.ref_len / 1e6 / (m / 1e3)), "gb_per_s": sig(alg / 1e9 / (m / 1e3)),
+            "hbm_frac": sig(alg / 1e9 / (m / 1e3) / hbm, 3), "bank_bytes": bank.n_bins * row,
+            "algorithmic_bytes": alg}
     del ref_d
+    return bank, info
 
-    out = {"form": form}
-    if form == "mixed":
-        # the mapper's side of the filter on the GPU: seed table, candidates,
-        # then the dispatcher over every read, then the Seed Location Checker
-        torch.cuda.empty_cache()  # the library allocates from the CUDA pool, not torch's cache
-        ref_d = dev(w.ref2bit)
-        reads_d, offs_d, E_d = dev(w.bases), dev(w.read_offsets), dev(w.E)
-        s.synchronize()
-        t0 = time.perf_counter()
-        with torch.cuda.stream(s):
-            idx = grim.grim_seed_index_build(ref_d, w.ref_len, w.meta["seed_k"], stream=s)
-        s.synchronize()
-        index_s = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        with torch.cuda.stream(s):
-            cb_d, co_d = grim.grim_seed_candidates(idx, reads_d, offs_d, w.bin_len, w.n_bins, w.meta["cap"],
-                                                   capacity=w.n_reads * 2048, stream=s)
-        s.synchronize()
-        cand_s = time.perf_counter() - t0
-        del ref_d
-        n_checks = int(cb_d.numel())
-        launches = -(-w.n_reads // 262144)
-        per_read = torch.diff(co_d)
-        ins = [reads_d, offs_d, cb_d, co_d, E_d]
-        pass_d = torch.empty(n_checks, dtype=torch.uint8, device="cuda")
-        with torch.cuda.stream(s):
-            tune = grim.grim_autotune(bank, *ins, pass_out=pass_d, stream=s)
-        s.synchronize()
-        choice = grim.grim_choose_form(bank, w.n_reads, n_checks)
-        scanned = []
 
-        def call():
-            _, n_sc = grim.grim_filter_auto(bank, *ins, pass_out=pass_d, stream=s)
-            scanned.append(n_sc)
+def finish(out, form, ctx, w, units, ms, steps, roof, launches, clk, bank_info):
+    total_ms = ctx.max_over_ranks(float(sum(ms)))
+    out.update({"value": units * ctx.world * steps / (total_ms / 1e3), "unit": UNIT,
+                "reads_per_s": w.n_reads * ctx.world * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
+                "steps": steps, "roofline": roof, "gpu_launches": launches * steps, "clocks": clk,
+                "bank_build": bank_info})
+    return out
 
-        ms, clk = ctx.timed(call, steps, warmup, clocks=primary)
-        ms_g, _ = ctx.timed(lambda: grim.grim_filter_batched(bank, *ins, pass_out=pass_d, tune=tune, stream=s),
-                            args.sub_steps, 1)
-        nb = min(w.n_reads, 65_536)  # the full scan is timed on one batch of reads
-        scan_ins = (reads_d, offs_d[:nb + 1], E_d[:nb])
-        res = grim.grim_scan(bank, *scan_ins, cap=1 << 24, stream=s)
-        ms_s, _ = ctx.timed(lambda: grim.grim_scan(bank, *scan_ins, out=res, stream=s), 1, 1)
-        n_pass = int(torch.count_nonzero(pass_d).item())
-        ms_l, _ = ctx.timed(lambda: grim.grim_locate(bank, cb_d, co_d, pass_d, capacity=n_pass, stream=s), 1, 1)
-        loc = grim.grim_locate(bank, cb_d, co_d, pass_d, capacity=n_pass, stream=s)
-        st, flags = grim.grim_bank_status(bank, s)
-        assert st == grim.GRIM_OK, (st, flags)
-        units = n_checks
-        avg = float(np.mean(ms))
-        g, sc, lc = float(np.mean(ms_g)), float(np.mean(ms_s)), float(np.mean(ms_l))
-        alg = n_checks * (row + 4 + 1) + int(w.read_offsets[-1]) + (w.n_reads + 1) * 16 + w.n_reads * 2
-        peak, peak_kind = load_peaks()
-        roof = {"bound": "hbm", "achieved": alg / (avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                "frac": alg / (avg / 1e3) / 1e9 / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
-                "kernel": "dispatcher -> gather_kernel<5,8>", "avg_step_ms": avg}
-        out["config_extra"] = {"checks_per_gpu_step": n_checks,
-                               "cands_per_read_mean": round(n_checks / w.n_reads, 2),
-                               "cands_per_read_max": int(per_read.max().item()),
-                               "candidates": "GPU seed table + grim_seed_candidates (12-mer seeds, cap 10000)"}
-        out["dispatch"] = {"choice": "scan" if choice == grim.GRIM_FORM_SCAN else "gather",
-                           "reads_scanned_per_step": scanned[-1] if scanned else 0}
-        out["gather_form"] = {"ms_per_step": g, "checks_per_s": units / (g / 1e3), "reads_per_s": w.n_reads / (g / 1e3)}
-        out["scan_form"] = {"ms_per_batch": sc, "batch_reads": nb,
-                            "checks_per_s_all_bins": nb * w.n_bins / (sc / 1e3), "reads_per_s": nb / (sc / 1e3),
-                            "pairs_passing": res.n_pairs,
-                            "note": "one batch of reads timed; the dispatcher's choice runs every read"}
-        out["seed_pipeline"] = {"seed_table_s": index_s, "candidates_s": cand_s,
-                                "candidates_reads_per_s": w.n_reads / cand_s, "locate_ms": lc,
-                                "locations_passing": loc.n,
-                                "reads_per_s_serial": w.n_reads / (cand_s + avg / 1e3 + lc / 1e3)}
-        out["pass_rate"] = n_pass / max(1, n_checks)
+
+def run_plain_or_gather(form, args, ctx, primary, peaks):
+    import torch
+
+    import paper_1711_01177_gb300 as grim
+    w = make_workload(form, args, ctx.rank)
+    steps = args.steps if primary else args.sub_steps
+    warmup = args.warmup if primary else 2
+    bank, bank_info = build_bank_timed(grim, ctx, w)
+    s = ctx.stream
+    ins = [ctx.dev(w.bases), ctx.dev(w.read_offsets), ctx.dev(w.cand_bins), ctx.dev(w.cand_offsets), ctx.dev(w.E)]
+    pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
+    ms, clk = ctx.timed(lambda: grim.grim_filter(bank, *ins, pass_out=pass_d, stream=s), steps, warmup)
+    st, flags = grim.grim_bank_status(bank, s)
+    assert st == grim.GRIM_OK, (st, flags)
+    row = bank.row_words * 4
+    alg = gather_bytes(w.n_checks, w, row)
+    avg = float(np.mean(ms))
+    ach = alg / (avg / 1e3) / 1e9
+    hbm, hbm_src = load_hbm_peak()
+    bank_bytes = bank.n_bins * row
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "peak_source": hbm_src, "kernel": f"gather_kernel<{w.q},8>", "algorithmic_bytes_per_launch": alg,
+            "launches_per_step": 1, "avg_step_ms": avg}
+    sha = source_sha()
+    rec = TRAFFIC_BY_SOURCE.get(sha, {}).get(form, {})
+    roof["source_sha"] = sha
+    roof["traffic"] = rec.get("bytes") if rec.get("reads") == w.n_reads else None
+    if bank_bytes < 100e6 and peaks.get("l2_read_gbs"):
+        roof["l2_frac"] = ach / peaks["l2_read_gbs"]
+        roof["l2_peak"] = peaks["l2_read_gbs"]
+        roof["note"] = (f"the {bank_bytes / 1e6:.1f} MB bank stays in the 129 MB L2: frac counts algorithmic bytes "
+                        f"against HBM, l2_frac against the measured L2 read bandwidth")
+        roof["summary_frac"], roof["summary_peak"] = roof["l2_frac"], "measured l2_read_gbs"
+    out = {"form": form, "pass_rate": float(pass_d.float().mean().item()),
+           "workload_stats": {"checks_per_gpu_step": w.n_checks,
+                              "cands_per_read_mean": round(w.n_checks / w.n_reads, 2),
+                              "cands_per_read_max": int(np.diff(w.cand_offsets).max())}}
+    if primary:
+        # end to end through grim_filter_host: page-locked host buffers in,
+        # chunks copied in / filtered / copied out on overlapping streams
+        h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.cand_bins), ctx.pin(w.cand_offsets),
+                ctx.pin(w.E)]
+        h_out = torch.empty(w.n_checks, dtype=torch.uint8).pin_memory()
+        e2e_ms, _ = ctx.timed(lambda: grim.grim_filter_host(bank, *h_in, pass_out=h_out, stream=s), steps, warmup,
+                              clocks=False)
+        assert torch.equal(h_out, pass_d.cpu()), "grim_filter_host differs from the device call"
+        out["e2e"] = {"value": w.n_checks * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3),
+                      "unit": UNIT, "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
+                      "d2h_bytes_per_step": h_out.numel(), "call": "grim_filter_host (host buffers)"}
+    if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(form, w, args.cpu_seconds)
+    del ins, pass_d
+    bank.free()
+    return finish(out, form, ctx, w, w.n_checks, ms, steps, roof, 1, clk, bank_info), w
+
+
+def run_batched(args, ctx, primary, peaks):
+    import torch
+
+    import paper_1711_01177_gb300 as grim
+    form = "batched"
+    w = make_workload(form, args, ctx.rank)
+    steps = args.steps if primary else args.sub_steps
+    warmup = args.warmup if primary else 2
+    bank, bank_info = build_bank_timed(grim, ctx, w)
+    s = ctx.stream
+    ins = [ctx.dev(w.bases), ctx.dev(w.read_offsets), ctx.dev(w.cand_bins), ctx.dev(w.cand_offsets), ctx.dev(w.E)]
+    pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(s):
+        tune = grim.grim_autotune(bank, *ins, pass_out=pass_d, stream=s)
+    s.synchronize()
+    ms, clk = ctx.timed(lambda: grim.grim_filter_batched(bank, *ins, pass_out=pass_d, tune=tune, stream=s), steps,
+                        warmup)
+    launches = -(-w.n_reads // int(tune.batch_reads))
+    ms_plain, _ = ctx.timed(lambda: grim.grim_filter(bank, *ins, pass_out=pass_d, stream=s), args.sub_steps, 2,
+                            clocks=False)
+    st, flags = grim.grim_bank_status(bank, s)
+    assert st == grim.GRIM_OK, (st, flags)
+    row = bank.row_words * 4
+    alg = gather_bytes(w.n_checks, w, row)
+    avg, ap = float(np.mean(ms)), float(np.mean(ms_plain))
+    hbm, hbm_src = load_hbm_peak()
+    ach = alg / (avg / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "peak_source": hbm_src, "kernel": f"gather_kernel<{w.q},{int(tune.warps_per_cta)}>",
+            "algorithmic_bytes_per_launch": alg // launches, "launches_per_step": launches, "avg_step_ms": avg}
+    out = {"form": form, "tune": tune.as_dict(), "pass_rate": float(pass_d.float().mean().item()),
+           "workload_stats": {"checks_per_gpu_step": w.n_checks,
+                              "cands_per_read_mean": round(w.n_checks / w.n_reads, 2)},
+           "plain_gather_same_workload": {"value": w.n_checks / (ap / 1e3), "ms_per_step": ap,
+                                          "frac": alg / (ap / 1e3) / 1e9 / hbm}}
+    if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(form, w, args.cpu_seconds)
+    del ins, pass_d
+    bank.free()
+    return finish(out, form, ctx, w, w.n_checks, ms, steps, roof, launches, clk, bank_info), w
+
+
+def run_fullscan(args, ctx, primary, peaks):
+    import torch
+
+    import paper_1711_01177_gb300 as grim
+    form = "fullscan"
+    w = make_workload(form, args, ctx.rank)
+    steps = args.steps if primary else args.sub_steps
+    warmup = args.warmup if primary else 1
+    bank, bank_info = build_bank_timed(grim, ctx, w)
+    s = ctx.stream
+    ins = [ctx.dev(w.bases), ctx.dev(w.read_offsets), ctx.dev(w.E)]
+    res = grim.grim_scan(bank, *ins, cap=1 << 24, stream=s)
+    call = lambda: grim.grim_scan(bank, *ins, out=res, stream=s)
+    ms, clk = ctx.timed(call, steps, warmup)
+    st, flags = grim.grim_bank_status(bank, s)
+    assert st == grim.GRIM_OK, (st, flags)
+    units = w.n_reads * w.n_bins
+    avg = float(np.mean(ms))
+    flops = 2.0 * units * (4 ** w.q)
+    tf = flops / (avg / 1e3) / 1e12
+    kind = grim.grim_scan_kind()
+    burst = peaks.get(f"{kind}_tflops")
+    roof = {"bound": "tensor", "achieved": tf, "peak": burst, "unit": "TFLOP/s",
+            "frac": tf / burst if burst else None, "traffic": None,
+            "peak_source": f"measured {kind}_tflops (grim_peak, operands in shared memory, burst)",
+            "kernel": f"scan_kernel<{w.q}> (+ scan_prep_kernel), tcgen05 kind::{kind}",
+            "algorithmic_flops_per_launch": flops, "avg_step_ms": avg}
+    for k in (f"{kind}_tmem_a_tflops", f"{kind}_tmem_a_tflops_sustained"):
+        if peaks.get(k):
+            roof["frac_of_" + k] = tf / peaks[k]
+    out = {"form": form, "pairs_passing": res.n_pairs}
+    if primary:
+        h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.E)]
+        n_pairs = res.n_pairs
+        h_read = torch.empty(n_pairs + 1, dtype=torch.int32).pin_memory()
+        h_bin = torch.empty(n_pairs + 1, dtype=torch.int32).pin_memory()
+        h_n = torch.empty(1, dtype=torch.int64).pin_memory()
+
+        def e2e_step():
+            for h, d in zip(h_in, ins):
+                d.copy_(h, non_blocking=True)
+            call()
+            h_n.copy_(res.n_pairs_dev, non_blocking=True)
+            h_read.copy_(res.pair_read[:n_pairs + 1], non_blocking=True)
+            h_bin.copy_(res.pair_bin[:n_pairs + 1], non_blocking=True)
+
+        e2e_ms, _ = ctx.timed(e2e_step, steps, warmup, clocks=False)
+        out["e2e"] = {"value": units * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
+                      "d2h_bytes_per_step": 8 + 8 * (n_pairs + 1)}
+    if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(form, w, args.cpu_seconds)
+    del ins, res
+    bank.free()
+    return finish(out, form, ctx, w, units, ms, steps, roof, 2, clk, bank_info), w
+
+
+def run_mixed(args, ctx, primary, peaks):
+    import torch
+
+    import paper_1711_01177_gb300 as grim
+    form = "mixed"
+    w = make_workload(form, args, ctx.rank)
+    steps = args.steps if primary else args.sub_steps
+    warmup = args.warmup if primary else 1
+    bank, bank_info = build_bank_timed(grim, ctx, w)
+    s, dev = ctx.stream, ctx.dev
+    torch.cuda.empty_cache()  # the library allocates from its own pool, not torch's cache
+    ref_d = dev(w.ref2bit)
+    reads_d, offs_d, E_d = dev(w.bases), dev(w.read_offsets), dev(w.E)
+    s.synchronize()
+    # the mapper's side of the filter on the GPU: seed table, then candidates
+    t0 = time.perf_counter()
+    with torch.cuda.stream(s):
+        idx = grim.grim_seed_index_build(ref_d, w.ref_len, w.meta["seed_k"], stream=s)
+    s.synchronize()
+    index_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    with torch.cuda.stream(s):
+        cb_d, co_d = grim.grim_seed_candidates(idx, reads_d, offs_d, w.bin_len, w.n_bins, w.meta["cap"],
+                                               capacity=w.n_reads * 2048, stream=s)
+    s.synchronize()
+    cand_s = time.perf_counter() - t0
+    n_checks = int(cb_d.numel())
+    per_read = torch.diff(co_d)
+    ins = [reads_d, offs_d, cb_d, co_d, E_d]
+    pass_d = torch.empty(n_checks, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(s):
+        tune = grim.grim_autotune(bank, *ins, pass_out=pass_d, stream=s)
+    s.synchronize()
+    choice = grim.grim_choose_form(bank, w.n_reads, n_checks)
+    scanned = []
+
+    def call():
+        _, n_sc = grim.grim_filter_auto(bank, *ins, pass_out=pass_d, stream=s)
+        scanned.append(n_sc)
+
+    ms, clk = ctx.timed(call, steps, warmup)
+    launches = -(-w.n_reads // 262_144)
+    ms_g, _ = ctx.timed(lambda: grim.grim_filter_batched(bank, *ins, pass_out=pass_d, tune=tune, stream=s),
+                        args.sub_steps, 1, clocks=False)
+    nb = min(w.n_reads, 65_536)  # the full scan is timed on one batch of reads
+    scan_ins = (reads_d, offs_d[:nb + 1], E_d[:nb])
+    res = grim.grim_scan(bank, *scan_ins, cap=1 << 24, stream=s)
+    ms_s, _ = ctx.timed(lambda: grim.grim_scan(bank, *scan_ins, out=res, stream=s), 1, 1, clocks=False)
+    n_pass = int(torch.count_nonzero(pass_d).item())
+    ms_l, _ = ctx.timed(lambda: grim.grim_locate(bank, cb_d, co_d, pass_d, capacity=n_pass, stream=s), 1, 1,
+                        clocks=False)
+    loc = grim.grim_locate(bank, cb_d, co_d, pass_d, capacity=n_pass, stream=s)
+    st, flags = grim.grim_bank_status(bank, s)
+    assert st == grim.GRIM_OK, (st, flags)
+    avg = float(np.mean(ms))
+    g, sc, lc = float(np.mean(ms_g)), float(np.mean(ms_s)), float(np.mean(ms_l))
+    row = bank.row_words * 4
+    alg = gather_bytes(n_checks, w, row)
+    hbm, hbm_src = load_hbm_peak()
+    ach = alg / (avg / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "peak_source": hbm_src, "kernel": "dispatcher -> gather_kernel<5,8>", "algorithmic_bytes_per_launch":
+            alg // launches, "launches_per_step": launches, "avg_step_ms": avg}
+    sha = source_sha()
+    rec = TRAFFIC_BY_SOURCE.get(sha, {}).get(form, {})
+    roof["source_sha"] = sha
+    if rec.get("reads"):
+        # measured on one batch launch; scaled to the average launch by checks
+        roof["traffic"] = int(rec["bytes"] * (n_checks / launches) / rec["checks"])
+        roof["traffic_note"] = (f"ncu DRAM bytes of one {rec['reads']}-read batch launch ({rec['checks']} checks), "
+                                f"scaled to the average launch by its checks")
+    out = {"form": form,
+           "workload_stats": {"checks_per_gpu_step": n_checks, "cands_per_read_mean": round(n_checks / w.n_reads, 2),
+                              "cands_per_read_max": int(per_read.max().item()),
+                              "candidates": "GPU seed table + grim_seed_candidates (12-mer seeds, cap 10000)"},
+           "dispatch": {"choice": "scan" if choice == grim.GRIM_FORM_SCAN else "gather",
+                        "reads_scanned_per_step": scanned[-1] if scanned else 0},
+           "gather_form": {"ms_per_step": g, "checks_per_s": n_checks / (g / 1e3), "reads_per_s": w.n_reads / (g / 1e3)},
+           "scan_form": {"ms_per_batch": sc, "batch_reads": nb, "checks_per_s_all_bins": nb * w.n_bins / (sc / 1e3),
+                         "reads_per_s": nb / (sc / 1e3), "pairs_passing": res.n_pairs,
+                         "note": "one batch of reads timed; the dispatcher's choice runs every read"},
+           "seed_pipeline": {"seed_table_s": index_s, "candidates_s": cand_s,
+                             "candidates_reads_per_s": w.n_reads / cand_s, "locate_ms": lc,
+                             "locations_passing": loc.n,
+                             "reads_per_s_serial": w.n_reads / (cand_s + avg / 1e3 + lc / 1e3)},
+           "pass_rate": n_pass / max(1, n_checks)}
+    del res
+    if not args.no_extras:
         # the paper's metrics (Sec. 5, 6.1): every passing location aligned
         # against its bin's span; every candidate of the first reads too, to
         # count misses (rejected locations that map)
-        ref_d = dev(w.ref2bit)
-        ms_v, _ = ctx.timed(lambda: grim.grim_verify(bank, ref_d, reads_d, offs_d, loc.read, loc.bin, stream=s), 1, 1)
+        ms_v, _ = ctx.timed(lambda: grim.grim_verify(bank, ref_d, reads_d, offs_d, loc.read, loc.bin, stream=s), 1, 1,
+                            clocks=False)
         dist = grim.grim_verify(bank, ref_d, reads_d, offs_d, loc.read, loc.bin, stream=s)
         st_pass = grim.grim_verify_stats(dist, loc.read, E_d, stream=s)
         nz = min(w.n_reads, 65_536)
@@ -413,165 +712,59 @@ def run_form(form, args, ctx, primary):
                                 "passing_with_mapping": st_all["passed"] - st_all["passed_unmapped"]},
             "note": "mapping = semi-global edit distance <= E of the read into the bin's span (grim_verify); "
                     "false negative rate in the paper's sense: passing locations without a mapping / passing"}
-        del loc, res, ins, cb_d, co_d, dist, dist_all, every  # the end-to-end steps make their own lists
+        del dist, dist_all, every
+        serial_s = cand_s + avg / 1e3 + lc / 1e3 + float(np.mean(ms_v)) / 1e3
+    del loc, ins
+    if primary:
+        # end to end through the public calls: reads in from pinned host
+        # memory, candidates on the GPU, the dispatcher, pass bytes back
+        del cb_d, co_d
         torch.cuda.empty_cache()
+        h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.E)]
+        h_out = torch.empty(n_checks, dtype=torch.uint8).pin_memory()
+
+        def e2e_step():
+            for h, d in zip(h_in, (reads_d, offs_d, E_d)):
+                d.copy_(h, non_blocking=True)
+            cb2, co2 = grim.grim_seed_candidates(idx, reads_d, offs_d, w.bin_len, w.n_bins, w.meta["cap"],
+                                                 capacity=n_checks, stream=s)
+            grim.grim_filter_auto(bank, reads_d, offs_d, cb2, co2, E_d, pass_out=pass_d, stream=s)
+            h_out.copy_(pass_d, non_blocking=True)
+
+        e2e_ms, _ = ctx.timed(e2e_step, steps, warmup, clocks=False)
+        out["e2e"] = {"value": n_checks * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
+                      "d2h_bytes_per_step": h_out.numel(),
+                      "includes": "reads copied in, seed candidates on the GPU (synchronising), dispatcher, pass "
+                                  "bytes to host"}
+        del h_in, h_out
+    else:
+        del cb_d, co_d
+    del pass_d
+    torch.cuda.empty_cache()
+    if not args.no_extras:
         # the whole path around the filter, alignment overlapping the next
         # batch's filtering (grim_map, 1M-read batches): once to warm, once timed
         align = torch.cuda.Stream()
         cap_loc = int(n_pass * 1.25) + 1024
-        with torch.cuda.stream(s):
-            grim.grim_map(bank, idx, ref_d, reads_d, offs_d, E_d, cap=w.meta["cap"], batch_reads=1 << 20,
-                          capacity=cap_loc, stream=s, align_stream=align)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        with torch.cuda.stream(s):
-            mp = grim.grim_map(bank, idx, ref_d, reads_d, offs_d, E_d, cap=w.meta["cap"], batch_reads=1 << 20,
-                               capacity=cap_loc, stream=s, align_stream=align)
-        torch.cuda.synchronize()
-        map_s = time.perf_counter() - t0
-        serial_s = cand_s + avg / 1e3 + lc / 1e3 + float(np.mean(ms_v)) / 1e3
-        out["seed_pipeline"].update({"overlapped_s": map_s, "overlapped_reads_per_s": w.n_reads / map_s,
-                                     "serial_sum_s": serial_s, "overlapped_locations": mp.n,
-                                     "overlapped_mapped": int(((mp.dist.to(torch.int32) & 0xFFFF) <= (
-                                         E_d.to(torch.int32) & 0xFFFF)[mp.read.long()]).sum().item())})
-        del mp, ref_d
-        torch.cuda.empty_cache()
-        if primary:
-            # end to end through the public calls: reads in from pinned host
-            # memory, candidates, filter, pass bytes back
-            h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.E)]
-            h_out = torch.empty(n_checks, dtype=torch.uint8).pin_memory()
-
-            def e2e_step():
-                for h, d in zip(h_in, (reads_d, offs_d, E_d)):
-                    d.copy_(h, non_blocking=True)
-                cb2, co2 = grim.grim_seed_candidates(idx, reads_d, offs_d, w.bin_len, w.n_bins, w.meta["cap"],
-                                                     capacity=n_checks, stream=s)
-                grim.grim_filter_auto(bank, reads_d, offs_d, cb2, co2, E_d, pass_out=pass_d, stream=s)
-                h_out.copy_(pass_d, non_blocking=True)
-
-            e2e_ms, _ = ctx.timed(e2e_step, steps, warmup)
-            out["e2e"] = {"value": units * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3), "unit": UNIT,
-                          "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
-                          "d2h_bytes_per_step": h_out.numel(),
-                          "includes": "seed candidates on the GPU (synchronising), dispatcher, pass bytes to host"}
-        idx.free()
-        del pass_d, reads_d, offs_d, E_d
-        torch.cuda.empty_cache()
-    elif form in ("gather", "batched"):
-        ins = [dev(w.bases), dev(w.read_offsets), dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)]
-        pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
-        tune = None
-        if form == "batched":
+        for rep in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             with torch.cuda.stream(s):
-                tune = grim.grim_autotune(bank, *ins, pass_out=pass_d, stream=s)
-            s.synchronize()
-            call = lambda: grim.grim_filter_batched(bank, *ins, pass_out=pass_d, tune=tune, stream=s)
-            launches = -(-w.n_reads // int(tune.batch_reads))
-            kernel = f"gather_kernel<{w.q},{int(tune.warps_per_cta)}>"
-        else:
-            call = lambda: grim.grim_filter(bank, *ins, pass_out=pass_d, stream=s)
-            launches = 1
-            kernel = f"gather_kernel<{w.q},8>"
-        ms, clk = ctx.timed(call, steps, warmup, clocks=primary)
-        units = w.n_checks
-        alg = gather_bytes(w, row)
-        peak, peak_kind = load_peaks()
-        avg = float(np.mean(ms))
-        roof = {"bound": "hbm", "achieved": alg / (avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                "frac": alg / (avg / 1e3) / 1e9 / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
-                "kernel": kernel, "algorithmic_bytes_per_launch": alg // launches, "launches_per_step": launches,
-                "avg_step_ms": avg}
-        if form == "gather":
-            sha = source_sha()
-            roof["source_sha"] = sha
-            rec = TRAFFIC_BY_SOURCE.get(sha, {})
-            roof["traffic"] = rec.get("bytes") if rec.get("reads") == w.n_reads else None
-            if w.q == 5:
-                roof["note"] = ("the 50 MB bank stays in the 129 MB L2, so algorithmic bytes exceed DRAM "
-                                "traffic; frac counts algorithmic bytes")
-        if form == "batched":
-            out["tune"] = tune.as_dict()
-            ms_plain, _ = ctx.timed(lambda: grim.grim_filter(bank, *ins, pass_out=pass_d, stream=s),
-                                    args.sub_steps, 2)
-            ap = float(np.mean(ms_plain))
-            out["plain_gather_same_workload"] = {
-                "value": units * ctx.world * len(ms_plain) / (ctx.max_over_ranks(sum(ms_plain)) / 1e3),
-                "ms_per_step": ap, "frac": alg / (ap / 1e3) / 1e9 / peak}
-        st, flags = grim.grim_bank_status(bank, s)
-        assert st == grim.GRIM_OK, (st, flags)
-        out["pass_rate"] = float(pass_d.float().mean().item())
-        if primary:
-            # end to end through grim_filter_host: page-locked host buffers in,
-            # chunks copied in / filtered / copied out on overlapping streams
-            h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.cand_bins), ctx.pin(w.cand_offsets),
-                    ctx.pin(w.E)]
-            h_out = torch.empty(w.n_checks, dtype=torch.uint8).pin_memory()
-
-            def e2e_step():
-                grim.grim_filter_host(bank, *h_in, pass_out=h_out, stream=s)
-
-            e2e_ms, _ = ctx.timed(e2e_step, steps, warmup)
-            assert torch.equal(h_out, pass_d.cpu()), "grim_filter_host differs from the device call"
-            out["e2e"] = {"value": units * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3), "unit": UNIT,
-                          "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
-                          "d2h_bytes_per_step": h_out.numel(), "call": "grim_filter_host (host buffers)"}
-            if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
-                out["cpu_baseline"] = cpu_baseline_filter(w, args.cpu_seconds)
-        del ins, pass_d
-    else:
-        ins = [dev(w.bases), dev(w.read_offsets), dev(w.E)]
-        cap = 1 << 24
-        res = grim.grim_scan(bank, *ins, cap=cap, stream=s)
-        call = lambda: grim.grim_scan(bank, *ins, out=res, stream=s)
-        ms, clk = ctx.timed(call, steps, warmup, clocks=primary)
-        st, flags = grim.grim_bank_status(bank, s)
-        assert st == grim.GRIM_OK, (st, flags)
-        n_pairs = res.n_pairs
-        units = w.n_reads * w.n_bins
-        launches = 2  # scan_prep_kernel + scan_kernel
-        avg = float(np.mean(ms))
-        flops = 2.0 * units * (4 ** w.q)
-        peak, peak_sust, src = load_fp8_peak()
-        roof = {"bound": "tensor", "achieved": flops / (avg / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / (avg / 1e3) / 1e12 / peak, "traffic": None,
-                "peak_source": f"{src} (e4m3 dense), burst", "kernel": f"scan_kernel<{w.q}> (+ scan_prep_kernel)",
-                "algorithmic_flops_per_launch": flops, "avg_step_ms": avg,
-                "frac_of_sustained": flops / (avg / 1e3) / 1e12 / peak_sust}
-        out["pairs_passing"] = n_pairs
-        if primary:
-            h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.E)]
-            h_read = torch.empty(n_pairs + 1, dtype=torch.int32).pin_memory()
-            h_bin = torch.empty(n_pairs + 1, dtype=torch.int32).pin_memory()
-            h_n = torch.empty(1, dtype=torch.int64).pin_memory()
-
-            def e2e_step():
-                for h, d in zip(h_in, ins):
-                    d.copy_(h, non_blocking=True)
-                call()
-                h_n.copy_(res.n_pairs_dev, non_blocking=True)
-                h_read.copy_(res.pair_read[:n_pairs + 1], non_blocking=True)
-                h_bin.copy_(res.pair_bin[:n_pairs + 1], non_blocking=True)
-
-            e2e_ms, _ = ctx.timed(e2e_step, steps, warmup)
-            out["e2e"] = {"value": units * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3), "unit": UNIT,
-                          "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
-                          "d2h_bytes_per_step": 8 + 8 * (n_pairs + 1)}
-        if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline_scan(w)
-        del ins, res
-    total_ms = ctx.max_over_ranks(float(sum(ms)))
-    out.update({"value": units * ctx.world * steps / (total_ms / 1e3), "unit": UNIT,
-                "reads_per_s": w.n_reads * ctx.world * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
-                "steps": steps, "roofline": roof, "gpu_launches": launches * steps, "clocks": clk,
-                "bank_build": bank_info, "config": describe(form, w)})
-    out["config"].update(out.pop("config_extra", {}))
-    bank.free()
-    del w
-    torch.cuda.synchronize()
+                mp = grim.grim_map(bank, idx, ref_d, reads_d, offs_d, E_d, cap=w.meta["cap"], batch_reads=1 << 20,
+                                   capacity=cap_loc, stream=s, align_stream=align)
+            torch.cuda.synchronize()
+            map_s = time.perf_counter() - t0
+        out["seed_pipeline"].update({"overlapped_s": map_s, "overlapped_reads_per_s": w.n_reads / map_s,
+                                     "serial_sum_s": serial_s, "overlapped_locations": mp.n})
+        del mp
+    idx.free()
+    del reads_d, offs_d, E_d, ref_d
     torch.cuda.empty_cache()
-    grim.grim_release_scratch()
-    return out
+    if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(form, w, args.cpu_seconds)
+    bank.free()
+    return finish(out, form, ctx, w, n_checks, ms, steps, roof, launches, clk, bank_info), w
 
 
 def q_sweep(args, ctx):
@@ -588,160 +781,74 @@ def q_sweep(args, ctx):
     ref_d = dev(w.ref2bit)
     ins = [dev(w.bases), dev(w.read_offsets), dev(w.cand_bins), dev(w.cand_offsets), dev(w.E)]
     pass_d = torch.empty(w.n_checks, dtype=torch.uint8, device="cuda")
-    peak, _ = load_peaks()
+    hbm, _ = load_hbm_peak()
     out = {"workload": f"{args.ref_bp / 1e6:g} Mbp repeat-rich reference, {w.n_reads} x 150 bp reads, "
                        f"12-mer seed candidates ({w.n_checks} checks), E = 7 for every q", "by_q": {}}
     for q in (4, 5, 6):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(s):
-            e0.record(s)
-            bank = grim.grim_build_bank(ref_d, w.ref_len, q, w.bin_len, w.overlap, stream=s)
-            e1.record(s)
-        s.synchronize()
-        ms, _ = ctx.timed(lambda: grim.grim_filter(bank, *ins, pass_out=pass_d, stream=s), args.sub_steps, 2)
+        bank = grim.grim_build_bank(ref_d, w.ref_len, q, w.bin_len, w.overlap, stream=s)
+        bms, _ = ctx.timed(lambda: grim.grim_build_bank_into(bank, ref_d, stream=s), 2, 1, clocks=False)
+        ms, _ = ctx.timed(lambda: grim.grim_filter(bank, *ins, pass_out=pass_d, stream=s), args.sub_steps, 2,
+                          clocks=False)
         st, flags = grim.grim_bank_status(bank, s)
         assert st == grim.GRIM_OK, (st, flags)
         avg = float(np.mean(ms))
         row = bank.row_words * 4
-        alg = gather_bytes(w, row)
-        out["by_q"][str(q)] = {"bank_bytes": bank.n_bins * row, "bank_build_ms": e0.elapsed_time(e1),
-                               "ms_per_step": avg, "checks_per_s": w.n_checks / (avg / 1e3),
-                               "hbm_frac": alg / (avg / 1e3) / 1e9 / peak,
-                               "pass_rate": float(pass_d.float().mean().item())}
+        alg = gather_bytes(w.n_checks, w, row)
+        out["by_q"][str(q)] = {"bank_bytes": bank.n_bins * row, "bank_build_ms": sig(float(np.median(bms))),
+                               "ms_per_step": sig(avg), "checks_per_s": sig(w.n_checks / (avg / 1e3)),
+                               "hbm_frac": sig(alg / (avg / 1e3) / 1e9 / hbm, 3),
+                               "pass_rate": sig(float(pass_d.float().mean().item()), 3)}
         bank.free()
     del ins, pass_d, ref_d
     torch.cuda.empty_cache()
     return out
 
 
-# --------------------------------------------------------------- CPU oracle
-
-def cpu_baseline_filter(w, seconds):
-    """The oracle, single-threaded, on the first reads of the same workload."""
-    import oracle
-    o = oracle.Oracle()
-    t0 = time.perf_counter()
-    ob = o.build_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
-    t_bank = time.perf_counter() - t0
-
-    def run(n):
-        co, ro = w.cand_offsets[:n + 1], w.read_offsets[:n + 1]
-        t = time.perf_counter()
-        o.filter(ob, w.q, w.bases[:ro[-1]], ro, w.cand_bins[:co[-1]], co, w.E[:n])
-        return time.perf_counter() - t, int(co[-1])
-
-    dt, nc = run(min(500, w.n_reads))
-    n = min(w.n_reads, max(500, int(500 * seconds / max(dt, 1e-6))))
-    dt, nc = run(n)
-    return {"value": nc / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n} reads ({nc} checks) of the same workload, oracle bank prebuilt "
-                      f"({t_bank:.1f} s, not timed), single thread",
-            "reads_per_s": n / dt, "seconds": round(dt, 2)}
+RUNNERS = {"plain": lambda a, c, p, k: run_plain_or_gather("plain", a, c, p, k),
+           "gather": lambda a, c, p, k: run_plain_or_gather("gather", a, c, p, k),
+           "batched": run_batched, "fullscan": run_fullscan, "mixed": run_mixed}
 
 
-def cpu_baseline_rows(w, seconds):
-    """The oracle on a genome-scale candidate list: each candidate's bitvector
-    built straight from the reference (oracle_bin_row), then summed
-    (oracle_sum_one); single-threaded, on the first candidates of the same
-    workload (a byte-per-bit oracle bank of 12.1M bins would not fit)."""
-    import oracle
-    o = oracle.Oracle()
-    t0 = time.perf_counter()
-    done = 0
-    r = 0
-    while time.perf_counter() - t0 < seconds and r < w.n_reads:
-        read = w.bases[w.read_offsets[r]:w.read_offsets[r + 1]]
-        for c in range(w.cand_offsets[r], w.cand_offsets[r + 1]):
-            row = o.bin_row(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap, int(w.cand_bins[c]))
-            o.sum_one(row, w.q, read)
-            done += 1
-        r += 1
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {r} reads ({done} checks) of the same workload, rows built per check, single thread",
-            "seconds": round(dt, 2)}
-
-
-def cpu_baseline_scan(w, n_reads=64, n_bins=20_000):
-    """The oracle's full scan, single-threaded, on the first reads x the first
-    bins of the same workload (the oracle bank of a reference prefix: its
-    first n_bins bins equal the full reference's)."""
-    import oracle
-    import synth
-    o = oracle.Oracle()
-    prefix = n_bins * w.bin_len + w.overlap
-    ob = o.build_bank(synth.pack2bit(w.codes[:prefix]), prefix, w.q, w.bin_len, w.overlap)[:n_bins]
-    t = time.perf_counter()
-    o.scan(ob, w.q, w.bases[:w.read_offsets[n_reads]], w.read_offsets[:n_reads + 1], w.E[:n_reads])
-    dt = time.perf_counter() - t
-    return {"value": n_reads * n_bins / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n_reads} reads x first {n_bins} bins of the same workload, single thread",
-            "seconds": round(dt, 2)}
+def summary(m):
+    """The compact record of one workload kept at the end of the line."""
+    r = m["roofline"]
+    frac = r.get("summary_frac", r.get("frac"))
+    peak_src = r.get("summary_peak", r.get("peak_source", ""))
+    cpu = m.get("cpu_baseline") or {}
+    clk = m.get("clocks") or {}
+    return {"value": sig(m["value"]), "ms_per_step": sig(m["ms_per_step"]), "reads_per_s": sig(m["reads_per_s"]),
+            "roofline": {"frac": sig(frac, 3), "peak": sig(r.get("l2_peak") if "summary_frac" in r else r["peak"]),
+                         "peak_source": peak_src.split(" (")[0], "hbm_frac": sig(r["frac"], 3)},
+            "cpu_baseline": sig(cpu.get("value")),
+            "clocks": {"sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons")}}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle
+    form = args.workload
+    w = make_workload(form, args, 0, cand_reads=16_384 if form == "mixed" else 0)
+    run, n_max, what = oracle_sampler(form, w)
+    info = cpu_info()
+    threads = info["nproc"]
     per_step = min(20.0, max(0.05, args.ref_seconds / max(1, args.steps + args.warmup)))
-    o = oracle.Oracle()
-    if args.workload == "fullscan":
-        import synth
-        w = make_fullscan(args, 0)
-        nb = 20_000
-        prefix = nb * w.bin_len + w.overlap
-        ob = o.build_bank(synth.pack2bit(w.codes[:prefix]), prefix, w.q, w.bin_len, w.overlap)[:nb]
-
-        def step(n):
-            t = time.perf_counter()
-            o.scan(ob, w.q, w.bases[:w.read_offsets[n]], w.read_offsets[:n + 1], w.E[:n])
-            return time.perf_counter() - t, n * nb
-
-        sample = f"first n reads x first {nb} bins per step"
-    elif args.workload == "mixed":
-        w = make_mixed(args, 0, cand_reads=4096)
-
-        def step(n):
-            t = time.perf_counter()
-            done = 0
-            for r in range(n):
-                read = w.bases[w.read_offsets[r]:w.read_offsets[r + 1]]
-                for c in range(w.cand_offsets[r], w.cand_offsets[r + 1]):
-                    o.sum_one(o.bin_row(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap, int(w.cand_bins[c])),
-                              w.q, read)
-                    done += 1
-            return time.perf_counter() - t, done
-
-        sample = "first n reads per step, rows built per check"
-    else:
-        w = make_gather(args, 0) if args.workload == "gather" else make_batched(args, 0)
-        ob = o.build_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
-
-        def step(n):
-            co, ro = w.cand_offsets[:n + 1], w.read_offsets[:n + 1]
-            t = time.perf_counter()
-            o.filter(ob, w.q, w.bases[:ro[-1]], ro, w.cand_bins[:co[-1]], co, w.E[:n])
-            return time.perf_counter() - t, int(co[-1])
-
-        sample = "first n reads per step"
-    dt, _ = step(16)
-    n_max = w.n_reads if w.cand_offsets is None else len(w.cand_offsets) - 1
-    n = min(n_max, max(16, int(16 * per_step / max(dt, 1e-6))))
     for _ in range(args.warmup):
-        step(n)
-    times, units = [], 0
+        oracle_rate(run, n_max, per_step, threads)
+    times, units, used = [], 0, 0
     for _ in range(args.steps):
-        dt, u = step(n)
+        rate, n, done, dt = oracle_rate(run, n_max, per_step, threads)
         times.append(dt)
-        units += u
+        units += done
+        used = n
     value = units / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": describe(args.workload, w),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample.replace("n reads", f"{n} reads") + ", single thread"},
+            "config": describe(form, w, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"per step the first {used} {what}, on {threads} threads",
+                             "cpu_model": info["cpu_model"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -761,32 +868,37 @@ def run_ours(args):
     grim.build()
     grim.load()
     ctx = Ctx(rank, world, local)
-    main_form = run_form(args.workload, args, ctx, primary=True)
+    peaks = measure_peaks(ctx)
+    main_form, w = RUNNERS[args.workload](args, ctx, True, peaks)
     subs = {}
-    if args.workload != "batched" and not args.no_batched:
-        subs["batched"] = run_form("batched", args, ctx, primary=False)
-    if args.workload != "fullscan" and not args.no_full_scan:
-        subs["full_scan"] = run_form("fullscan", args, ctx, primary=False)
-    if args.workload != "mixed" and not args.no_mixed:
-        subs["mixed"] = run_form("mixed", args, ctx, primary=False)
-    if not args.no_q_sweep:
-        subs["q_sweep"] = q_sweep(args, ctx)
+    if not args.only:
+        for form in ("plain", "gather", "fullscan", "batched", "mixed"):
+            if form != args.workload:
+                subs[form], _ = RUNNERS[form](args, ctx, False, peaks)
+    sweep = q_sweep(args, ctx) if not (args.no_q_sweep or args.only) else None
     if rank == 0:
         m = main_form
         line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "e4m3" if args.workload == "fullscan" else "u32",
-                "data": "synthetic",
-                "config": dict(m["config"], parallelism=f"replicas x{world} (read batches per GPU, no collective)"),
-                "reads_per_s": m["reads_per_s"], "roofline": m["roofline"], "e2e": m["e2e"],
-                "gpu_launches": m["gpu_launches"], "clocks": m["clocks"], "cpu_baseline": m.get("cpu_baseline"),
-                "bank_build": m["bank_build"]}
-        for k in ("pass_rate", "tune", "plain_gather_same_workload", "pairs_passing", "dispatch", "gather_form",
-                  "scan_form"):
+                "scaling": "weak", "vs_baseline": None, "dtype": "e2m1" if args.workload == "fullscan" else "u32",
+                "data": "synthetic", "config": describe(args.workload, w, world), "reads_per_s": m["reads_per_s"],
+                "roofline": m["roofline"], "e2e": m.get("e2e"), "gpu_launches": m["gpu_launches"],
+                "clocks": m["clocks"], "cpu_baseline": m.get("cpu_baseline"), "bank_build": m["bank_build"],
+                "peaks": peaks}
+        for k in ("workload_stats", "pass_rate", "tune", "plain_gather_same_workload", "pairs_passing", "dispatch",
+                  "gather_form", "scan_form", "verification", "seed_pipeline"):
             if k in m:
                 line[k] = m[k]
-        for k, v in subs.items():
-            line[k] = {kk: vv for kk, vv in v.items() if kk != "clocks"}
+        if sweep:
+            line["q_sweep"] = sweep
+        if subs:
+            # details of the other workloads, then their summaries as the
+            # line's last key
+            line["details"] = {SUMMARY_KEY[f]: {k: v for k, v in d.items()
+                                                if k in ("bank_build", "workload_stats", "pass_rate", "tune",
+                                                         "plain_gather_same_workload", "pairs_passing")}
+                               for f, d in subs.items()}
+            line["configs"] = {SUMMARY_KEY[f]: summary(d) for f, d in subs.items()}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -26,7 +26,7 @@ def _worker(rank, world, port, out):
         import bench
         import oracle
         args = types.SimpleNamespace(ref_bp=2_000_000, reads=400)
-        w = bench.make_gather(args, rank)
+        w = bench.make_workload("gather", args, rank)
         o = oracle.Oracle()
         ob = o.build_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
         p, _ = o.filter(ob, w.q, w.bases, w.read_offsets, w.cand_bins, w.cand_offsets, w.E)
