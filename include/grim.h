@@ -120,6 +120,8 @@ int grim_last_cuda_error(void);
  *                            block scales).
  *   GRIM_PEAK_MXF4_TMEM_A, GRIM_PEAK_E4M3_TMEM_A   the same with A in tensor
  *                            memory (the full scan's arrangement).
+ *   GRIM_PEAK_MXF4_TMEM_A_N128, GRIM_PEAK_E4M3_TMEM_A_N128   the same with
+ *                            N = 128.
  *   GRIM_PEAK_INT8_MMA_SYNC  `work` trips of 8 legacy mma.sync m16n8k32 s8 per
  *                            warp, 32 warps per SM; *units = integer ops.
  * *ms = CUDA-event time of the timed launch on `stream`, after one warm-up
@@ -132,6 +134,8 @@ int grim_last_cuda_error(void);
 #define GRIM_PEAK_MXF4_TMEM_A 4
 #define GRIM_PEAK_E4M3_TMEM_A 5
 #define GRIM_PEAK_INT8_MMA_SYNC 6
+#define GRIM_PEAK_MXF4_TMEM_A_N128 7 /* the full scan's MMA shape: 128 x 128 x 64, A in tensor memory */
+#define GRIM_PEAK_E4M3_TMEM_A_N128 8
 int grim_peak(int kind, int64_t work, double* units, float* ms, void* stream);
 
 #define GRIM_FAULT_NONE 0

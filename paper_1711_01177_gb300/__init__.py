@@ -68,7 +68,7 @@ SIGNATURES = {
 }
 GRIM_FAULT_NONE, GRIM_FAULT_ALLOC, GRIM_FAULT_LAUNCH = 0, 1, 2
 (GRIM_PEAK_L2_READ, GRIM_PEAK_E4M3, GRIM_PEAK_MXF4, GRIM_PEAK_MXF4_TMEM_A, GRIM_PEAK_E4M3_TMEM_A,
- GRIM_PEAK_INT8_MMA_SYNC) = range(1, 7)
+ GRIM_PEAK_INT8_MMA_SYNC, GRIM_PEAK_MXF4_TMEM_A_N128, GRIM_PEAK_E4M3_TMEM_A_N128) = range(1, 9)
 GRIM_FORM_GATHER, GRIM_FORM_SCAN = 0, 1
 
 

@@ -9,14 +9,16 @@
 // exactly once, split in two rows: P (the core's first r starts) and R (the
 // rest); then
 //     row(b) = P_b | R_b | (P|R)_{b+1} | ... | (P|R)_{b+J} | P_{b+J+1}.
-// The rows being built live in shared memory in a thread-private transposed
-// layout - word w of lane l's row at w * 32 + l - so the bank a thread
-// touches depends on its lane only: a warp's 32 shared-memory ORs never
-// collide, whatever its tokens.  Tokens come from a 64-bit window of the
-// core's bases (staged in shared memory in reversed base order, first base
-// most significant), one shift per token at a compile-time offset.  The
-// finished rows pass through shared memory once more so that each warp
-// stores its 32 consecutive rows with whole 512-byte writes.
+// A warp takes 32 consecutive cores and finishes the rows of the first
+// 32 - (J + 1), the neighbours' words coming by shuffle, so warps never wait
+// for one another.  The rows being built live in shared memory in a
+// thread-private transposed layout - word w of lane l's row at w * 32 + l -
+// so the bank a thread touches depends on its lane only: a warp's 32
+// shared-memory ORs never collide, whatever its tokens.  Tokens come from a
+// 64-bit window of the core's bases (reversed to first base most
+// significant), one shift per token at a compile-time offset.  The finished
+// rows pass through shared memory once more so that each warp stores its
+// consecutive rows with whole 512-byte writes.
 //
 // Fallback kernels (q = 6, very long bins or overlaps, unaligned input): one
 // CTA owns a run of consecutive bins and keeps their rows in shared memory;
@@ -167,7 +169,7 @@ bank_build_staged_kernel(const uint8_t* __restrict__ ref2bit, int64_t len, int b
 constexpr int kLaneWarps = 4;                  // 128 cores per CTA
 constexpr int kLaneCores = kLaneWarps * 32;
 constexpr int kLaneMaxBinLen = 1024;           // staged bases per core (two staging buffers)
-constexpr int kLaneMaxJ = 16;                  // whole following cores in a span
+constexpr int kLaneMaxJ = 16;                  // whole following cores in a span (out_w >= 15)
 
 template <int Q>
 struct LaneGeo {
@@ -246,20 +248,19 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Issues the copies of one tile's packed words (its kLaneCores cores from c0
-// and the first word after them) into a staging buffer; words past the reference
-// are zero-filled by the copy itself.
-__device__ __forceinline__ void stage_tile(const uint8_t* __restrict__ ref2bit, int64_t nbytes, int64_t c0, int wpc,
-                                           uint32_t stage_s) {
-    const int total = kLaneCores * wpc + 1;
+// Issues the copies of one warp tile's packed words (its 32 cores from c0 and
+// the first word after them) into the warp's staging buffer; words past the
+// reference are zero-filled by the copy itself.
+__device__ __forceinline__ void stage_warp_tile(const uint8_t* __restrict__ ref2bit, int64_t nbytes, int64_t c0,
+                                                int wpc, uint32_t stage_s, int lane) {
+    const int total = 32 * wpc + 1;
     const int64_t g0 = c0 * (int64_t)wpc;
     if (4 * (g0 + total) <= nbytes) {  // the whole tile lies inside the reference
         const uint8_t* src = ref2bit + 4 * g0;
-        for (int i = threadIdx.x; i < total; i += kLaneCores)
-            cp_async4(stage_s + 4u * (uint32_t)stage_pos(i), src + 4 * i, 4);
+        for (int i = lane; i < total; i += 32) cp_async4(stage_s + 4u * (uint32_t)stage_pos(i), src + 4 * i, 4);
         return;
     }
-    for (int i = threadIdx.x; i < total; i += kLaneCores) {
+    for (int i = lane; i < total; i += 32) {
         const int64_t byte = 4 * (g0 + i);
         const int64_t avail = nbytes - byte;
         const int n = avail >= 4 ? 4 : (avail > 0 ? (int)avail : 0);
@@ -268,58 +269,62 @@ __device__ __forceinline__ void stage_tile(const uint8_t* __restrict__ ref2bit, 
     }
 }
 
-// Persistent: each CTA takes tiles of kLaneCores cores (out_per_cta bins each),
-// the next tile's reference words copied in while the current one is built.
+// Persistent, one warp per work unit: warp tile u holds cores
+// [u * out_w, u * out_w + 32) and finishes the rows of its first out_w =
+// 32 - (J + 1) (the last J + 1 cores only complete their neighbours' rows),
+// so a warp never waits for another.  The next warp tile's reference words
+// are copied in while the current one is built.
 template <int Q>
 __global__ void __launch_bounds__(kLaneCores, 4)
 bank_build_lanes_kernel(const uint8_t* __restrict__ ref2bit, int64_t len, int bin_len, int r_pref, int J,
-                        int64_t n_bins, int64_t n_tiles, uint32_t* __restrict__ bank) {
+                        int64_t n_bins, int64_t n_units, uint32_t* __restrict__ bank) {
     using LG = LaneGeo<Q>;
     constexpr int RW = LG::kRW;
     extern __shared__ uint4 lane_smem4[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = threadIdx.x;                           // this thread's core within the tile
-    const int out_per_cta = kLaneCores - (J + 1);         // the last J + 1 cores only complete others' rows
-    const int wpc = bin_len >> 4;                         // packed words per core
-    const int stage_words = stage_pos(kLaneCores * wpc + 1) + 1;
+    const int out_w = 32 - (J + 1);   // rows finished per warp tile
+    const int wpc = bin_len >> 4;     // packed words per core
+    const int stage_words = stage_pos(32 * wpc + 1) + 1;
     const int64_t nbytes = (len + 3) >> 2;
 
     // rows: the P and R row sets of every warp, aligned so that the word
     // offset bits of a transposed row never meet the base address; then two
-    // staging buffers
+    // staging buffers per warp
     const uint32_t raw = shared_addr(lane_smem4);
     const uint32_t pad = ((raw + LG::kRowSetBytes - 1) & ~(uint32_t)(LG::kRowSetBytes - 1)) - raw;
     uint32_t* rows = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(lane_smem4) + pad);
-    uint32_t* stage = rows + kLaneWarps * 2 * RW * 32;
     const uint32_t rows_s = raw + pad;
-    const uint32_t stage_s = rows_s + (uint32_t)(kLaneWarps * 2 * LG::kRowSetBytes);
+    uint32_t* my_stage = rows + kLaneWarps * 2 * RW * 32 + warp * 2 * stage_words;
+    const uint32_t my_stage_s = rows_s + 4u * (uint32_t)(kLaneWarps * 2 * RW * 32 + warp * 2 * stage_words);
     const uint32_t baseP = rows_s + (uint32_t)((warp * 2) * LG::kRowSetBytes) + 4u * lane;
     const uint32_t baseR = baseP + LG::kRowSetBytes;
-    uint4* my_sets = reinterpret_cast<uint4*>(rows + warp * 2 * RW * 32);  // this warp's P and R sets
+    uint32_t* myP = rows + warp * 2 * RW * 32 + lane;  // word w of this lane's P row at myP[32 w]
+    uint32_t* myR = myP + RW * 32;
+    uint4* my_sets = reinterpret_cast<uint4*>(rows + warp * 2 * RW * 32);
 
-    int64_t tile = blockIdx.x;
-    if (tile < n_tiles) stage_tile(ref2bit, nbytes, tile * out_per_cta, wpc, stage_s);
+    const int64_t stride = (int64_t)gridDim.x * kLaneWarps;
+    int64_t unit = (int64_t)blockIdx.x * kLaneWarps + warp;
+    if (unit < n_units) stage_warp_tile(ref2bit, nbytes, unit * out_w, wpc, my_stage_s, lane);
     cp_async_commit();
-    for (int it = 0; tile < n_tiles; tile += gridDim.x, it++) {
-        const int64_t c0 = tile * out_per_cta;
+    for (int it = 0; unit < n_units; unit += stride, it++) {
+        const int64_t c0 = unit * out_w;
         const int buf = it & 1;
-        const int64_t next = tile + gridDim.x;
-        if (next < n_tiles)
-            stage_tile(ref2bit, nbytes, next * out_per_cta, wpc, stage_s + 4u * (uint32_t)(stage_words * (buf ^ 1)));
+        const int64_t next = unit + stride;
+        if (next < n_units)
+            stage_warp_tile(ref2bit, nbytes, next * out_w, wpc, my_stage_s + 4u * (uint32_t)(stage_words * (buf ^ 1)),
+                            lane);
         cp_async_commit();
-        // this warp's rows are free once its own stores of the last tile read them
-        __syncwarp();
 #pragma unroll
         for (int i = lane; i < 2 * RW * 8; i += 32) my_sets[i] = make_uint4(0, 0, 0, 0);
         cp_async_wait<1>();  // this tile's words have landed (the next tile's may not)
-        __syncthreads();
+        __syncwarp();
 
         // token starts of this core: [0, n_lane) (clipped at the reference end)
         {
-            const int64_t left = len - Q + 1 - (c0 + k) * (int64_t)bin_len;
+            const int64_t left = len - Q + 1 - (c0 + lane) * (int64_t)bin_len;
             const int n_lane = left <= 0 ? 0 : (left < bin_len ? (int)left : bin_len);
-            const uint32_t* st = stage + stage_words * buf;
-            const int g = k * wpc;
+            const uint32_t* st = my_stage + stage_words * buf;
+            const int g = lane * wpc;
             uint32_t hi = reverse_bases(st[stage_pos(g)]);
             for (int j = 0; j < wpc; j++) {
                 const uint32_t lo = reverse_bases(st[stage_pos(g + j + 1)]);
@@ -338,65 +343,56 @@ bank_build_lanes_kernel(const uint8_t* __restrict__ ref2bit, int64_t len, int bi
                 hi = lo;
             }
         }
-        __syncthreads();
+        __syncwarp();
 
-        // this core's bin row: P|R of cores k .. k+J, P of core k+J+1
+        // this core's bin row: P|R of cores lane .. lane+J, P of core
+        // lane+J+1, the neighbours' words by shuffle
         uint32_t v[RW];
 #pragma unroll
-        for (int w = 0; w < RW; w++) v[w] = 0;
-        const int64_t b = c0 + k;
-        if (k < out_per_cta && b < n_bins) {
-            for (int i = 0; i <= J + 1; i++) {
-                const int m = k + i;
-                const uint32_t* Pm = rows + ((m >> 5) * 2) * (RW * 32) + (m & 31);
-                const uint32_t* Rm = Pm + RW * 32;
-                if (i <= J) {
-#pragma unroll
-                    for (int w = 0; w < RW; w++) v[w] |= Pm[w * 32] | Rm[w * 32];
-                } else {
-#pragma unroll
-                    for (int w = 0; w < RW; w++) v[w] |= Pm[w * 32];
-                }
-            }
+        for (int w = 0; w < RW; w++) {
+            const uint32_t pw = myP[32 * w];
+            const uint32_t cw = pw | myR[32 * w];
+            uint32_t x = cw;
+            for (int i = 1; i <= J; i++) x |= __shfl_down_sync(kFull, cw, i);
+            v[w] = x | __shfl_down_sync(kFull, pw, J + 1);
         }
-        __syncthreads();
+        __syncwarp();
 
         // rows through the warp's R row set (free now) in row-major order,
         // 16-byte chunks swizzled by lane, then 512-byte stores
-        uint8_t* out_s = reinterpret_cast<uint8_t*>(rows) + (warp * 2 + 1) * LG::kRowSetBytes;
+        uint8_t* out_s = reinterpret_cast<uint8_t*>(myR - lane);
 #pragma unroll
         for (int c = 0; c < LG::kChunks; c++)
             *reinterpret_cast<uint4*>(out_s + lane * (RW * 4) + 16 * (c ^ (lane & (LG::kChunks - 1)))) =
                 make_uint4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
         __syncwarp();
-        const int64_t bw = c0 + warp * 32;  // the warp's first bin
-        int n_rows = out_per_cta - warp * 32;
-        if (n_rows > 32) n_rows = 32;
-        if (bw + n_rows > n_bins) n_rows = (int)(n_bins - bw);
+        int n_rows = out_w;
+        if (c0 + n_rows > n_bins) n_rows = (int)(n_bins - c0);
 #pragma unroll
         for (int i = 0; i < LG::kChunks; i++) {
             const int o = (i * 32 + lane) * 16;  // byte offset in the staged rows
             const int r = o / (RW * 4), slot = (o % (RW * 4)) / 16;
             const int c = slot ^ (r & (LG::kChunks - 1));
             if (r < n_rows)
-                reinterpret_cast<uint4*>(bank + (bw + r) * RW)[c] = *reinterpret_cast<const uint4*>(out_s + o);
+                reinterpret_cast<uint4*>(bank + (c0 + r) * RW)[c] = *reinterpret_cast<const uint4*>(out_s + o);
         }
+        __syncwarp();  // the row sets are read before the next tile zeroes them
     }
     cp_async_wait<0>();
 }
 
 // Shared memory of the lane kernel: row sets (+ alignment slack) and two
-// staging buffers.
+// staging buffers per warp.
 template <int Q>
 constexpr size_t lane_smem_bytes(int bin_len) {
     return (size_t)kLaneWarps * 2 * LaneGeo<Q>::kRowSetBytes + LaneGeo<Q>::kRowSetBytes +
-           2 * 4 * (size_t)(kLaneCores * (bin_len >> 4) + 1 + ((kLaneCores * (bin_len >> 4) + 1) >> 5) + 1);
+           (size_t)kLaneWarps * 2 * 4 * (size_t)(32 * (bin_len >> 4) + 1 + ((32 * (bin_len >> 4) + 1) >> 5) + 1);
 }
 
 template <int Q>
 static int launch_lanes(const uint8_t* ref2bit, grim_bank* bank, cudaStream_t s, int r_pref, int J) {
-    const int out_per_cta = kLaneCores - (J + 1);
-    const int64_t n_tiles = (bank->n_bins + out_per_cta - 1) / out_per_cta;
+    const int out_w = 32 - (J + 1);
+    const int64_t n_units = (bank->n_bins + out_w - 1) / out_w;
     const size_t smem = lane_smem_bytes<Q>(bank->bin_len);
     static DeviceCache attr[64];  // per device: the largest size set so far
     const int slot = device_slot();
@@ -410,9 +406,10 @@ static int launch_lanes(const uint8_t* ref2bit, grim_bank* bank, cudaStream_t s,
     GRIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bank_build_lanes_kernel<Q>, kLaneCores, smem));
     if (per_sm < 1) return GRIM_ENOTSUP;  // cannot happen below kLaneMaxBinLen
     int64_t blocks = (int64_t)sm_count() * per_sm;
-    if (blocks > n_tiles) blocks = n_tiles;
+    const int64_t need = (n_units + kLaneWarps - 1) / kLaneWarps;
+    if (blocks > need) blocks = need;
     bank_build_lanes_kernel<Q><<<grim::fault_grid((unsigned)blocks), kLaneCores, smem, s>>>(
-        ref2bit, bank->len, bank->bin_len, r_pref, J, bank->n_bins, n_tiles, bank->bits);
+        ref2bit, bank->len, bank->bin_len, r_pref, J, bank->n_bins, n_units, bank->bits);
     GRIM_CUDA_TRY(cudaGetLastError());
     return GRIM_OK;
 }

@@ -112,13 +112,16 @@ __device__ __forceinline__ uint32_t row_sum_csa(const uint4 (&v)[2], const uint4
 // requested kAhead steps before they are scored, into kBufs rotating
 // register buffers.  A past-the-end or out-of-range id fetches row 0, which
 // is scored but never stored.
-template <int Q>
+template <int Q, bool DEEP>
 struct Stream {
     using G = GatherGeo<Q>;
     static constexpr int kWinSteps = 32 / G::kBPS;       // steps per id window
-    // row buffers (a divisor of kWinSteps): two for q <= 5, whose smaller
-    // register budget lets 4 CTAs share an SM; four for q = 6
-    static constexpr int kBufs = (Q <= 5 && kWinSteps >= 2) ? 2 : (kWinSteps >= 4 ? 4 : kWinSteps);
+    // row buffers (a divisor of kWinSteps): two for q <= 5 with the bank in
+    // L2, whose smaller register budget lets 4 CTAs share an SM; four for
+    // q = 6 and for banks read from HBM (DEEP: three steps of rows in flight
+    // per warp cover the longer latency)
+    static constexpr int kBufs =
+        (Q <= 5 && !DEEP && kWinSteps >= 2) ? 2 : (kWinSteps >= 4 ? 4 : kWinSteps);
     static constexpr int kAhead = kBufs - 1;                      // steps a row is requested early
     static_assert(kWinSteps % kBufs == 0, "buffer rotation must repeat every window");
     uint32_t win_cur, win_next;  // candidate ids c = base + lane, base + 32 + lane
@@ -140,11 +143,11 @@ __device__ __forceinline__ void fetch_row(uint4 (&r)[GatherGeo<Q>::kVPL], uint32
 }
 
 // Before the token work: the first two id windows and the first kAhead steps' rows.
-template <int Q>
-__device__ __forceinline__ void stream_start(Stream<Q>& st, const uint32_t* __restrict__ cands, int n,
+template <int Q, bool DEEP>
+__device__ __forceinline__ void stream_start(Stream<Q, DEEP>& st, const uint32_t* __restrict__ cands, int n,
                                              const uint32_t* __restrict__ bank, uint32_t n_bins32, int lane) {
     using G = GatherGeo<Q>;
-    using S = Stream<Q>;
+    using S = Stream<Q, DEEP>;
     st.win_cur = window_id(cands, lane, n);
     st.win_next = window_id(cands, 32 + lane, n);
     const int s = lane % G::kLPB, g = lane / G::kLPB;
@@ -190,13 +193,14 @@ struct StepReducer {
 // Score the read's candidates.  NP > 0: NP planes held in registers;
 // NP == 0: P planes read from shared memory.  cands / pass / sums point at
 // the read's first candidate.
-template <int Q, int NP>
-__device__ __forceinline__ void score_read(Stream<Q>& st, const uint4* __restrict__ planes, int P, int T, int n,
-                                           const uint32_t* __restrict__ cands, const uint32_t* __restrict__ bank,
-                                           uint32_t n_bins32, uint8_t* __restrict__ pass,
-                                           uint16_t* __restrict__ sums, int lane, uint32_t& flags) {
+template <int Q, int NP, bool DEEP>
+__device__ __forceinline__ void score_read(Stream<Q, DEEP>& st, const uint4* __restrict__ planes, int P, int T,
+                                           int n, const uint32_t* __restrict__ cands,
+                                           const uint32_t* __restrict__ bank, uint32_t n_bins32,
+                                           uint8_t* __restrict__ pass, uint16_t* __restrict__ sums, int lane,
+                                           uint32_t& flags) {
     using G = GatherGeo<Q>;
-    using S = Stream<Q>;
+    using S = Stream<Q, DEEP>;
     const int s = lane % G::kLPB, g = lane / G::kLPB;
     uint4 pl[NP > 0 ? NP : 1][G::kVPL];
     if (NP > 0) {
@@ -333,7 +337,7 @@ __device__ __forceinline__ void gather_cta_setup(uint4* smem, int warps) {
 // The whole filter for read r, by one warp (steps 0-5 above).  The warp's
 // count planes are zero on entry and left zero on exit.
 // ro, re: the read's bases; co, ce: its candidates; e: its edit budget.
-template <int Q>
+template <int Q, bool DEEP>
 __device__ __forceinline__ void gather_read(int64_t ro, int64_t re, int64_t co, int64_t ce, int e,
                                             const uint32_t* __restrict__ bank, int64_t n_bins,
                                             const uint8_t* __restrict__ reads,
@@ -350,8 +354,8 @@ __device__ __forceinline__ void gather_read(int64_t ro, int64_t re, int64_t co, 
     const uint32_t n_bins32 = (uint32_t)n_bins;  // n_bins < 2^32 (checked when the bank is built)
     const int n_c = (int)(ce - co);
     const uint32_t* cands = cand_bins + co;
-    Stream<Q> st;
-    if (n_c > 0) stream_start<Q>(st, cands, n_c, bank, n_bins32, lane);
+    Stream<Q, DEEP> st;
+    if (n_c > 0) stream_start<Q, DEEP>(st, cands, n_c, bank, n_bins32, lane);
 
     bool bad_read = false;
     int L = 0;
@@ -403,16 +407,16 @@ __device__ __forceinline__ void gather_read(int64_t ro, int64_t re, int64_t co, 
         if (bad_read || used == 0)
             write_constant(co, ce, cand_bins, n_bins, !bad_read && T <= 0, pass, sums, lane, flags);
         else if (used == 1)
-            score_read<Q, 1>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+            score_read<Q, 1, DEEP>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
                              lane, flags);
         else if (used == 2)
-            score_read<Q, 2>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+            score_read<Q, 2, DEEP>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
                              lane, flags);
         else if (Q <= 5 && used == 3)  // for q = 6 three planes stay in shared memory
-            score_read<Q, 3>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+            score_read<Q, 3, DEEP>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
                              lane, flags);
         else
-            score_read<Q, 0>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
+            score_read<Q, 0, DEEP>(st, planes4, used, T, n_c, cands, bank, n_bins32, pass + co, sums ? sums + co : nullptr,
                              lane, flags);
     }
 
@@ -470,8 +474,8 @@ __device__ __forceinline__ int64_t cost_share(int64_t total, int64_t i, int64_t 
 //  - counter != nullptr: every warp claims from that zeroed device counter,
 //    which also absorbs speed differences between SMs; the batched filter
 //    resets it before each launch of its graph.
-template <int Q, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, (Q >= 6 ? 24 : 32) / WARPS)
+template <int Q, int WARPS, bool DEEP>
+__global__ void __launch_bounds__(WARPS * 32, (Q >= 6 || DEEP ? 24 : 32) / WARPS)
 gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* __restrict__ reads,
               const int64_t* __restrict__ read_offsets, int64_t n_reads, const uint32_t* __restrict__ cand_bins,
               const int64_t* __restrict__ cand_offsets, const uint16_t* __restrict__ E,
@@ -511,16 +515,20 @@ gather_kernel(const uint32_t* __restrict__ bank, int64_t n_bins, const uint8_t* 
         if ((int64_t)r0 >= r_end) break;
         const int64_t r1 = (int64_t)r0 + claim < r_end ? (int64_t)r0 + claim : r_end;
         for (int64_t r = (int64_t)r0; r < r1; r++)
-            gather_read<Q>(read_offsets[r], read_offsets[r + 1], cand_offsets[r], cand_offsets[r + 1], E[r], bank,
-                           n_bins, reads, cand_bins, pass, sums, planes, lane, flags);
+            gather_read<Q, DEEP>(read_offsets[r], read_offsets[r + 1], cand_offsets[r], cand_offsets[r + 1], E[r],
+                                 bank, n_bins, reads, cand_bins, pass, sums, planes, lane, flags);
     }
     flags = __reduce_or_sync(kFull, flags);
     if (lane == 0 && flags) atomicOr(status, flags);
 }
 
+// Banks larger than this are read from HBM rather than L2: the gather then
+// keeps three steps of rows in flight per warp (the DEEP form).
+constexpr double kDeepBankBytes = 96e6;
+
 // One launch over reads [r0, r0 + n) with `per_sm` CTAs per SM (0 = as many
 // as fit).
-template <int Q, int WARPS>
+template <int Q, int WARPS, bool DEEP>
 static int launch_range(const grim_bank* bank, const GatherArgs& a, int64_t r0, int64_t n, int per_sm, int claim,
                         unsigned long long* counter, cudaStream_t s) {
     constexpr size_t smem = gather_smem_bytes<Q>(WARPS);
@@ -529,10 +537,11 @@ static int launch_range(const grim_bank* bank, const GatherArgs& a, int64_t r0, 
     if (slot < 0) return GRIM_ENOTSUP;
     if (max_blocks_of[slot].load() == 0) {
         if (smem > 48 * 1024)
-            GRIM_CUDA_TRY(
-                cudaFuncSetAttribute(gather_kernel<Q, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            GRIM_CUDA_TRY(cudaFuncSetAttribute(gather_kernel<Q, WARPS, DEEP>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int b = 0;
-        GRIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gather_kernel<Q, WARPS>, WARPS * 32, smem));
+        GRIM_CUDA_TRY(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gather_kernel<Q, WARPS, DEEP>, WARPS * 32, smem));
         max_blocks_of[slot].store(b > 0 ? b : 1);
     }
     const int max_blocks = max_blocks_of[slot].load();
@@ -542,7 +551,7 @@ static int launch_range(const grim_bank* bank, const GatherArgs& a, int64_t r0, 
     const int64_t need = (n + (int64_t)WARPS * claim - 1) / ((int64_t)WARPS * claim);  // a claim per warp at least
     if (need < blocks) blocks = need;
     if (counter) GRIM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
-    gather_kernel<Q, WARPS><<<grim::fault_grid((unsigned)blocks), WARPS * 32, smem, s>>>(
+    gather_kernel<Q, WARPS, DEEP><<<grim::fault_grid((unsigned)blocks), WARPS * 32, smem, s>>>(
         bank->bits, bank->n_bins, a.reads, a.read_offsets + r0, n, a.cand_bins, a.cand_offsets + r0, a.E + r0,
         a.pass, a.sums, bank->status, claim, counter);
     GRIM_CUDA_TRY(cudaGetLastError());
@@ -553,11 +562,18 @@ template <int Q>
 static int launch_batches(const grim_bank* bank, const GatherArgs& a, const grim_tune& t,
                           unsigned long long* counter, cudaStream_t s) {
     const int64_t batch = t.batch_reads > 0 ? t.batch_reads : a.n_reads;
+    const bool deep = Q <= 5 && (double)bank->n_bins * (double)bank->row_words * 4.0 > kDeepBankBytes;
+    constexpr bool kDeepForm = Q <= 5;  // q = 6 keeps its rows three steps ahead in either form
     for (int64_t r0 = 0; r0 < a.n_reads; r0 += batch) {
         const int64_t n = (a.n_reads - r0) < batch ? (a.n_reads - r0) : batch;
-        const int rc = t.warps_per_cta == 4
-                           ? launch_range<Q, 4>(bank, a, r0, n, t.ctas_per_sm, t.reads_per_claim, counter, s)
-                           : launch_range<Q, 8>(bank, a, r0, n, t.ctas_per_sm, t.reads_per_claim, counter, s);
+        const int pc = t.ctas_per_sm, rc_ = t.reads_per_claim;
+        int rc;
+        if (deep)
+            rc = t.warps_per_cta == 4 ? launch_range<Q, 4, kDeepForm>(bank, a, r0, n, pc, rc_, counter, s)
+                                      : launch_range<Q, 8, kDeepForm>(bank, a, r0, n, pc, rc_, counter, s);
+        else
+            rc = t.warps_per_cta == 4 ? launch_range<Q, 4, false>(bank, a, r0, n, pc, rc_, counter, s)
+                                      : launch_range<Q, 8, false>(bank, a, r0, n, pc, rc_, counter, s);
         if (rc != GRIM_OK) return rc;
     }
     return GRIM_OK;

@@ -58,8 +58,9 @@ constexpr int kPeakSmem = kPeakABytes + kPeakBBytes + 1024 + 64;
 
 // MODE 0: kind::f8f6f4 e4m3, A smem;  1: kind::mxf4, A smem;
 //      2: kind::mxf4, A tmem;         3: kind::f8f6f4 e4m3, A tmem.
+// N: the MMA's N (256, or 128 as in the full scan).
 // The MMAs cycle over the four 32-byte K slices of one 128-byte block.
-template <int MODE>
+template <int MODE, int N>
 __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, uint32_t seed, uint32_t* status) {
     extern __shared__ uint8_t peak_smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)peak_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int64_t iters, uint32_t
     tc_fence_after();
 
     if (threadIdx.x == 0) {
-        const uint32_t idesc = kMx ? idesc_mxf4(kPeakM, kPeakN) : idesc_f8(kPeakM, kPeakN);
+        const uint32_t idesc = kMx ? idesc_mxf4(kPeakM, N) : idesc_f8(kPeakM, N);
         const uint32_t a_s = smem_addr(sA), b_s = smem_addr(sB);
         for (int64_t i = 0; i < iters; i++) {
             const uint32_t kk = (uint32_t)i & 3;
@@ -204,41 +205,42 @@ int grim_peak(int kind, int64_t work, double* units, float* ms, void* stream) {
             err = cudaGetLastError();
         }
         u = (double)work * reps;
-    } else if (kind >= GRIM_PEAK_E4M3 && kind <= GRIM_PEAK_E4M3_TMEM_A) {
+    } else if ((kind >= GRIM_PEAK_E4M3 && kind <= GRIM_PEAK_E4M3_TMEM_A) || kind == GRIM_PEAK_MXF4_TMEM_A_N128 ||
+               kind == GRIM_PEAK_E4M3_TMEM_A_N128) {
         // work = MMAs per CTA; one CTA per SM
         const size_t smem = grim::kPeakSmem;
-        const int mode = kind - GRIM_PEAK_E4M3;
+        const int mode = kind == GRIM_PEAK_MXF4_TMEM_A_N128 ? 2
+                         : kind == GRIM_PEAK_E4M3_TMEM_A_N128 ? 3
+                                                              : kind - GRIM_PEAK_E4M3;
         const int k_elems = (mode == 1 || mode == 2) ? 64 : 32;
+        const int n_mma = kind >= GRIM_PEAK_MXF4_TMEM_A_N128 ? 128 : grim::kPeakN;
         scratch_bytes = 256;
         if (err == cudaSuccess) err = grim::scratch_alloc(&scratch, scratch_bytes, s);
         if (err == cudaSuccess) err = cudaMemsetAsync(scratch, 0, 4, s);
+        const bool n128 = kind >= GRIM_PEAK_MXF4_TMEM_A_N128;
         auto launch = [&](int64_t iters) {
             uint32_t* st = (uint32_t*)scratch;
-            switch (mode) {
-                case 0:
-                    grim::tc_peak_kernel<0><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st);
-                    break;
-                case 1:
-                    grim::tc_peak_kernel<1><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st);
-                    break;
-                case 2:
-                    grim::tc_peak_kernel<2><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st);
-                    break;
-                default:
-                    grim::tc_peak_kernel<3><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st);
-                    break;
+            switch (mode + (n128 ? 4 : 0)) {
+                case 0: grim::tc_peak_kernel<0, 256><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
+                case 1: grim::tc_peak_kernel<1, 256><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
+                case 2: grim::tc_peak_kernel<2, 256><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
+                case 3: grim::tc_peak_kernel<3, 256><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
+                case 6: grim::tc_peak_kernel<2, 128><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
+                default: grim::tc_peak_kernel<3, 128><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
             }
             return cudaGetLastError();
         };
         const cudaFuncAttribute kSmemAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        if (err == cudaSuccess) err = cudaFuncSetAttribute(grim::tc_peak_kernel<0>, kSmemAttr, (int)smem);
-        if (err == cudaSuccess) err = cudaFuncSetAttribute(grim::tc_peak_kernel<1>, kSmemAttr, (int)smem);
-        if (err == cudaSuccess) err = cudaFuncSetAttribute(grim::tc_peak_kernel<2>, kSmemAttr, (int)smem);
-        if (err == cudaSuccess) err = cudaFuncSetAttribute(grim::tc_peak_kernel<3>, kSmemAttr, (int)smem);
+        if (err == cudaSuccess) err = cudaFuncSetAttribute(grim::tc_peak_kernel<0, 256>, kSmemAttr, (int)smem);
+        if (err == cudaSuccess) err = cudaFuncSetAttribute(grim::tc_peak_kernel<1, 256>, kSmemAttr, (int)smem);
+        if (err == cudaSuccess) err = cudaFuncSetAttribute(grim::tc_peak_kernel<2, 256>, kSmemAttr, (int)smem);
+        if (err == cudaSuccess) err = cudaFuncSetAttribute(grim::tc_peak_kernel<3, 256>, kSmemAttr, (int)smem);
+        if (err == cudaSuccess) err = cudaFuncSetAttribute(grim::tc_peak_kernel<2, 128>, kSmemAttr, (int)smem);
+        if (err == cudaSuccess) err = cudaFuncSetAttribute(grim::tc_peak_kernel<3, 128>, kSmemAttr, (int)smem);
         if (err == cudaSuccess) err = launch(work < 64 ? work : 64);  // warm-up
         if (err == cudaSuccess) err = cudaEventRecord(e0, s);
         if (err == cudaSuccess) err = launch(work);
-        u = 2.0 * grim::kPeakM * grim::kPeakN * k_elems * (double)work * sms;
+        u = 2.0 * grim::kPeakM * n_mma * k_elems * (double)work * sms;
     } else if (kind == GRIM_PEAK_INT8_MMA_SYNC) {
         // work = loop trips; 8 mma.sync per trip per warp
         const int blocks = sms * 4, threads = 256;
@@ -263,7 +265,7 @@ int grim_peak(int kind, int64_t work, double* units, float* ms, void* stream) {
     float t = 0;
     if (rc == GRIM_OK && err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
     uint32_t flags = 0;
-    if (rc == GRIM_OK && err == cudaSuccess && kind >= GRIM_PEAK_E4M3 && kind <= GRIM_PEAK_E4M3_TMEM_A)
+    if (rc == GRIM_OK && err == cudaSuccess && kind >= GRIM_PEAK_E4M3 && kind != GRIM_PEAK_INT8_MMA_SYNC)
         err = cudaMemcpy(&flags, scratch, 4, cudaMemcpyDeviceToHost);
     if (scratch) cudaFreeAsync(scratch, s);
     cudaEventDestroy(e0);

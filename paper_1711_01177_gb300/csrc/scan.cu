@@ -27,7 +27,8 @@
 //   B   : the read tile's 128 digit rows x K/2 bytes, staged once per work
 //         item in shared memory in the 128-byte-swizzled K-major layout;
 //   bank: tiles of 128 bin rows stream through a 4-deep shared-memory ring
-//         by 1-D TMA bulk copies (warp 0);
+//         by 2-D TMA tensor copies (warp 0), 16-byte chunks swizzled across
+//         the banks so that the expanders' row reads never collide;
 //   A   : warps 2-9 (one thread per bin = per TMEM lane; two groups of four
 //         warps taking alternate K chunks) mask 512 bits of their bin's row
 //         into 512 e2m1 values and store them straight into tensor memory
@@ -41,6 +42,9 @@
 //         (read, bin, sum) triples with warp-aggregated atomics.
 // Every wait is an mbarrier try_wait bounded by a time limit; on expiry the
 // CTA raises GRIM_FLAG_TIMEOUT, drains and frees its tensor memory.
+#include <cuda.h>  // CUtensorMap (encoded through the runtime's driver entry point)
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "grim_internal.cuh"
@@ -88,6 +92,10 @@ struct ScanGeo {
     static constexpr int kChunks = kK / kChunkTok;
     static constexpr int kBBytes = kRowsTile * kKBytes;                       // staged B tile
     static constexpr int kBankTileBytes = kBinTile * kRowBytes;
+    // TMA swizzle of the bank tiles: 16-byte chunk bits [4, 7) of a shared
+    // address XOR its bits [7, 10) (128-byte rows), bit 4 XOR bit 7 (32-byte
+    // rows), none for 16-byte rows
+    static constexpr uint32_t kSwzMask = kRowBytes >= 128 ? 7u : (kRowBytes >= 32 ? 1u : 0u);
     static_assert(kRowBytes * 8 <= kK, "a bank row fits the padded K");
     static_assert(kKBytes % 128 == 0 && kACols <= 64, "B rows are whole 128-byte swizzle atoms");
 };
@@ -309,7 +317,7 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     for (int64_t bt = bt0; bt < bt1; bt++) {
         const uint32_t buf = acc_cnt & 1, phb = (acc_cnt >> 1) & 1;
-        if (!__all_sync(kFull, mbar_wait(&acc_full[buf], phb, abort_flag))) break;
+        if (!mbar_wait_warp(&acc_full[buf], phb, abort_flag)) break;
         tc_fence_after();
         const uint32_t col0 = tmem + lane_base + kAccCol + buf * kRowsTile;
         const int64_t b = P.bin_begin + bt * kBinTile + m;
@@ -328,8 +336,15 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
                     if (lane == 0) mbar_arrive(&acc_empty[buf]);
                 }
                 uint32_t any = 0;
+                const float4* t4 = reinterpret_cast<const float4*>(sTf + 64 * h);
 #pragma unroll
-                for (int i = 0; i < 64; i++) any |= (uint32_t)(__uint_as_float(v[i]) >= sTf[64 * h + i]);
+                for (int i = 0; i < 16; i++) {
+                    const float4 t = t4[i];  // four thresholds in one shared load
+                    any |= (uint32_t)(__uint_as_float(v[4 * i]) >= t.x) |
+                           (uint32_t)(__uint_as_float(v[4 * i + 1]) >= t.y) |
+                           (uint32_t)(__uint_as_float(v[4 * i + 2]) >= t.z) |
+                           (uint32_t)(__uint_as_float(v[4 * i + 3]) >= t.w);
+                }
                 if (__any_sync(kFull, bin_ok && any)) {
                     int sums[64];
 #pragma unroll
@@ -360,8 +375,13 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
                     if (lane == 0) mbar_arrive(&acc_empty[buf]);
                 }
                 uint32_t any = 0;
+                const int4* t4 = reinterpret_cast<const int4*>(sT + G * g);
 #pragma unroll
-                for (int i = 0; i < G; i++) any |= (uint32_t)(acc[i] >= sT[G * g + i]);
+                for (int i = 0; i < G / 4; i++) {
+                    const int4 t = t4[i];
+                    any |= (uint32_t)(acc[4 * i] >= t.x) | (uint32_t)(acc[4 * i + 1] >= t.y) |
+                           (uint32_t)(acc[4 * i + 2] >= t.z) | (uint32_t)(acc[4 * i + 3] >= t.w);
+                }
                 if (__any_sync(kFull, bin_ok && any))
                     scan_emit<G>(P, acc, G * g, valid_reads, sT, sRid, b, bin_ok, lane);
             }
@@ -371,7 +391,7 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
 }
 
 template <int Q>
-__global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
+__global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(const __grid_constant__ CUtensorMap tmap, ScanParams P) {
     using G = ScanGeo<Q>;
     using S = ScanSmem<Q>;
     extern __shared__ uint8_t scan_smem_raw[];
@@ -492,11 +512,9 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
                     const uint32_t s = bank_cnt % kBankStages, ph = (bank_cnt / kBankStages) & 1;
                     if (!mbar_wait(&bank_empty[s], ph ^ 1, abort_flag)) break;
                     const int64_t b0 = P.bin_begin + bt * kBinTile;
-                    const int rows = (int)((P.bin_end - b0) < kBinTile ? (P.bin_end - b0) : (int64_t)kBinTile);
-                    const uint32_t bytes = (uint32_t)rows * G::kRowBytes;
-                    mbar_arrive_expect_tx(&bank_full[s], bytes);
-                    bulk_copy_g2s(sBank + (size_t)s * G::kBankTileBytes, P.bank + (size_t)b0 * G::kRowWords, bytes,
-                                  &bank_full[s]);
+                    // the whole box arrives; rows past the bank read as zeros
+                    mbar_arrive_expect_tx(&bank_full[s], (uint32_t)G::kBankTileBytes);
+                    tma_load_2d(sBank + (size_t)s * G::kBankTileBytes, &tmap, 0, (int)b0, &bank_full[s]);
                     bank_cnt++;
                 }
             }
@@ -543,11 +561,10 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
             const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
             for (int64_t bt = bt0; bt < bt1; bt++) {
                 const uint32_t s = bank_cnt % kBankStages, ph = (bank_cnt / kBankStages) & 1;
-                if (!__all_sync(kFull, mbar_wait(&bank_full[s], ph, abort_flag))) break;
+                if (!mbar_wait_warp(&bank_full[s], ph, abort_flag)) break;
                 const int64_t b0 = P.bin_begin + bt * kBinTile;
                 const int rows = (int)((P.bin_end - b0) < kBinTile ? (P.bin_end - b0) : (int64_t)kBinTile);
-                const uint4* myrow = reinterpret_cast<const uint4*>(sBank + (size_t)s * G::kBankTileBytes +
-                                                                    (size_t)m * G::kRowBytes);
+                const uint32_t tile_off = (uint32_t)s * G::kBankTileBytes + (uint32_t)m * G::kRowBytes;
                 bool ok = true;
                 for (int c = 0; c < G::kChunks; c++, a_cnt++) {
                     if ((a_cnt & 1u) != group) continue;
@@ -558,9 +575,12 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
 #pragma unroll
                     for (int u = 0; u < kVec; u++) {
                         const int wv = c * kVec + u;  // 16-byte vector of the row
-                        bits[u] = (m < rows && 4 * wv < G::kRowWords) ? myrow[wv] : make_uint4(0, 0, 0, 0);
+                        const uint32_t a = tile_off + 16u * wv;  // unswizzled offset, then the TMA's pattern
+                        const uint32_t off = a ^ (((a >> 7) & G::kSwzMask) << 4);
+                        bits[u] = (m < rows && 4 * wv < G::kRowWords) ? *reinterpret_cast<const uint4*>(sBank + off)
+                                                                      : make_uint4(0, 0, 0, 0);
                     }
-                    if (!__all_sync(kFull, mbar_wait(&a_empty[sa], pha ^ 1, abort_flag))) {
+                    if (!mbar_wait_warp(&a_empty[sa], pha ^ 1, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -636,6 +656,41 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(ScanParams P) {
 
 // ------------------------------------------------------------ host launch
 
+// cuTensorMapEncodeTiled, looked up once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// The bank as a 2-D tensor of n_bins rows x row bytes, read in boxes of
+// 128 rows, swizzled as ScanGeo::kSwzMask describes.
+template <int Q>
+static int bank_tensor_map(const grim_bank* bank, CUtensorMap* map) {
+    using G = ScanGeo<Q>;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return GRIM_ENOTSUP;
+    const cuuint64_t dims[2] = {(cuuint64_t)G::kRowBytes, (cuuint64_t)bank->n_bins};
+    const cuuint64_t strides[1] = {(cuuint64_t)G::kRowBytes};
+    const cuuint32_t box[2] = {(cuuint32_t)G::kRowBytes, (cuuint32_t)kBinTile};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapSwizzle swz = G::kSwzMask == 7u ? CU_TENSOR_MAP_SWIZZLE_128B
+                                   : G::kSwzMask == 1u ? CU_TENSOR_MAP_SWIZZLE_32B
+                                                       : CU_TENSOR_MAP_SWIZZLE_NONE;
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)bank->bits, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? GRIM_OK : GRIM_ECUDA;
+}
+
 template <int Q>
 static int launch_scan_q(const grim_bank* bank, const uint8_t* reads, const int64_t* read_offsets, int64_t n_reads,
                          const uint16_t* E, int64_t bin_begin, int64_t bin_end, const ScanOut& out, void* scratch,
@@ -692,7 +747,11 @@ static int launch_scan_q(const grim_bank* bank, const uint8_t* reads, const int6
         P.sc = sc;
         P.out = out;
         P.status = bank->status;
-        scan_kernel<Q><<<grim::fault_grid(sm_count()), kScanThreads, smem, s>>>(P);
+        if (bin_end > (int64_t)0x7fffffff) return GRIM_ENOTSUP;  // TMA row coordinates are 32-bit
+        CUtensorMap tmap;
+        const int rc = bank_tensor_map<Q>(bank, &tmap);
+        if (rc != GRIM_OK) return rc;
+        scan_kernel<Q><<<grim::fault_grid(sm_count()), kScanThreads, smem, s>>>(tmap, P);
         GRIM_CUDA_TRY(cudaGetLastError());
     }
     return GRIM_OK;

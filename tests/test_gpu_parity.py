@@ -92,6 +92,23 @@ def test_filter_plain_gather_workload_full(oracle):
     bank.free()
 
 
+def test_filter_bank_beyond_l2_takes_the_deep_form(oracle):
+    """A 200 Mbp bank (100 MB at q=5, beyond the L2) is read by the gather
+    form that keeps three steps of rows in flight; every pass byte and sum
+    against the oracle, each candidate's bitvector rebuilt from the reference."""
+    w = synth.gather_iid(ref_len=200_000_000, n_reads=20_000, k=32)
+    bank = gpu_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
+    assert bank.n_bins * bank.row_words * 4 > 96e6
+    p, s, st, flags = run_filter(bank, w.bases, w.read_offsets, w.cand_bins, w.cand_offsets, w.E)
+    assert st == grim.GRIM_OK and flags == 0
+    op, os_ = oracle.filter_rows(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap, w.bases, w.read_offsets,
+                                 w.cand_bins, w.cand_offsets, w.E)
+    assert np.array_equal(s, os_.astype(np.uint16))
+    assert np.array_equal(p, op)
+    assert 0 < p.sum() < len(p)
+    bank.free()
+
+
 @pytest.mark.parametrize("q", [1, 2, 3, 4, 5, 6])
 def test_filter_every_q_ragged(oracle, q):
     rng = np.random.default_rng(40 + q)
