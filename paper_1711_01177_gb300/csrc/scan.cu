@@ -29,17 +29,18 @@
 //   bank: tiles of 128 bin rows stream through a 4-deep shared-memory ring
 //         by 2-D TMA tensor copies (warp 0), 16-byte chunks swizzled across
 //         the banks so that the expanders' row reads never collide;
-//   A   : warps 2-9 (one thread per bin = per TMEM lane; two groups of four
-//         warps taking alternate K chunks) mask 512 bits of their bin's row
-//         into 512 e2m1 values and store them straight into tensor memory
-//         (3 stages of 64 columns, 8 MMAs per stage) - the expanded operand
-//         never touches shared memory;
+//   A   : warps 2-5 (one thread per bin = per TMEM lane) mask 512 bits of
+//         their bin's row into 512 e2m1 values and store them straight into
+//         tensor memory (3 stages of 64 columns, 8 MMAs per stage) - the
+//         expanded operand never touches shared memory;
 //   MMA : warp 1 issues M=128 (bins) x N=128 (rows) x K=64 tcgen05.mma with A
 //         from TMEM, B from shared memory and the unit scale factors from
 //         TMEM, accumulating in TMEM (two 128-column accumulators);
-//   out : warps 10-13 read the accumulators with tcgen05.ld, recombine digits,
-//         compare with each read's threshold and append the rare passing
-//         (read, bin, sum) triples with warp-aggregated atomics.
+//   out : warps 6-13, two per lane quadrant, each read half of the tile's
+//         accumulator columns with tcgen05.ld, hand the accumulator back to
+//         the MMAs as soon as the values are in registers, then recombine
+//         digits, compare with each read's threshold and append the rare
+//         passing (read, bin, sum) triples with warp-aggregated atomics.
 // Every wait is an mbarrier try_wait bounded by a time limit; on expiry the
 // CTA raises GRIM_FLAG_TIMEOUT, drains and frees its tensor memory.
 #include <cuda.h>  // CUtensorMap (encoded through the runtime's driver entry point)
@@ -61,9 +62,9 @@ static __device__ __align__(256) uint8_t g_scan_scratch[GRIM_SCAN_NOALLOC_SCRATC
 
 // ------------------------------------------------------------ constants
 
-constexpr int kScanThreads = 448;   // 14 warps: TMA, MMA, 2 x 4 expand, 4 epilogue
-constexpr int kExpandWarp0 = 2;     // expander warps 2..9: group (warp-2)/4 takes every other K chunk
-constexpr int kEpilogueWarp0 = 10;  // epilogue warps 10..13
+constexpr int kScanThreads = 448;   // 14 warps: TMA, MMA, 4 expand, 8 epilogue
+constexpr int kExpandWarp0 = 2;     // expander warps 2..5, one per TMEM lane quadrant
+constexpr int kEpilogueWarp0 = 6;   // epilogue warps 6..13: two per quadrant, each half of the reads
 constexpr int kBinTile = 128;       // bins per MMA tile (M, TMEM lanes)
 constexpr int kRowsTile = 128;      // B rows per read tile (N)
 constexpr int kBankStages = 4;
@@ -299,9 +300,11 @@ __device__ __forceinline__ void scan_emit(const ScanParams& P, const int* sums, 
 }
 
 // Epilogue of one work item for reads with D base-4 digits (N = 128 / D
-// reads per tile): thread = bin row = TMEM lane of its warp's quadrant.
-// Accumulator column d*N + n holds the digit-d sum of read n (an exact
-// integer in f32); Sum = sum_d 4^d * column d*N + n.
+// reads per tile): thread = bin row = TMEM lane of its warp's quadrant; the
+// warp takes reads [half * N/2, (half + 1) * N/2).  Accumulator column
+// d*N + n holds the digit-d sum of read n (an exact integer in f32);
+// Sum = sum_d 4^d * column d*N + n.  All of the warp's columns are loaded
+// before the accumulator is handed back.
 template <int D>
 __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem, uint64_t* acc_full,
                                               uint64_t* acc_empty, volatile int* abort_flag,
@@ -309,12 +312,13 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
                                               const uint32_t* __restrict__ sRid, int valid_reads, int64_t bt0,
                                               int64_t bt1, uint32_t& acc_cnt) {
     constexpr int N = kRowsTile / D;
-    constexpr int G = N < 32 ? N : 32;  // reads per group
-    constexpr int DPL = 32 / G;         // digits per 32-column load
+    constexpr int G = N / 2;  // reads of this warp: 64, 32, 16, 8 (64 loaded columns in all)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quad = warp & 3;
+    const int half = (warp - kEpilogueWarp0) >> 2;
     const int m = quad * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    const int n0 = half * G;  // first read of this warp
     for (int64_t bt = bt0; bt < bt1; bt++) {
         const uint32_t buf = acc_cnt & 1, phb = (acc_cnt >> 1) & 1;
         if (!mbar_wait_warp(&acc_full[buf], phb, abort_flag)) break;
@@ -322,69 +326,48 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
         const uint32_t col0 = tmem + lane_base + kAccCol + buf * kRowsTile;
         const int64_t b = P.bin_begin + bt * kBinTile + m;
         const bool bin_ok = b < P.bin_end;
+        uint32_t v[64];
+#pragma unroll
+        for (int d = 0; d < D; d++) tmem_ld<G>(col0 + d * N + n0, v + d * G);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
         if (D == 1) {
             // one digit: the accumulator is the sum; compare it with T in f32
+            uint32_t any = 0;
+            const float4* t4 = reinterpret_cast<const float4*>(sTf + n0);
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                uint32_t v[64];
-                tmem_ld32(col0 + 64 * h, v);
-                tmem_ld32(col0 + 64 * h + 32, v + 32);
-                tmem_wait_ld();
-                if (h == 1) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&acc_empty[buf]);
-                }
-                uint32_t any = 0;
-                const float4* t4 = reinterpret_cast<const float4*>(sTf + 64 * h);
+            for (int i = 0; i < G / 4; i++) {
+                const float4 t = t4[i];  // four thresholds in one shared load
+                any |= (uint32_t)(__uint_as_float(v[4 * i]) >= t.x) |
+                       (uint32_t)(__uint_as_float(v[4 * i + 1]) >= t.y) |
+                       (uint32_t)(__uint_as_float(v[4 * i + 2]) >= t.z) |
+                       (uint32_t)(__uint_as_float(v[4 * i + 3]) >= t.w);
+            }
+            if (__any_sync(kFull, bin_ok && any)) {
+                int sums[G];
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const float4 t = t4[i];  // four thresholds in one shared load
-                    any |= (uint32_t)(__uint_as_float(v[4 * i]) >= t.x) |
-                           (uint32_t)(__uint_as_float(v[4 * i + 1]) >= t.y) |
-                           (uint32_t)(__uint_as_float(v[4 * i + 2]) >= t.z) |
-                           (uint32_t)(__uint_as_float(v[4 * i + 3]) >= t.w);
-                }
-                if (__any_sync(kFull, bin_ok && any)) {
-                    int sums[64];
-#pragma unroll
-                    for (int i = 0; i < 64; i++) sums[i] = (int)__uint_as_float(v[i]);
-                    scan_emit<64>(P, sums, 64 * h, valid_reads, sT, sRid, b, bin_ok, lane);
-                }
+                for (int i = 0; i < G; i++) sums[i] = (int)__uint_as_float(v[i]);
+                scan_emit<G>(P, sums, n0, valid_reads, sT, sRid, b, bin_ok, lane);
             }
         } else {
-            // D digits: groups of G reads, DPL digit columns per 32-column load
+            int acc[G];
 #pragma unroll
-            for (int g = 0; g < N / G; g++) {
-                int acc[G];
+            for (int i = 0; i < G; i++) {
+                acc[i] = 0;
 #pragma unroll
-                for (int i = 0; i < G; i++) acc[i] = 0;
-#pragma unroll
-                for (int d = 0; d < D; d += DPL) {
-                    uint32_t v[32];
-                    tmem_ld32(col0 + d * N + G * g, v);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int e = 0; e < DPL; e++)
-#pragma unroll
-                        for (int i = 0; i < G; i++) acc[i] += (int)__uint_as_float(v[e * G + i]) << (2 * (d + e));
-                }
-                if (g == N / G - 1) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&acc_empty[buf]);
-                }
-                uint32_t any = 0;
-                const int4* t4 = reinterpret_cast<const int4*>(sT + G * g);
-#pragma unroll
-                for (int i = 0; i < G / 4; i++) {
-                    const int4 t = t4[i];
-                    any |= (uint32_t)(acc[4 * i] >= t.x) | (uint32_t)(acc[4 * i + 1] >= t.y) |
-                           (uint32_t)(acc[4 * i + 2] >= t.z) | (uint32_t)(acc[4 * i + 3] >= t.w);
-                }
-                if (__any_sync(kFull, bin_ok && any))
-                    scan_emit<G>(P, acc, G * g, valid_reads, sT, sRid, b, bin_ok, lane);
+                for (int d = 0; d < D; d++) acc[i] += (int)__uint_as_float(v[d * G + i]) << (2 * d);
             }
+            uint32_t any = 0;
+            const int4* t4 = reinterpret_cast<const int4*>(sT + n0);
+#pragma unroll
+            for (int i = 0; i < G / 4; i++) {
+                const int4 t = t4[i];
+                any |= (uint32_t)(acc[4 * i] >= t.x) | (uint32_t)(acc[4 * i + 1] >= t.y) |
+                       (uint32_t)(acc[4 * i + 2] >= t.z) | (uint32_t)(acc[4 * i + 3] >= t.w);
+            }
+            if (__any_sync(kFull, bin_ok && any)) scan_emit<G>(P, acc, n0, valid_reads, sT, sRid, b, bin_ok, lane);
         }
         acc_cnt++;
     }
@@ -420,7 +403,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(const __grid_cons
     if (threadIdx.x == 0) {
         for (int i = 0; i < kBankStages; i++) {
             mbar_init(&bank_full[i], 1);
-            mbar_init(&bank_empty[i], 8);
+            mbar_init(&bank_empty[i], 4);
         }
         for (int i = 0; i < kAStages; i++) {
             mbar_init(&a_full[i], 4);
@@ -428,7 +411,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(const __grid_cons
         }
         for (int i = 0; i < 2; i++) {
             mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], 4);
+            mbar_init(&acc_empty[i], 8);
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -439,7 +422,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(const __grid_cons
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    if (warp >= kEpilogueWarp0) {
+    if (warp >= kEpilogueWarp0 && warp < kEpilogueWarp0 + 4) {
         // unit scale factors (ue8m0 127 = 1.0 in every byte) for A and B
         uint32_t v[32];
 #pragma unroll
@@ -553,10 +536,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(const __grid_cons
                 }
             }
         } else if (warp < kEpilogueWarp0) {
-            // ---- expanders: thread = bin row = TMEM lane; group g takes the
-            // K chunks whose running index has parity g (alternate A stages)
+            // ---- expanders: thread = bin row = TMEM lane
             const int quad = warp & 3;
-            const uint32_t group = (uint32_t)((warp - kExpandWarp0) >> 2);
             const int m = quad * 32 + lane;
             const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
             for (int64_t bt = bt0; bt < bt1; bt++) {
@@ -567,7 +548,6 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(const __grid_cons
                 const uint32_t tile_off = (uint32_t)s * G::kBankTileBytes + (uint32_t)m * G::kRowBytes;
                 bool ok = true;
                 for (int c = 0; c < G::kChunks; c++, a_cnt++) {
-                    if ((a_cnt & 1u) != group) continue;
                     const uint32_t sa = a_cnt % kAStages, pha = (a_cnt / kAStages) & 1;
                     // this stage's bank words (rows shorter than the padded K read as 0)
                     constexpr int kVec = G::kWordsPerChunk / 4;
