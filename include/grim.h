@@ -371,9 +371,9 @@ int grim_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read_o
  * (64 MiB) compiled into the library: every GPU on which the library is
  * loaded holds it until the process exits.  A call needing more is
  * rejected with GRIM_ESCRATCH before anything is enqueued; the need is
- * 256 + sum over c = 0 .. 3 of ceil(n_reads / (128 >> c)) * 128 * K / 2
+ * 256 + sum over c = 0 .. 3 of ceil(n_reads / (256 >> c)) * 256 * K / 2
  * bytes (K = max(256, 4^q)) plus two small index arrays per c, which allows
- * at most 8,688 reads per call at q = 5 and 34,368 at q <= 4.
+ * at most 8,672 reads per call at q = 5 and 34,336 at q <= 4.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any
  * stream capture.  Every call uses the same array and finds the previous

@@ -90,8 +90,8 @@ void form_costs(const grim_bank* bank, int64_t n_reads, int64_t n_checks, double
         const double bank_bytes = (double)bank->n_bins * row_bytes;
         rg = bank_bytes > 96e6 ? 6.0e12 / (row_bytes + 5.0) : 3.5e10;
     }
-    // full scan: 2 * 4^q flops per check on the e4m3 tensor path at ~1.8e15 flops/s
-    const double rs = bank->q <= GRIM_MAX_SCAN_Q ? 1.8e15 / (2.0 * (double)(int64_t(1) << (2 * bank->q))) : 0.0;
+    // full scan: 2 * 4^q flops per check on the FP4 (mxf4) tensor path at ~4.5e15 flops/s
+    const double rs = bank->q <= GRIM_MAX_SCAN_Q ? 4.5e15 / (2.0 * (double)(int64_t(1) << (2 * bank->q))) : 0.0;
     *t_gather = (double)n_checks / rg + (double)n_reads * 2e-10;
     *t_scan = rs > 0 ? (double)n_reads * (double)bank->n_bins / rs + 50e-6 : 1e30;
 }

@@ -20,11 +20,11 @@
 // accumulation is exact and the pass decision is bit-identical to counting
 // tokens one by one.  Reads whose counts stay below 4 (nearly all) take one
 // row; counts up to 15, 255 and 65,535 take 2, 4 and 8; the prep kernel packs
-// reads into tiles of 128 rows by digit class (128 x 1, 64 x 2, 32 x 4, 16 x 8).
+// reads into tiles of 256 rows by digit class (256 x 1, 128 x 2, 64 x 4, 32 x 8).
 //
 // Data flow per CTA (persistent, one per SM; a work item = one read tile x
 // one run of bin tiles):
-//   B   : the read tile's 128 digit rows x K/2 bytes, staged once per work
+//   B   : the read tile's 256 digit rows x K/2 bytes, staged once per work
 //         item in shared memory in the 128-byte-swizzled K-major layout;
 //   bank: tiles of 128 bin rows stream through a 4-deep shared-memory ring
 //         by 2-D TMA tensor copies (warp 0), 16-byte chunks swizzled across
@@ -33,14 +33,17 @@
 //         their bin's row into 512 e2m1 values and store them straight into
 //         tensor memory (3 stages of 64 columns, 8 MMAs per stage) - the
 //         expanded operand never touches shared memory;
-//   MMA : warp 1 issues M=128 (bins) x N=128 (rows) x K=64 tcgen05.mma with A
+//   MMA : warp 1 issues M=128 (bins) x N=256 (rows) x K=64 tcgen05.mma with A
 //         from TMEM, B from shared memory and the unit scale factors from
-//         TMEM, accumulating in TMEM (two 128-column accumulators);
-//   out : warps 6-13, two per lane quadrant, each read half of the tile's
-//         accumulator columns with tcgen05.ld, hand the accumulator back to
-//         the MMAs as soon as the values are in registers, then recombine
-//         digits, compare with each read's threshold and append the rare
-//         passing (read, bin, sum) triples with warp-aggregated atomics.
+//         TMEM, accumulating in one 256-column TMEM accumulator (at N=256 an
+//         MMA runs at the full rate whatever the commits and operand
+//         rotation around it; at N=128 those cost ~40%);
+//   out : warps 6-21, four per lane quadrant, each load a quarter of the
+//         tile's accumulator columns (64) with tcgen05.ld in one round and
+//         hand the accumulator back to the MMAs at once (with one
+//         accumulator, the MMAs wait for it), then recombine digits,
+//         compare with each read's threshold and append the rare passing
+//         (read, bin, sum) triples with warp-aggregated atomics.
 // Every wait is an mbarrier try_wait bounded by a time limit; on expiry the
 // CTA raises GRIM_FLAG_TIMEOUT, drains and frees its tensor memory.
 #include <cuda.h>  // CUtensorMap (encoded through the runtime's driver entry point)
@@ -62,14 +65,15 @@ static __device__ __align__(256) uint8_t g_scan_scratch[GRIM_SCAN_NOALLOC_SCRATC
 
 // ------------------------------------------------------------ constants
 
-constexpr int kScanThreads = 448;   // 14 warps: TMA, MMA, 4 expand, 8 epilogue
+constexpr int kScanThreads = 704;   // 22 warps: TMA, MMA, 4 expand, 16 epilogue
 constexpr int kExpandWarp0 = 2;     // expander warps 2..5, one per TMEM lane quadrant
-constexpr int kEpilogueWarp0 = 6;   // epilogue warps 6..13: two per quadrant, each half of the reads
+constexpr int kEpilogueWarp0 = 6;   // epilogue warps 6..21: four per quadrant, each a quarter of the reads
+constexpr int kEpilogueWarps = 16;
 constexpr int kBinTile = 128;       // bins per MMA tile (M, TMEM lanes)
-constexpr int kRowsTile = 128;      // B rows per read tile (N)
+constexpr int kRowsTile = 256;      // B rows per read tile (N)
 constexpr int kBankStages = 4;
 constexpr int kAStages = 3;         // A stages in tensor memory, filled by alternate expander groups
-constexpr int kAccCol = 0;          // two accumulators: columns [0, 256)
+constexpr int kAccCol = 0;          // the accumulator: columns [0, 256)
 constexpr int kSfCol = 256;         // unit scale factors of A and B: columns [256, 288)
 constexpr int kACol = 288;          // A stages: 3 x 64 columns from 288
 constexpr int kTmemCols = 512;
@@ -299,12 +303,12 @@ __device__ __forceinline__ void scan_emit(const ScanParams& P, const int* sums, 
     }
 }
 
-// Epilogue of one work item for reads with D base-4 digits (N = 128 / D
+// Epilogue of one work item for reads with D base-4 digits (N = 256 / D
 // reads per tile): thread = bin row = TMEM lane of its warp's quadrant; the
-// warp takes reads [half * N/2, (half + 1) * N/2).  Accumulator column
-// d*N + n holds the digit-d sum of read n (an exact integer in f32);
-// Sum = sum_d 4^d * column d*N + n.  All of the warp's columns are loaded
-// before the accumulator is handed back.
+// warp takes the GR = 64 / D reads from quarter * N/4, i.e. 64 accumulator
+// columns.  Column d*N + n holds the digit-d sum of read n (an exact
+// integer in f32); Sum = sum_d 4^d * column d*N + n.  The accumulator is
+// handed back as soon as the columns are in registers.
 template <int D>
 __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem, uint64_t* acc_full,
                                               uint64_t* acc_empty, volatile int* abort_flag,
@@ -312,33 +316,33 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
                                               const uint32_t* __restrict__ sRid, int valid_reads, int64_t bt0,
                                               int64_t bt1, uint32_t& acc_cnt) {
     constexpr int N = kRowsTile / D;
-    constexpr int G = N / 2;  // reads of this warp: 64, 32, 16, 8 (64 loaded columns in all)
+    constexpr int GR = 64 / D;  // reads of this warp: 64, 32, 16, 8
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quad = warp & 3;
-    const int half = (warp - kEpilogueWarp0) >> 2;
+    const int quarter = (warp - kEpilogueWarp0) >> 2;
     const int m = quad * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    const int n0 = half * G;  // first read of this warp
+    const uint32_t col0 = tmem + lane_base + kAccCol;
+    const int n0 = quarter * GR;  // first read of this warp
     for (int64_t bt = bt0; bt < bt1; bt++) {
-        const uint32_t buf = acc_cnt & 1, phb = (acc_cnt >> 1) & 1;
-        if (!mbar_wait_warp(&acc_full[buf], phb, abort_flag)) break;
+        const uint32_t phb = acc_cnt & 1;
+        if (!mbar_wait_warp(acc_full, phb, abort_flag)) break;
         tc_fence_after();
-        const uint32_t col0 = tmem + lane_base + kAccCol + buf * kRowsTile;
         const int64_t b = P.bin_begin + bt * kBinTile + m;
         const bool bin_ok = b < P.bin_end;
         uint32_t v[64];
 #pragma unroll
-        for (int d = 0; d < D; d++) tmem_ld<G>(col0 + d * N + n0, v + d * G);
+        for (int d = 0; d < D; d++) tmem_ld<GR>(col0 + d * N + n0, v + d * GR);
         tmem_wait_ld();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        if (lane == 0) mbar_arrive(acc_empty);
         if (D == 1) {
             // one digit: the accumulator is the sum; compare it with T in f32
             uint32_t any = 0;
             const float4* t4 = reinterpret_cast<const float4*>(sTf + n0);
 #pragma unroll
-            for (int i = 0; i < G / 4; i++) {
+            for (int i = 0; i < GR / 4; i++) {
                 const float4 t = t4[i];  // four thresholds in one shared load
                 any |= (uint32_t)(__uint_as_float(v[4 * i]) >= t.x) |
                        (uint32_t)(__uint_as_float(v[4 * i + 1]) >= t.y) |
@@ -346,28 +350,28 @@ __device__ __forceinline__ void scan_epilogue(const ScanParams& P, uint32_t tmem
                        (uint32_t)(__uint_as_float(v[4 * i + 3]) >= t.w);
             }
             if (__any_sync(kFull, bin_ok && any)) {
-                int sums[G];
+                int sums[GR];
 #pragma unroll
-                for (int i = 0; i < G; i++) sums[i] = (int)__uint_as_float(v[i]);
-                scan_emit<G>(P, sums, n0, valid_reads, sT, sRid, b, bin_ok, lane);
+                for (int i = 0; i < GR; i++) sums[i] = (int)__uint_as_float(v[i]);
+                scan_emit<GR>(P, sums, n0, valid_reads, sT, sRid, b, bin_ok, lane);
             }
         } else {
-            int acc[G];
+            int acc[GR];
 #pragma unroll
-            for (int i = 0; i < G; i++) {
+            for (int i = 0; i < GR; i++) {
                 acc[i] = 0;
 #pragma unroll
-                for (int d = 0; d < D; d++) acc[i] += (int)__uint_as_float(v[d * G + i]) << (2 * d);
+                for (int d = 0; d < D; d++) acc[i] += (int)__uint_as_float(v[d * GR + i]) << (2 * d);
             }
             uint32_t any = 0;
             const int4* t4 = reinterpret_cast<const int4*>(sT + n0);
 #pragma unroll
-            for (int i = 0; i < G / 4; i++) {
+            for (int i = 0; i < GR / 4; i++) {
                 const int4 t = t4[i];
                 any |= (uint32_t)(acc[4 * i] >= t.x) | (uint32_t)(acc[4 * i + 1] >= t.y) |
                        (uint32_t)(acc[4 * i + 2] >= t.z) | (uint32_t)(acc[4 * i + 3] >= t.w);
             }
-            if (__any_sync(kFull, bin_ok && any)) scan_emit<G>(P, acc, n0, valid_reads, sT, sRid, b, bin_ok, lane);
+            if (__any_sync(kFull, bin_ok && any)) scan_emit<GR>(P, acc, n0, valid_reads, sT, sRid, b, bin_ok, lane);
         }
         acc_cnt++;
     }
@@ -390,8 +394,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(const __grid_cons
     uint64_t* a_full = bars + 2 * kBankStages;
     uint64_t* a_empty = a_full + kAStages;
     uint64_t* acc_full = a_empty + kAStages;
-    uint64_t* acc_empty = acc_full + 2;
-    uint64_t* drain_bar = acc_empty + 2;
+    uint64_t* acc_empty = acc_full + 1;
+    uint64_t* drain_bar = acc_empty + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kMisc);
     volatile int* s_item = reinterpret_cast<volatile int*>(smem + S::kMisc + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + S::kMisc + 8);
@@ -409,10 +413,8 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(const __grid_cons
             mbar_init(&a_full[i], 4);
             mbar_init(&a_empty[i], 1);
         }
-        for (int i = 0; i < 2; i++) {
-            mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], 8);
-        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, kEpilogueWarps);
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -505,10 +507,10 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(const __grid_cons
             // ---- MMA issuer
             if (lane == 0) {
                 for (int64_t bt = bt0; bt < bt1; bt++) {
-                    const uint32_t buf = acc_cnt & 1, phb = (acc_cnt >> 1) & 1;
-                    if (!mbar_wait(&acc_empty[buf], phb ^ 1, abort_flag)) break;
+                    const uint32_t phb = acc_cnt & 1;
+                    if (!mbar_wait(acc_empty, phb ^ 1, abort_flag)) break;
                     tc_fence_after();
-                    const uint32_t d_tmem = tmem + kAccCol + buf * kRowsTile;
+                    const uint32_t d_tmem = tmem + kAccCol;
                     bool ok = true;
                     for (int c = 0; c < G::kChunks; c++) {
                         const uint32_t sa = a_cnt % kAStages, pha = (a_cnt / kAStages) & 1;
@@ -531,7 +533,7 @@ __global__ void __launch_bounds__(kScanThreads, 1) scan_kernel(const __grid_cons
                         a_cnt++;
                     }
                     if (!ok) break;
-                    mma_commit(&acc_full[buf]);
+                    mma_commit(acc_full);
                     acc_cnt++;
                 }
             }

@@ -30,7 +30,7 @@ from gpu_util import dev, host
 
 pytestmark = pytest.mark.gpu
 
-MAX_READS_Q5 = 8_688  # the largest request the 64 MiB array holds at q = 5
+MAX_READS_Q5 = 8_672  # the largest request the 64 MiB array holds at q = 5
 
 
 def _ptr(t):
