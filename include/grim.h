@@ -549,7 +549,8 @@ int grim_verify_stats(const uint8_t* pass, const uint16_t* dist, const uint32_t*
  * next (Sec. 4.2 / 6.1: alignment proceeds while the Filter Bitmask
  * Generator moves on, with a double-buffered bitmask between them).  The
  * filter steps run on `stream`, the distances on `align_stream` (NULL: a
- * stream created for the call).
+ * stream created for the call at the device's lowest priority; a caller's
+ * own align_stream is best given a lower priority than `stream`).
  *   bank, idx, ref2bit   the bank, the seed table (grim_seed_index_build)
  *                        and the 2-bit reference, of the same reference.
  *   reads, read_offsets, n_reads (< 2^32), E   as for grim_filter.
@@ -562,8 +563,10 @@ int grim_verify_stats(const uint8_t* pass, const uint16_t* dist, const uint32_t*
  *   *n_loc               host: the number of passing locations.
  * Returns GRIM_EOVERFLOW when n_loc > capacity (the first `capacity` are
  * written).  Synchronises both streams; working memory (library pool): two
- * candidate slots sized to the largest batch (5 bytes per candidate each),
- * plus the scratch of the steps it calls.
+ * candidate slots sized to the largest batch (5 bytes per candidate each:
+ * 1.25 x the most candidates per read seen by earlier grim_seed_candidates
+ * calls with `idx`, at least 512 per read; a batch needing more grows its
+ * slot and is redone), plus the scratch of the steps it calls.
  */
 int grim_map(const grim_bank* bank, const grim_seed_index* idx, const uint8_t* ref2bit, const uint8_t* reads,
              const int64_t* read_offsets, int64_t n_reads, const uint16_t* E, int cap, int64_t batch_reads,

@@ -125,6 +125,11 @@ int launch_scan(const grim_bank* bank, const uint8_t* reads, const int64_t* read
                 uint16_t* pair_sum, int64_t cap, int64_t* n_pairs, uint32_t* read_pass, void* scratch,
                 cudaStream_t stream);
 
+// Candidates that n_reads reads are expected to need, from the most per
+// read that grim_seed_candidates has produced with this index (0 before
+// its first call).
+int64_t seed_candidates_hint(const grim_seed_index* idx, int64_t n_reads);
+
 // Device address and size of the fixed scratch of grim_scan_noalloc
 // (looked up once per device, with that device current).
 int scan_noalloc_scratch(void** ptr, size_t* bytes);

@@ -55,7 +55,11 @@ int grim_map(const grim_bank* bank, const grim_seed_index* idx, const uint8_t* r
     bool own_sa = false;
     cudaError_t e = cudaSuccess;
     if (!sa) {
-        e = cudaStreamCreateWithFlags(&sa, cudaStreamNonBlocking);
+        // the aligner's own stream at the lowest priority: the filter's
+        // kernels go first when both streams have work
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sa, cudaStreamNonBlocking, least);
         if (e != cudaSuccess) {
             grim::set_last_cuda_error(e);
             return GRIM_ECUDA;
@@ -63,9 +67,14 @@ int grim_map(const grim_bank* bank, const grim_seed_index* idx, const uint8_t* r
         own_sa = true;
     }
     const int64_t max_nb = n_reads < batch_reads ? n_reads : batch_reads;
+    // candidate room per slot: what earlier calls with this index needed
+    // (and a quarter more), else 512 per read; a batch that needs more grows
+    // the slot and is redone
+    const int64_t hint = grim::seed_candidates_hint(idx, max_nb);
+    const int64_t slot_cap = hint + hint / 4 > max_nb * 512 ? hint + hint / 4 : max_nb * 512;
     grim::Slot slot[2];
     for (int i = 0; i < 2 && e == cudaSuccess; i++) {
-        slot[i].cap = max_nb * 512;
+        slot[i].cap = slot_cap;
         e = grim::scratch_alloc((void**)&slot[i].cand, (size_t)slot[i].cap * 4, sf);
         if (e == cudaSuccess) e = grim::scratch_alloc((void**)&slot[i].pass, (size_t)slot[i].cap, sf);
         if (e == cudaSuccess) e = grim::scratch_alloc((void**)&slot[i].co, (size_t)(max_nb + 1) * 8, sf);

@@ -30,9 +30,17 @@ struct grim_seed_index {
     int device;
     uint32_t* offsets;    // device, 4^k + 1 entries
     uint32_t* positions;  // device, len - k + 1 entries
+    // the most candidates per read (x 16, rounded up) that a call has
+    // produced: a sizing hint for callers that allocate per batch
+    mutable std::atomic<int64_t> per_read_x16{0};
 };
 
 namespace grim {
+
+int64_t seed_candidates_hint(const grim_seed_index* idx, int64_t n_reads) {
+    return idx->per_read_x16.load() * n_reads / 16;
+}
+
 namespace {
 
 // ------------------------------------------------------------ prefix sums
@@ -333,6 +341,65 @@ __device__ __forceinline__ void radix_sort(uint32_t* A, uint32_t* B, I n, int pa
     }
 }
 
+constexpr int kBucketBits = 10;  // the shared-memory sort's buckets: the keys' top 10 bits
+constexpr int kBuckets = 1 << kBucketBits;
+constexpr int kMaxBucket = 256;  // a fuller bucket hands the votes to the radix sort
+
+// Ascending sort of the shared-memory keys A[0..n) (padded layout), all
+// below 2^key_bits, into A, with B as the second buffer: the keys go to
+// kBuckets buckets by their top bits (one counting pass, one scatter with
+// shared atomics), then every key takes its final place in its bucket by
+// counting the bucket's keys below it, ties broken by position.  The order
+// of equal keys is immaterial here (only the sorted values and their run
+// lengths are used).  Returns false, with A unchanged, when a bucket holds
+// more than kMaxBucket keys.  cnt: 2 * kBuckets words.
+__device__ bool bucket_sort_smem(uint32_t* A, uint32_t* B, int n, int key_bits, uint32_t* cnt, uint32_t* ws32) {
+    constexpr int kPer = kBuckets / kDedupThreads;  // buckets per thread
+    const int t = threadIdx.x;
+    const int shift = key_bits > kBucketBits ? key_bits - kBucketBits : 0;
+    uint32_t* start = cnt;              // first slot of each bucket
+    uint32_t* cursor = cnt + kBuckets;  // counts, then scatter cursors, then bucket ends
+    for (int b = t; b < kBuckets; b += kDedupThreads) cursor[b] = 0;
+    __syncthreads();
+    for (int i = t; i < n; i += kDedupThreads) atomicAdd(&cursor[A[rx_at<true>(i)] >> shift], 1u);
+    __syncthreads();
+    uint32_t c[kPer], sum = 0, mx = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        c[k] = cursor[kPer * t + k];
+        sum += c[k];
+        mx = c[k] > mx ? c[k] : mx;
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan<uint32_t>(sum, ws32, &tot);
+    if (__syncthreads_or(mx > (uint32_t)kMaxBucket)) return false;
+#pragma unroll
+    for (int k = 0; k < kPer; k++) {
+        start[kPer * t + k] = run;
+        cursor[kPer * t + k] = run;
+        run += c[k];
+    }
+    __syncthreads();
+    for (int i = t; i < n; i += kDedupThreads) {
+        const uint32_t key = A[rx_at<true>(i)];
+        B[rx_at<true>((int)atomicAdd(&cursor[key >> shift], 1u))] = key;
+    }
+    __syncthreads();
+    for (int i = t; i < n; i += kDedupThreads) {
+        const uint32_t key = B[rx_at<true>(i)];
+        const uint32_t bk = key >> shift;
+        const int s0 = (int)start[bk], s1 = (int)cursor[bk];
+        int rank = s0;
+        for (int j = s0; j < s1; j++) {
+            const uint32_t o = B[rx_at<true>(j)];
+            rank += (o < key) | ((o == key) & (j < i));
+        }
+        A[rx_at<true>(rank)] = key;
+    }
+    __syncthreads();
+    return true;
+}
+
 // Votes of run j of the sorted votes: starts st[0..u), n votes in all.
 template <typename I>
 __device__ __forceinline__ uint32_t run_votes(const uint32_t* st, I u, I n, I j) {
@@ -355,10 +422,12 @@ __device__ int64_t count_votes_at_least(const uint32_t* st, I u, I n, uint32_t v
 // indices) reads A through the padded layout; the other case is global
 // memory throughout.
 template <bool SMEM, typename I>
-__device__ __forceinline__ int64_t dedupe_read(uint32_t* A, uint32_t* B, I n, int cap, int passes, uint32_t* cnt,
+__device__ __forceinline__ int64_t dedupe_read(uint32_t* A, uint32_t* B, I n, int cap, int passes, int bits,
+                                               uint32_t* cnt,
                                                uint32_t* st, uint32_t* out, uint32_t* ws32, int64_t* ws,
                                                unsigned int* max_votes) {
-    radix_sort<SMEM, I>(A, B, n, passes, cnt, ws32);
+    if (!SMEM || !bucket_sort_smem(A, B, (int)n, bits, cnt, ws32))
+        radix_sort<SMEM, I>(A, B, n, passes, cnt, ws32);
     // run starts -> st[0..u), kDedupItems consecutive votes per thread
     I u = 0;
     for (I c0 = 0; c0 < n; c0 += (I)kDedupChunk) {
@@ -431,13 +500,15 @@ __device__ __forceinline__ int64_t dedupe_read(uint32_t* A, uint32_t* B, I n, in
 
 // One CTA per read of the batch: its votes sorted, runs found, the cap
 // applied and the kept bins (ascending) written to H[hit_off[r] - h0 ...],
-// their number to kept[r].  S: scratch of 8 bytes per vote, used as 2n u32:
-// run starts from the front; reads too long for shared memory also use the
-// back half as the sort's second buffer and build their list after the
-// starts before copying it to H.  `passes`: radix digits covering every bin
-// id (even).
+// their number to kept[r].  Reads of up to kDedupSmem votes work in shared
+// memory (bucket sort, else radix sort; run starts in the sort's second
+// buffer).  Longer reads use S, scratch of 8 bytes per vote, as 2n u32: run
+// starts from the front, the back half as the radix sort's second buffer,
+// then their list after the starts before it is copied to H.  `passes`:
+// radix digits covering every bin id (even); `bits`: bits of the largest bin id.
 __global__ void __launch_bounds__(kDedupThreads)
-seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, int passes, uint32_t* __restrict__ H,
+seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, int passes, int bits,
+                   uint32_t* __restrict__ H,
                    unsigned long long* __restrict__ S, int64_t* __restrict__ kept) {
     extern __shared__ uint32_t dedupe_smem[];
     __shared__ int64_t ws[32];
@@ -458,12 +529,13 @@ seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, int
         const int ni = (int)n;
         for (int i = threadIdx.x; i < ni; i += blockDim.x) A_s[rx_at<true>(i)] = H[base + i];
         __syncthreads();
-        n_keep = dedupe_read<true, int>(A_s, B_s, ni, cap, passes, cnt, st, H + base, ws32, ws, &max_votes);
+        // the run starts go to B_s, free once A_s is sorted
+        n_keep = dedupe_read<true, int>(A_s, B_s, ni, cap, passes, bits, cnt, B_s, H + base, ws32, ws, &max_votes);
     } else {
         uint32_t* cnt = dedupe_smem + 2 * kDedupPadded;
         // the list is built after the starts (st + n: the sort's buffer, free by then)
         uint32_t* list = st + n;
-        n_keep = dedupe_read<false, int64_t>(H + base, st + n, n, cap, passes, cnt, st, list, ws32, ws, &max_votes);
+        n_keep = dedupe_read<false, int64_t>(H + base, st + n, n, cap, passes, bits, cnt, st, list, ws32, ws, &max_votes);
         __syncthreads();
         for (int64_t j = threadIdx.x; j < n_keep; j += blockDim.x) H[base + j] = list[j];
     }
@@ -785,7 +857,7 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
                                                              read_offsets + r0, nb, hit_off + r0, h0,
                                                              (uint32_t)bin_len, (uint32_t)(n_bins - 1), H);
         grim::seed_dedupe_kernel<<<grim::fault_grid((unsigned)nb), grim::kDedupThreads, grim::kDedupSmemBytes, s>>>(
-            hit_off + r0, h0, cap, passes, H, S, kept);
+            hit_off + r0, h0, cap, passes, bits, H, S, kept);
         e = cudaGetLastError();
         // offsets continue from the previous batch's total in cand_offsets[r0]
         if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(kept, cand_offsets + r0, nb, 0, s, cand_offsets + r0);
@@ -811,6 +883,10 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
     }
     if (rc != GRIM_OK) return rc;
     *n_cands = total;
+    const int64_t x16 = (total * 16 + n_reads - 1) / n_reads;
+    int64_t seen = idx->per_read_x16.load();
+    while (x16 > seen && !idx->per_read_x16.compare_exchange_weak(seen, x16)) {
+    }
     return total > capacity ? GRIM_EOVERFLOW : GRIM_OK;
 }
 

@@ -119,6 +119,29 @@ def test_reads_beyond_shared_memory_sort(oracle):
     idx.free()
 
 
+def test_crowded_bin_takes_the_radix_sort(oracle):
+    """A 600-base poly-A stretch: a poly-A read's 8 seeds each hit ~590
+    positions in two or three bins, so one bin collects several hundred of
+    the read's ~4,700 votes.  Reads of that kind (one with 3 seeds, ~1,770
+    votes, within shared memory) are sorted by the radix sort instead of the
+    bucket sort; the lists must still match the oracle's."""
+    rng = np.random.default_rng(43)
+    n = 200_000
+    codes = synth.ref_iid(n, 43)
+    codes[50_000:50_600] = 0
+    reads = [np.zeros(36, np.uint8), np.zeros(100, np.uint8), rng.integers(0, 4, 100).astype(np.uint8),
+             codes[120_000:120_100].copy()]
+    bases = np.concatenate(reads)
+    off = np.concatenate([[0], np.cumsum([len(x) for x in reads])]).astype(np.int64)
+    n_bins = -(-n // 256)
+    idx = grim.grim_seed_index_build(dev(synth.pack2bit(codes)), n, 12)
+    for cap in (2, 10_000):
+        cb, co = grim.grim_seed_candidates(idx, dev(bases), dev(off), 256, n_bins, cap)
+        ocb, oco = oracle.seed_candidates(codes, 12, bases, off, 256, n_bins, cap)
+        assert np.array_equal(host(co, np.int64), oco) and np.array_equal(host(cb, np.uint32), ocb)
+    idx.free()
+
+
 def test_overflow_is_reported_then_retried(oracle):
     n = 200_000
     codes = synth.ref_with_repeats(n, 51, 0.3, n_fam=10, fam_min=100, fam_max=2000)
