@@ -58,8 +58,15 @@ SUMMARY_KEY = {"plain": "1_plain_1Mbp", "gather": "2_gather_100Mbp", "fullscan":
 # ncu capture, valid only for the kernel source it was taken on:
 # {source hash: {form: {"bytes": per launch, "reads": reads per launch}}}
 TRAFFIC_BY_SOURCE: dict[str, dict] = {
-    # gather_kernel<5,8>, 1M reads, 74.8M checks: 660.20 MB read + 74.78 MB written
-    "0b92bfcdafdb14db": {"gather": {"bytes": 734_982_656, "reads": 1_000_000}},
+    "6a81e5e59a6342ab": {
+        # gather_kernel<5,4,DEEP>, one 262,144-read batch of the 3.1 Gbp dispatcher
+        # workload, 438,575,706 checks: 54,623,412,480 B read + 445,977,600 B written
+        "mixed": {"bytes": 55_069_390_080, "reads": 262_144, "checks": 438_575_706},
+        # gather_kernel<5,8>, 100 Mbp, 1M reads, 74.8M checks: 663,338,752 B read + 71,910,656 B written
+        "gather": {"bytes": 735_249_408, "reads": 1_000_000},
+        # gather_kernel<5,8>, 1 Mbp, 10,000 reads, 320,000 checks: 3,017,216 B read, the output stays in L2
+        "plain": {"bytes": 3_017_216, "reads": 10_000},
+    },
 }
 
 
@@ -651,7 +658,13 @@ def run_mixed(args, ctx, primary, peaks):
         scanned.append(n_sc)
 
     ms, clk = ctx.timed(call, steps, warmup)
-    launches = -(-w.n_reads // 262_144)
+    # the dispatcher's kernels per step: the batch-bounds gather, one launch
+    # per run of gathered batches (here all of them: one), and per scanned
+    # batch the prep, scan and the two join kernels
+    n_sc = scanned[-1] if scanned else 0
+    sc_batches = -(-n_sc // 262_144)
+    launches = 1 if n_sc < w.n_reads else sc_batches
+    kernels_per_step = 1 + (1 if n_sc < w.n_reads else 0) + 4 * sc_batches
     ms_g, _ = ctx.timed(lambda: grim.grim_filter_batched(bank, *ins, pass_out=pass_d, tune=tune, stream=s),
                         args.sub_steps, 1, clocks=False)
     nb = min(w.n_reads, 65_536)  # the full scan is timed on one batch of reads
@@ -773,7 +786,7 @@ def run_mixed(args, ctx, primary, peaks):
     if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(form, w, args.cpu_seconds)
     bank.free()
-    return finish(out, form, ctx, w, n_checks, ms, steps, roof, launches, clk, bank_info), w
+    return finish(out, form, ctx, w, n_checks, ms, steps, roof, kernels_per_step, clk, bank_info), w
 
 
 def q_sweep(args, ctx):

@@ -325,9 +325,11 @@ int grim_choose_form(const grim_bank* bank, int64_t n_reads, int64_t n_checks, i
  * picks.  A scanned batch's passing pairs are joined back onto its
  * candidates on the device, so both forms give the same bytes.  Gathered
  * batches use the launch shape grim_autotune chose for this bank's q on
- * this device (the defaults before it has run), without graphs.  Reads each
- * batch's candidate count from the device (synchronising `stream` once per
- * batch) and takes the scan's working memory from the library's pool.
+ * this device (the defaults before it has run), without graphs; a run of
+ * consecutive gathered batches is one launch.  Reads every batch's
+ * candidate count from the device up front (synchronising `stream` once,
+ * and once more per scanned batch) and takes the scan's working memory and
+ * a small bounds array from the library's pool.
  * *n_scanned (host, nullable) receives the number of reads that went
  * through the full scan.
  */

@@ -6,6 +6,7 @@
 // per-candidate mask with a device hash join, so both forms give the same
 // bytes.
 #include <mutex>
+#include <vector>
 
 #include "grim_internal.cuh"
 
@@ -27,6 +28,16 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 
 // passing pairs -> open-addressing set of (read << 32 | bin)
+// bounds[i] = cand_offsets[min(i * batch_reads, n_reads)] for i <= n_batches:
+// every batch's first candidate and the end of the last.
+__global__ void batch_bounds_kernel(const int64_t* __restrict__ cand_offsets, int64_t n_reads, int64_t batch_reads,
+                                    int64_t n_batches, int64_t* __restrict__ bounds) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n_batches) return;
+    const int64_t r = i * batch_reads < n_reads ? i * batch_reads : n_reads;
+    bounds[i] = cand_offsets[r];
+}
+
 __global__ void join_insert_kernel(const uint32_t* __restrict__ pr, const uint32_t* __restrict__ pb, int64_t n,
                                    uint64_t r0, unsigned long long* __restrict__ table, uint64_t mask) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -130,17 +141,46 @@ int grim_filter_auto(const grim_bank* bank, const uint8_t* reads, const int64_t*
     // so a graph per batch would only churn the bank's graph cache)
     grim_tune t = grim::tuned_shape(bank);
     t.use_graph = 0;
-    t.batch_reads = batch_reads;
-    for (int64_t r0 = 0; r0 < n_reads; r0 += batch_reads) {
+    // every batch's candidate count with one copy and one synchronisation
+    const int64_t n_batches = (n_reads + batch_reads - 1) / batch_reads;
+    std::vector<int64_t> bounds((size_t)n_batches + 1);
+    {
+        int64_t* bd = nullptr;
+        GRIM_CUDA_TRY(grim::scratch_alloc((void**)&bd, (size_t)(n_batches + 1) * 8, s));
+        const int64_t nb = (n_batches + 1 + 255) / 256;
+        grim::batch_bounds_kernel<<<grim::fault_grid((unsigned)nb), 256, 0, s>>>(cand_offsets, n_reads, batch_reads,
+                                                                                n_batches, bd);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bounds.data(), bd, (size_t)(n_batches + 1) * 8, cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(bd, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            grim::set_last_cuda_error(e);
+            return GRIM_ECUDA;
+        }
+    }
+    // consecutive gathered batches run as one persistent launch (no tail and
+    // no host round trip between them); scanned batches one by one
+    int64_t run0 = -1;  // first read of the pending run of gathered batches
+    auto flush = [&](int64_t r_end) -> int {
+        if (run0 < 0) return GRIM_OK;
+        const int64_t n = r_end - run0;
+        t.batch_reads = n;
+        const int r = grim_filter_batched(bank, reads, read_offsets + run0, n, cand_bins, cand_offsets + run0,
+                                          E + run0, pass, nullptr, &t, stream);
+        run0 = -1;
+        return r;
+    };
+    for (int64_t b = 0; b < n_batches; b++) {
+        const int64_t r0 = b * batch_reads;
         const int64_t n = (n_reads - r0) < batch_reads ? (n_reads - r0) : batch_reads;
-        int64_t bounds[2];
-        GRIM_CUDA_TRY(cudaMemcpyAsync(&bounds[0], cand_offsets + r0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        GRIM_CUDA_TRY(cudaMemcpyAsync(&bounds[1], cand_offsets + r0 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        GRIM_CUDA_TRY(cudaStreamSynchronize(s));
         int form = GRIM_FORM_GATHER;
-        grim_choose_form(bank, n, bounds[1] - bounds[0], &form);
+        grim_choose_form(bank, n, bounds[b + 1] - bounds[b], &form);
         bool done = false;
         if (form == GRIM_FORM_SCAN) {
+            rc = flush(r0);
+            if (rc != GRIM_OK) return rc;
             // scan the batch over every bin; join its pairs back onto the candidates
             const int64_t cap = 1 << 24;
             size_t table_n = 1;
@@ -163,11 +203,12 @@ int grim_filter_auto(const grim_bank* bank, const uint8_t* reads, const int64_t*
                 cudaMemsetAsync(table, 0xFF, table_n * 8, s);
                 const int64_t ib = (np + grim::kJoinThreads - 1) / grim::kJoinThreads;
                 if (np > 0)
-                    grim::join_insert_kernel<<<grim::fault_grid((unsigned)(ib < 65535 ? ib : 65535)), grim::kJoinThreads, 0, s>>>(
-                        pr, pb, np, 0, table, table_n - 1);
+                    grim::join_insert_kernel<<<grim::fault_grid((unsigned)(ib < 65535 ? ib : 65535)),
+                                               grim::kJoinThreads, 0, s>>>(pr, pb, np, 0, table, table_n - 1);
                 const int64_t lb = (n * 32 + grim::kJoinThreads - 1) / grim::kJoinThreads;
-                grim::join_lookup_kernel<<<grim::fault_grid((unsigned)(lb < 65535 ? lb : 65535)), grim::kJoinThreads, 0, s>>>(
-                    cand_offsets + r0, n, 0, cand_bins, bank->n_bins, table, table_n - 1, pass, bank->status);
+                grim::join_lookup_kernel<<<grim::fault_grid((unsigned)(lb < 65535 ? lb : 65535)), grim::kJoinThreads,
+                                           0, s>>>(cand_offsets + r0, n, 0, cand_bins, bank->n_bins, table,
+                                                   table_n - 1, pass, bank->status);
                 cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess) {
                     grim::set_last_cuda_error(e);
@@ -179,12 +220,11 @@ int grim_filter_auto(const grim_bank* bank, const uint8_t* reads, const int64_t*
             cudaFreeAsync(mem, s);
             if (rc != GRIM_OK) return rc;
         }
-        if (!done) {
-            rc = grim_filter_batched(bank, reads, read_offsets + r0, n, cand_bins, cand_offsets + r0, E + r0, pass,
-                                     nullptr, &t, stream);
-            if (rc != GRIM_OK) return rc;
-        }
+        // a gathered batch (or a scan whose pairs overflowed) joins the run
+        if (!done && run0 < 0) run0 = r0;
     }
+    rc = flush(n_reads);
+    if (rc != GRIM_OK) return rc;
     return GRIM_OK;
 }
 

@@ -18,15 +18,18 @@ def _lib():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
 
 
-def dense_workload(n_reads=10_000, ref_len=256_000, dense_frac=1.0, seed=4):
-    """Every bin as a candidate for the first dense_frac of the reads, 8 for the rest."""
+def dense_workload(n_reads=10_000, ref_len=256_000, dense_frac=1.0, seed=4, dense_of=None):
+    """Every bin as a candidate for the first dense_frac of the reads (or
+    the reads r with dense_of(r)), 8 for the rest."""
     rng = np.random.default_rng(seed)
     codes = synth.ref_with_repeats(ref_len, seed, 0.3, n_fam=10, fam_min=100, fam_max=2000)
     off = synth.read_offsets(n_reads, 100, 100, seed)
     bases, starts = synth.reads(codes, off, seed, 0.03, 0.01)
     nb = -(-ref_len // 256)
     n_dense = int(n_reads * dense_frac)
-    lists = [np.arange(nb, dtype=np.uint32) if r < n_dense else
+    if dense_of is None:
+        dense_of = lambda r: r < n_dense  # noqa: E731
+    lists = [np.arange(nb, dtype=np.uint32) if dense_of(r) else
              np.sort(rng.choice(nb, 8, replace=False)).astype(np.uint32) for r in range(n_reads)]
     co = np.concatenate([[0], np.cumsum([len(x) for x in lists])]).astype(np.int64)
     return codes, bases, off, np.concatenate(lists), co, np.full(n_reads, 5, np.uint16)
@@ -61,6 +64,17 @@ def test_dense_candidates_take_the_scan_form(oracle):
 
 def test_mixed_batches_use_both_forms(oracle):
     codes, bases, off, cb, co, E = dense_workload(n_reads=8_000, ref_len=512_000, dense_frac=0.5, seed=6)
+    scanned, _, _ = run_auto(oracle, codes, bases, off, cb, co, E, batch_reads=2000)
+    assert scanned == 4000
+
+
+def test_alternating_batches_run_gathers_between_scans(oracle):
+    """Batches of 2,000 reads alternate sparse (gathered) and dense (scanned),
+    two sparse batches in a row once, and the last batch is ragged: the
+    gathered batches between two scans run as one launch, and every pass byte
+    still equals the oracle's."""
+    dense = lambda r: (r // 2000) in (1, 4)  # noqa: E731
+    codes, bases, off, cb, co, E = dense_workload(n_reads=11_000, ref_len=512_000, seed=8, dense_of=dense)
     scanned, _, _ = run_auto(oracle, codes, bases, off, cb, co, E, batch_reads=2000)
     assert scanned == 4000
 

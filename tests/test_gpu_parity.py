@@ -92,11 +92,13 @@ def test_filter_plain_gather_workload_full(oracle):
     bank.free()
 
 
-def test_filter_bank_beyond_l2_takes_the_deep_form(oracle):
-    """A 200 Mbp bank (100 MB at q=5, beyond the L2) is read by the gather
-    form that keeps three steps of rows in flight; every pass byte and sum
-    against the oracle, each candidate's bitvector rebuilt from the reference."""
-    w = synth.gather_iid(ref_len=200_000_000, n_reads=20_000, k=32)
+@pytest.mark.parametrize("q,ref_len", [(5, 200_000_000), (6, 60_000_000)])
+def test_filter_bank_beyond_l2_takes_the_deep_form(oracle, q, ref_len):
+    """Banks beyond the L2 (200 Mbp at q=5: 100 MB, read by the gather form
+    that keeps three steps of rows in flight; 60 Mbp at q=6: 120 MB); every
+    pass byte and sum against the oracle, each candidate's bitvector rebuilt
+    from the reference."""
+    w = synth.gather_iid(ref_len=ref_len, n_reads=20_000, k=32, q=q)
     bank = gpu_bank(w.ref2bit, w.ref_len, w.q, w.bin_len, w.overlap)
     assert bank.n_bins * bank.row_words * 4 > 96e6
     p, s, st, flags = run_filter(bank, w.bases, w.read_offsets, w.cand_bins, w.cand_offsets, w.E)
