@@ -838,9 +838,12 @@ def summary(m):
     peak_src = r.get("summary_peak", r.get("peak_source", ""))
     cpu = m.get("cpu_baseline") or {}
     clk = m.get("clocks") or {}
+    roof = {"bound": r.get("bound"), "frac": sig(frac, 3),
+            "peak": sig(r.get("l2_peak") if "summary_frac" in r else r["peak"]), "peak_source": peak_src.split(" (")[0]}
+    if r.get("bound") == "hbm":
+        roof["hbm_frac"] = sig(r["frac"], 3)  # algorithmic bytes against HBM, also for L2-resident banks
     return {"value": sig(m["value"]), "ms_per_step": sig(m["ms_per_step"]), "reads_per_s": sig(m["reads_per_s"]),
-            "roofline": {"frac": sig(frac, 3), "peak": sig(r.get("l2_peak") if "summary_frac" in r else r["peak"]),
-                         "peak_source": peak_src.split(" (")[0], "hbm_frac": sig(r["frac"], 3)},
+            "roofline": roof,
             "cpu_baseline": sig(cpu.get("value")),
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons")}}
 
