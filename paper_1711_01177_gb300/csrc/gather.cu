@@ -123,6 +123,11 @@ struct Stream {
     static constexpr int kBufs =
         (Q <= 5 && !DEEP && kWinSteps >= 2) ? 2 : (kWinSteps >= 4 ? 4 : kWinSteps);
     static constexpr int kAhead = kBufs - 1;                      // steps a row is requested early
+    // q = 6: rows are also prefetched into L2 this many steps ahead (within
+    // the two id windows held), which covers more of the DRAM latency than
+    // the register buffers alone
+    static constexpr int kPrefetch = Q >= 6 ? 8 : 0;
+    static_assert(kPrefetch < kWinSteps, "a prefetched id must lie in the next window at most");
     static_assert(kWinSteps % kBufs == 0, "buffer rotation must repeat every window");
     uint32_t win_cur, win_next;  // candidate ids c = base + lane, base + 32 + lane
     uint4 r[kBufs][G::kVPL];
@@ -130,6 +135,20 @@ struct Stream {
 
 __device__ __forceinline__ uint32_t window_id(const uint32_t* __restrict__ cands, int c, int n) {
     return c < n ? __ldg(cands + c) : 0xFFFFFFFFu;
+}
+
+// Asks the L2 for the 128-byte lines of a row that will be scored later
+// (no register holds it meanwhile): lane s of the row group covers the
+// lines holding its vectors when s is a multiple of 8 (8 x 16 bytes).
+template <int Q>
+__device__ __forceinline__ void prefetch_row(uint32_t id, const uint32_t* __restrict__ bank, uint32_t n_bins32,
+                                             int s) {
+    using G = GatherGeo<Q>;
+    if ((s & 7) != 0) return;
+    const uint32_t b = id < n_bins32 ? id : 0u;
+    const uint4* row = reinterpret_cast<const uint4*>(bank) + (size_t)b * G::kRowVecs + s;
+#pragma unroll
+    for (int u = 0; u < G::kVPL; u++) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + u * G::kLPB));
 }
 
 template <int Q>
@@ -225,6 +244,13 @@ __device__ __forceinline__ void score_read(Stream<Q, DEEP>& st, const uint4* __r
                     const uint32_t src = ahead < S::kWinSteps ? st.win_cur : st.win_next;
                     const uint32_t id = __shfl_sync(kFull, src, idx);
                     fetch_row<Q>(st.r[(t + S::kAhead) % S::kBufs], id, bank, n_bins32, s);
+                }
+                if constexpr (S::kPrefetch > 0) {
+                    const int ahead = t + S::kPrefetch;
+                    const int idx = (ahead % S::kWinSteps) * G::kBPS + g;
+                    const uint32_t src = ahead < S::kWinSteps ? st.win_cur : st.win_next;
+                    const uint32_t id = __shfl_sync(kFull, src, idx);
+                    prefetch_row<Q>(id, bank, n_bins32, s);
                 }
                 // score this step's rows
                 const uint4 (&v)[G::kVPL] = st.r[t % S::kBufs];
