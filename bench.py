@@ -56,16 +56,20 @@ SUMMARY_KEY = {"plain": "1_plain_1Mbp", "gather": "2_gather_100Mbp", "fullscan":
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one gather launch, from an
 # ncu capture, valid only for the kernel source it was taken on:
-# {source hash: {form: {"bytes": per launch, "reads": reads per launch}}}
+# {source hash: {form: {"bytes": per launch, "reads": reads per launch,
+#                       "checks": checks of the launch where it is scaled by checks}}}
 TRAFFIC_BY_SOURCE: dict[str, dict] = {
-    "6a81e5e59a6342ab": {
-        # gather_kernel<5,4,DEEP>, one 262,144-read batch of the 3.1 Gbp dispatcher
-        # workload, 438,575,706 checks: 54,623,412,480 B read + 445,977,600 B written
-        "mixed": {"bytes": 55_069_390_080, "reads": 262_144, "checks": 438_575_706},
-        # gather_kernel<5,8>, 100 Mbp, 1M reads, 74.8M checks: 663,338,752 B read + 71,910,656 B written
-        "gather": {"bytes": 735_249_408, "reads": 1_000_000},
-        # gather_kernel<5,8>, 1 Mbp, 10,000 reads, 320,000 checks: 3,017,216 B read, the output stays in L2
-        "plain": {"bytes": 3_017_216, "reads": 10_000},
+    "07abad9295d617a2": {
+        # gather_kernel<5,8,DEEP>, one 262,144-read batch of the 3.1 Gbp dispatcher
+        # workload, 438,575,706 checks: 54,666,395,904 B read + 439,968,256 B written
+        "mixed": {"bytes": 55_106_364_160, "reads": 262_144, "checks": 438_575_706},
+        # gather_kernel<5,8>, 100 Mbp, 1M reads, 74.8M checks: 663,430,656 B read + 72,020,736 B written
+        "gather": {"bytes": 735_451_392, "reads": 1_000_000},
+        # gather_kernel<5,8>, 1 Mbp, 10,000 reads, 320,000 checks: 3,017,472 B read, the output stays in L2
+        "plain": {"bytes": 3_017_472, "reads": 10_000},
+        # gather_kernel<6,8>, one 262,144-read batch of the q=6 workload, 153,942,833 checks:
+        # 47,242,048,768 B read + 164,398,080 B written
+        "batched": {"bytes": 47_406_446_848, "reads": 262_144, "checks": 153_942_833},
     },
 }
 
@@ -415,9 +419,28 @@ def measure_peaks(ctx):
         rates.append(u / (ms / 1e3))
     out["mxf4_tmem_a_tflops_sustained"] = float(np.median(rates[len(rates) // 2:])) / 1e12
     out["int8_mma_sync_tops"] = best(grim.GRIM_PEAK_INT8_MMA_SYNC, 4000) / 1e12
+    # this box's copy bandwidth, taken the way the HBM figure above was
+    # (b.copy_(a) over 1 Gi bf16 elements, read + write bytes, best of 10):
+    # context for the spread of DRAM-bound lines between boxes; the
+    # roofline keeps hbm_gbs
+    import torch
+    a = torch.empty(1 << 30, dtype=torch.bfloat16, device="cuda")
+    b = torch.empty_like(a)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bw = []
+    with torch.cuda.stream(ctx.stream):
+        for _ in range(10):
+            e0.record(ctx.stream)
+            b.copy_(a)
+            e1.record(ctx.stream)
+            ctx.stream.synchronize()
+            bw.append(4.0 * a.numel() / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del a, b
+    out["hbm_copy_gbs_this_box"] = max(bw)
     out["how"] = ("grim_peak: L2 = 32 MiB read 40x with ld.global.cg.v4 on every SM; tensor = one CTA per SM "
                   "issuing dense tcgen05.mma 128x256 (e4m3 K=32 / mxf4 e2m1 K=64, unit scales) back to back, "
-                  "operands in shared (or A in tensor) memory; best of 3 launches; int8 = mma.sync m16n8k32 s8")
+                  "operands in shared (or A in tensor) memory; best of 3 launches; int8 = mma.sync m16n8k32 s8; "
+                  "hbm_copy_gbs_this_box = torch copy on this box")
     return {k: (sig(v) if isinstance(v, float) else v) for k, v in out.items()}
 
 
@@ -540,6 +563,14 @@ def run_batched(args, ctx, primary, peaks):
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
             "peak_source": hbm_src, "kernel": f"gather_kernel<{w.q},{int(tune.warps_per_cta)}>",
             "algorithmic_bytes_per_launch": alg // launches, "launches_per_step": launches, "avg_step_ms": avg}
+    sha = source_sha()
+    rec = TRAFFIC_BY_SOURCE.get(sha, {}).get(form, {})
+    roof["source_sha"] = sha
+    if rec.get("reads"):
+        # measured on one batch launch; scaled to the average launch by checks
+        roof["traffic"] = int(rec["bytes"] * (w.n_checks / launches) / rec["checks"])
+        roof["traffic_note"] = (f"ncu DRAM bytes of one {rec['reads']}-read batch launch ({rec['checks']} checks), "
+                                f"scaled to the average launch by its checks")
     out = {"form": form, "tune": tune.as_dict(), "pass_rate": float(pass_d.float().mean().item()),
            "workload_stats": {"checks_per_gpu_step": w.n_checks,
                               "cands_per_read_mean": round(w.n_checks / w.n_reads, 2)},
@@ -684,8 +715,12 @@ def run_mixed(args, ctx, primary, peaks):
     hbm, hbm_src = load_hbm_peak()
     ach = alg / (avg / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-            "peak_source": hbm_src, "kernel": "dispatcher -> gather_kernel<5,8>", "algorithmic_bytes_per_launch":
+            "peak_source": hbm_src, "kernel": "dispatcher -> gather_kernel<5,*,DEEP>", "algorithmic_bytes_per_launch":
             alg // launches, "launches_per_step": launches, "avg_step_ms": avg}
+    if peaks.get("hbm_copy_gbs_this_box"):
+        # context: boxes differ by several percent on this DRAM-bound line
+        roof["this_box_copy_gbs"] = peaks["hbm_copy_gbs_this_box"]
+        roof["frac_of_this_box_copy"] = ach / peaks["hbm_copy_gbs_this_box"]
     sha = source_sha()
     rec = TRAFFIC_BY_SOURCE.get(sha, {}).get(form, {})
     roof["source_sha"] = sha
@@ -742,7 +777,8 @@ def run_mixed(args, ctx, primary, peaks):
         del cb_d, co_d
         torch.cuda.empty_cache()
         h_in = [ctx.pin(w.bases), ctx.pin(w.read_offsets), ctx.pin(w.E)]
-        h_out = torch.empty(n_checks, dtype=torch.uint8).pin_memory()
+        bits_d = torch.empty((n_checks + 31) // 32, dtype=torch.int32, device="cuda")
+        h_out = torch.empty(bits_d.numel(), dtype=torch.int32).pin_memory()
 
         def e2e_step():
             for h, d in zip(h_in, (reads_d, offs_d, E_d)):
@@ -750,15 +786,18 @@ def run_mixed(args, ctx, primary, peaks):
             cb2, co2 = grim.grim_seed_candidates(idx, reads_d, offs_d, w.bin_len, w.n_bins, w.meta["cap"],
                                                  capacity=n_checks, stream=s)
             grim.grim_filter_auto(bank, reads_d, offs_d, cb2, co2, E_d, pass_out=pass_d, stream=s)
-            h_out.copy_(pass_d, non_blocking=True)
+            # the filter bitmask (Sec. 3.3): one bit per (read, candidate bin)
+            grim.grim_pack_mask(pass_d, bits_d, stream=s)
+            h_out.copy_(bits_d, non_blocking=True)
 
         e2e_ms, _ = ctx.timed(e2e_step, steps, warmup, clocks=False)
         out["e2e"] = {"value": n_checks * ctx.world * steps / (ctx.max_over_ranks(sum(e2e_ms)) / 1e3), "unit": UNIT,
                       "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in h_in),
-                      "d2h_bytes_per_step": h_out.numel(),
-                      "includes": "reads copied in, seed candidates on the GPU (synchronising), dispatcher, pass "
-                                  "bytes to host"}
-        del h_in, h_out
+                      "d2h_bytes_per_step": h_out.numel() * h_out.element_size(),
+                      "includes": "reads copied in from pinned memory, seed candidates on the GPU (synchronising), "
+                                  "dispatcher, the pass bitmask (one bit per check, grim_pack_mask) to pinned host "
+                                  "memory"}
+        del h_in, h_out, bits_d
     else:
         del cb_d, co_d
     del pass_d
@@ -769,17 +808,25 @@ def run_mixed(args, ctx, primary, peaks):
         # the filter's stream ahead of the aligner's when both have work
         filt, align = torch.cuda.Stream(priority=-1), torch.cuda.Stream(priority=0)
         cap_loc = int(n_pass * 1.25) + 1024
-        for rep in range(2):
+
+        def map_time(align_stream):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with torch.cuda.stream(filt):
-                mp = grim.grim_map(bank, idx, ref_d, reads_d, offs_d, E_d, cap=w.meta["cap"], batch_reads=1 << 20,
-                                   capacity=cap_loc, stream=filt, align_stream=align)
+                m = grim.grim_map(bank, idx, ref_d, reads_d, offs_d, E_d, cap=w.meta["cap"], batch_reads=1 << 20,
+                                  capacity=cap_loc, stream=filt, align_stream=align_stream)
             torch.cuda.synchronize()
-            map_s = time.perf_counter() - t0
+            return time.perf_counter() - t0, m
+
+        map_time(align)  # warm: slot sizes, pools
+        map_s, mp = map_time(align)
+        # the same batches with the aligner on the filter's stream: no overlap
+        same_s, mp_same = map_time(filt)
+        assert mp_same.n == mp.n
         out["seed_pipeline"].update({"overlapped_s": map_s, "overlapped_reads_per_s": w.n_reads / map_s,
-                                     "serial_sum_s": serial_s, "overlapped_locations": mp.n})
-        del mp
+                                     "serial_sum_s": serial_s, "same_batches_one_stream_s": same_s,
+                                     "overlapped_locations": mp.n})
+        del mp, mp_same
     idx.free()
     del reads_d, offs_d, E_d, ref_d
     torch.cuda.empty_cache()
