@@ -306,6 +306,10 @@ bank_build_lanes_kernel(const uint8_t* __restrict__ ref2bit, int64_t len, int bi
     int64_t unit = (int64_t)blockIdx.x * kLaneWarps + warp;
     if (unit < n_units) stage_warp_tile(ref2bit, nbytes, unit * out_w, wpc, my_stage_s, lane);
     cp_async_commit();
+    // the row sets start zeroed; afterwards every read of them (the rows,
+    // then the staged output) swaps in zeros, so no tile needs a clearing pass
+#pragma unroll
+    for (int i = lane; i < 2 * RW * 8; i += 32) my_sets[i] = make_uint4(0, 0, 0, 0);
     for (int it = 0; unit < n_units; unit += stride, it++) {
         const int64_t c0 = unit * out_w;
         const int buf = it & 1;
@@ -314,8 +318,6 @@ bank_build_lanes_kernel(const uint8_t* __restrict__ ref2bit, int64_t len, int bi
             stage_warp_tile(ref2bit, nbytes, next * out_w, wpc, my_stage_s + 4u * (uint32_t)(stage_words * (buf ^ 1)),
                             lane);
         cp_async_commit();
-#pragma unroll
-        for (int i = lane; i < 2 * RW * 8; i += 32) my_sets[i] = make_uint4(0, 0, 0, 0);
         cp_async_wait<1>();  // this tile's words have landed (the next tile's may not)
         __syncwarp();
 
@@ -350,8 +352,8 @@ bank_build_lanes_kernel(const uint8_t* __restrict__ ref2bit, int64_t len, int bi
         uint32_t v[RW];
 #pragma unroll
         for (int w = 0; w < RW; w++) {
-            const uint32_t pw = myP[32 * w];
-            const uint32_t cw = pw | myR[32 * w];
+            const uint32_t pw = atomicExch(&myP[32 * w], 0u);
+            const uint32_t cw = pw | atomicExch(&myR[32 * w], 0u);
             uint32_t x = cw;
             for (int i = 1; i <= J; i++) x |= __shfl_down_sync(kFull, cw, i);
             v[w] = x | __shfl_down_sync(kFull, pw, J + 1);
@@ -373,10 +375,13 @@ bank_build_lanes_kernel(const uint8_t* __restrict__ ref2bit, int64_t len, int bi
             const int o = (i * 32 + lane) * 16;  // byte offset in the staged rows
             const int r = o / (RW * 4), slot = (o % (RW * 4)) / 16;
             const int c = slot ^ (r & (LG::kChunks - 1));
+            unsigned long long* h = reinterpret_cast<unsigned long long*>(out_s + o);
+            const unsigned long long lo = atomicExch(h, 0ull), hi = atomicExch(h + 1, 0ull);
             if (r < n_rows)
-                reinterpret_cast<uint4*>(bank + (c0 + r) * RW)[c] = *reinterpret_cast<const uint4*>(out_s + o);
+                reinterpret_cast<uint4*>(bank + (c0 + r) * RW)[c] =
+                    make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
         }
-        __syncwarp();  // the row sets are read before the next tile zeroes them
+        __syncwarp();  // the row sets are cleared before the next tile's tokens
     }
     cp_async_wait<0>();
 }
