@@ -735,7 +735,8 @@ def run_mixed(args, ctx, primary, peaks):
                               "candidates": "GPU seed table + grim_seed_candidates (12-mer seeds, cap 10000)"},
            "dispatch": {"choice": "scan" if choice == grim.GRIM_FORM_SCAN else "gather",
                         "reads_scanned_per_step": scanned[-1] if scanned else 0},
-           "gather_form": {"ms_per_step": g, "checks_per_s": n_checks / (g / 1e3), "reads_per_s": w.n_reads / (g / 1e3)},
+           "gather_form": {"ms_per_step": g, "checks_per_s": n_checks / (g / 1e3),
+                           "reads_per_s": w.n_reads / (g / 1e3)},
            "scan_form": {"ms_per_batch": sc, "batch_reads": nb, "checks_per_s_all_bins": nb * w.n_bins / (sc / 1e3),
                          "reads_per_s": nb / (sc / 1e3), "pairs_passing": res.n_pairs,
                          "note": "one batch of reads timed; the dispatcher's choice runs every read"},

@@ -616,8 +616,9 @@ def grim_filter_host(bank: Bank, reads: torch.Tensor, read_offsets: torch.Tensor
         raise ValueError("cand_offsets / E sizes do not match read_offsets")
     if pass_out is None:
         pass_out = torch.empty(cand_bins.numel(), dtype=torch.uint8)
-    _check(load().grim_filter_host(bank.handle, _host_ptr(reads, "reads", 1), _host_ptr(read_offsets, "read_offsets", 8),
-                                   n_reads, _host_ptr(cand_bins, "cand_bins", 4),
+    _check(load().grim_filter_host(bank.handle, _host_ptr(reads, "reads", 1),
+                                   _host_ptr(read_offsets, "read_offsets", 8), n_reads,
+                                   _host_ptr(cand_bins, "cand_bins", 4),
                                    _host_ptr(cand_offsets, "cand_offsets", 8), _host_ptr(E, "E", 2),
                                    _host_ptr(pass_out, "pass", 1), chunk_reads, _stream_ptr(stream)),
            "grim_filter_host")

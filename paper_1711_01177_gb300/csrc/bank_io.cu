@@ -180,8 +180,8 @@ int grim_pack_mask(const uint8_t* pass, int64_t n, uint32_t* bits, void* stream)
     const int64_t words = (n + 31) / 32;
     const int64_t need = (words + 255) / 256;
     const int64_t cap = (int64_t)grim::sm_count() * 16;
-    grim::pack_mask_kernel<<<grim::fault_grid((unsigned)(need < cap ? need : cap)), 256, 0, s>>>(pass, n, ((uintptr_t)pass & 15) == 0,
-                                                                             bits);
+    grim::pack_mask_kernel<<<grim::fault_grid((unsigned)(need < cap ? need : cap)), 256, 0, s>>>(
+            pass, n, ((uintptr_t)pass & 15) == 0, bits);
     GRIM_CUDA_TRY(cudaGetLastError());
     return GRIM_OK;
 }

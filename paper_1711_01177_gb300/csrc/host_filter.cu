@@ -162,8 +162,8 @@ int grim_filter_host(const grim_bank* bank, const uint8_t* reads, const int64_t*
         if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(sf, s.out, 0);  // chunk c - 2's bytes have left
         if (e != cudaSuccess) break;
         const int64_t need = (nr + 1 + 255) / 256;
-        grim::rebase_kernel<<<grim::fault_grid((unsigned)(need < 1024 ? need : 1024)), 256, 0, sf>>>(ro_all + r0, co_all + r0, s.ro,
-                                                                                  s.co, nr + 1, ro0, co0);
+        grim::rebase_kernel<<<grim::fault_grid((unsigned)(need < 1024 ? need : 1024)), 256, 0, sf>>>(
+                ro_all + r0, co_all + r0, s.ro, s.co, nr + 1, ro0, co0);
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
         rc = grim::launch_gather(bank, s.reads, s.ro, nr, s.cb, s.co, E_all + r0, s.pass, nullptr, sf);

@@ -220,13 +220,14 @@ int grim_peak(int kind, int64_t work, double* units, float* ms, void* stream) {
         const bool n128 = kind >= GRIM_PEAK_MXF4_TMEM_A_N128;
         auto launch = [&](int64_t iters) {
             uint32_t* st = (uint32_t*)scratch;
+            const unsigned g = grim::fault_grid(sms);
             switch (mode + (n128 ? 4 : 0)) {
-                case 0: grim::tc_peak_kernel<0, 256><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
-                case 1: grim::tc_peak_kernel<1, 256><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
-                case 2: grim::tc_peak_kernel<2, 256><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
-                case 3: grim::tc_peak_kernel<3, 256><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
-                case 6: grim::tc_peak_kernel<2, 128><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
-                default: grim::tc_peak_kernel<3, 128><<<grim::fault_grid(sms), 128, smem, s>>>(iters, 0x1234u, st); break;
+                case 0: grim::tc_peak_kernel<0, 256><<<g, 128, smem, s>>>(iters, 0x1234u, st); break;
+                case 1: grim::tc_peak_kernel<1, 256><<<g, 128, smem, s>>>(iters, 0x1234u, st); break;
+                case 2: grim::tc_peak_kernel<2, 256><<<g, 128, smem, s>>>(iters, 0x1234u, st); break;
+                case 3: grim::tc_peak_kernel<3, 256><<<g, 128, smem, s>>>(iters, 0x1234u, st); break;
+                case 6: grim::tc_peak_kernel<2, 128><<<g, 128, smem, s>>>(iters, 0x1234u, st); break;
+                default: grim::tc_peak_kernel<3, 128><<<g, 128, smem, s>>>(iters, 0x1234u, st); break;
             }
             return cudaGetLastError();
         };

@@ -130,8 +130,8 @@ int grim_map(const grim_bank* bank, const grim_seed_index* idx, const uint8_t* r
             if (rc == GRIM_OK && r0 > 0) {
                 const int64_t need = (kept + 255) / 256;
                 const int64_t grid = (int64_t)grim::sm_count() * 8;
-                grim::add_base_kernel<<<grim::fault_grid((unsigned)(need < grid ? need : grid)), 256, 0, sa>>>(loc_read + written, kept,
-                                                                                            (uint32_t)r0);
+                grim::add_base_kernel<<<grim::fault_grid((unsigned)(need < grid ? need : grid)), 256, 0, sa>>>(
+                        loc_read + written, kept, (uint32_t)r0);
                 e = cudaGetLastError();
             }
         }

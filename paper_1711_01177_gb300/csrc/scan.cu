@@ -69,6 +69,8 @@ constexpr int kScanThreads = 704;   // 22 warps: TMA, MMA, 4 expand, 16 epilogue
 constexpr int kExpandWarp0 = 2;     // expander warps 2..5, one per TMEM lane quadrant
 constexpr int kEpilogueWarp0 = 6;   // epilogue warps 6..21: four per quadrant, each a quarter of the reads
 constexpr int kEpilogueWarps = 16;
+static_assert(kEpilogueWarp0 == kExpandWarp0 + 4 && kScanThreads == 32 * (kEpilogueWarp0 + kEpilogueWarps),
+              "warp roles: TMA, MMA, four expanders, the epilogue");
 constexpr int kBinTile = 128;       // bins per MMA tile (M, TMEM lanes)
 constexpr int kRowsTile = 256;      // B rows per read tile (N)
 constexpr int kBankStages = 4;
@@ -702,8 +704,8 @@ static int launch_scan_q(const grim_bank* bank, const uint8_t* reads, const int6
         const int64_t need = (n_reads + kPrepWarps - 1) / kPrepWarps;
         const int64_t cap = (int64_t)sm_count() * 16;
         const int64_t blocks = need < cap ? need : cap;
-        scan_prep_kernel<Q><<<grim::fault_grid((unsigned)blocks), kPrepWarps * 32, smem, s>>>(reads, read_offsets, n_reads, E, sc,
-                                                                            bank->status);
+        scan_prep_kernel<Q><<<grim::fault_grid((unsigned)blocks), kPrepWarps * 32, smem, s>>>(
+                reads, read_offsets, n_reads, E, sc, bank->status);
         GRIM_CUDA_TRY(cudaGetLastError());
     }
     {

@@ -535,7 +535,8 @@ seed_dedupe_kernel(const int64_t* __restrict__ hit_off, int64_t h0, int cap, int
         uint32_t* cnt = dedupe_smem + 2 * kDedupPadded;
         // the list is built after the starts (st + n: the sort's buffer, free by then)
         uint32_t* list = st + n;
-        n_keep = dedupe_read<false, int64_t>(H + base, st + n, n, cap, passes, bits, cnt, st, list, ws32, ws, &max_votes);
+        n_keep = dedupe_read<false, int64_t>(H + base, st + n, n, cap, passes, bits, cnt, st, list, ws32, ws,
+                                             &max_votes);
         __syncthreads();
         for (int64_t j = threadIdx.x; j < n_keep; j += blockDim.x) H[base + j] = list[j];
     }
@@ -740,7 +741,8 @@ int grim_seed_index_build(const uint8_t* ref2bit, int64_t len, int k, void* stre
         if (e == cudaSuccess && rc == GRIM_OK)
             e = cudaMemcpyAsync(cursor, idx->offsets, (size_t)nk * 4, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess && rc == GRIM_OK) {
-            grim::seed_index_kernel<true><<<grim::fault_grid(blocks), 256, 0, s>>>(ref2bit, npos, k, cursor, idx->positions);
+            grim::seed_index_kernel<true><<<grim::fault_grid(blocks), 256, 0, s>>>(
+                    ref2bit, npos, k, cursor, idx->positions);
             e = cudaGetLastError();
         }
     }
@@ -800,7 +802,8 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
     GRIM_CUDA_TRY(grim::scratch_alloc((void**)&hit_off, (size_t)(n_reads + 1) * 8, s));
     GRIM_CUDA_TRY(grim::scratch_alloc((void**)&info, 64, s));  // batch bounds
     int rc = GRIM_OK;
-    grim::seed_hits_kernel<<<grim::fault_grid(blocks), threads, 0, s>>>(idx->offsets, idx->k, reads, read_offsets, n_reads, hit_off);
+    grim::seed_hits_kernel<<<grim::fault_grid(blocks), threads, 0, s>>>(
+            idx->offsets, idx->k, reads, read_offsets, n_reads, hit_off);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(hit_off, hit_off, n_reads, 0, s);
 
@@ -853,17 +856,17 @@ int grim_seed_candidates(const grim_seed_index* idx, const uint8_t* reads, const
         const int64_t wb = (nb * 32 + threads - 1) / threads;
         const unsigned bb = (unsigned)(wb < 65535 ? wb : 65535);
         if (votes > 0)
-            grim::seed_expand_kernel<<<grim::fault_grid(bb), threads, 0, s>>>(idx->offsets, idx->positions, idx->k, reads,
-                                                             read_offsets + r0, nb, hit_off + r0, h0,
-                                                             (uint32_t)bin_len, (uint32_t)(n_bins - 1), H);
+            grim::seed_expand_kernel<<<grim::fault_grid(bb), threads, 0, s>>>(
+                    idx->offsets, idx->positions, idx->k, reads, read_offsets + r0, nb, hit_off + r0, h0,
+                    (uint32_t)bin_len, (uint32_t)(n_bins - 1), H);
         grim::seed_dedupe_kernel<<<grim::fault_grid((unsigned)nb), grim::kDedupThreads, grim::kDedupSmemBytes, s>>>(
             hit_off + r0, h0, cap, passes, bits, H, S, kept);
         e = cudaGetLastError();
         // offsets continue from the previous batch's total in cand_offsets[r0]
         if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(kept, cand_offsets + r0, nb, 0, s, cand_offsets + r0);
         if (e == cudaSuccess && rc == GRIM_OK) {
-            grim::seed_copy_kernel<<<grim::fault_grid(bb), threads, 0, s>>>(H, hit_off + r0, h0, cand_offsets + r0, nb, cand_bins,
-                                                          capacity);
+            grim::seed_copy_kernel<<<grim::fault_grid(bb), threads, 0, s>>>(
+                    H, hit_off + r0, h0, cand_offsets + r0, nb, cand_bins, capacity);
             e = cudaGetLastError();
         }
         r0 = r1;
@@ -907,7 +910,8 @@ int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* c
     int64_t* counts = nullptr;
     GRIM_CUDA_TRY(grim::scratch_alloc((void**)&counts, (size_t)(tiles + 1) * 8, s));
     const bool aligned = ((uintptr_t)pass & 15) == 0;
-    grim::locate_count_kernel<<<grim::fault_grid((unsigned)tiles), grim::kScanThreads, 0, s>>>(pass, n_cands, aligned, counts);
+    grim::locate_count_kernel<<<grim::fault_grid((unsigned)tiles), grim::kScanThreads, 0, s>>>(
+            pass, n_cands, aligned, counts);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) rc = grim::exclusive_scan<int64_t>(counts, counts, tiles, 0, s);
     if (e == cudaSuccess && rc == GRIM_OK)
@@ -919,8 +923,8 @@ int grim_locate(const grim_bank* bank, const uint8_t* ref2bit, const uint32_t* c
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && rc == GRIM_OK && segments && capacity > 0) {
-        grim::locate_segments_kernel<<<grim::fault_grid(grim::sm_count() * 8), 256, 0, s>>>(ref2bit, n_loc, capacity, loc_begin,
-                                                                          loc_end, segments, seg_stride);
+        grim::locate_segments_kernel<<<grim::fault_grid(grim::sm_count() * 8), 256, 0, s>>>(
+                ref2bit, n_loc, capacity, loc_begin, loc_end, segments, seg_stride);
         e = cudaGetLastError();
     }
     cudaFreeAsync(counts, s);

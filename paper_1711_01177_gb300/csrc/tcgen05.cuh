@@ -82,8 +82,8 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 // into shared memory, completing bytes on the mbarrier.
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(smem_addr(dst)),
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
         "l"(tmap), "r"(x), "r"(y), "r"(smem_addr(bar))
         : "memory");
 }

@@ -187,15 +187,15 @@ int grim_verify(const grim_bank* bank, const uint8_t* ref2bit, const uint8_t* re
     const int64_t cap = (int64_t)grim::sm_count() * 16;
     const unsigned blocks = (unsigned)(need < cap ? need : cap);
     // reads of up to 128, 129-256 and 257-512 bases
-    grim::verify_kernel<0, 2><<<grim::fault_grid(blocks), 256, 0, s>>>(ref2bit, bank->len, bank->n_bins, bank->bin_len, bank->overlap,
-                                                    reads, read_offsets, n_reads, loc_read, loc_bin, n_loc, dist,
-                                                    bank->status);
-    grim::verify_kernel<3, 4><<<grim::fault_grid(blocks), 256, 0, s>>>(ref2bit, bank->len, bank->n_bins, bank->bin_len, bank->overlap,
-                                                    reads, read_offsets, n_reads, loc_read, loc_bin, n_loc, dist,
-                                                    bank->status);
-    grim::verify_kernel<5, 8><<<grim::fault_grid(blocks), 256, 0, s>>>(ref2bit, bank->len, bank->n_bins, bank->bin_len, bank->overlap,
-                                                    reads, read_offsets, n_reads, loc_read, loc_bin, n_loc, dist,
-                                                    bank->status);
+    grim::verify_kernel<0, 2><<<grim::fault_grid(blocks), 256, 0, s>>>(
+            ref2bit, bank->len, bank->n_bins, bank->bin_len, bank->overlap, reads, read_offsets, n_reads, loc_read,
+            loc_bin, n_loc, dist, bank->status);
+    grim::verify_kernel<3, 4><<<grim::fault_grid(blocks), 256, 0, s>>>(
+            ref2bit, bank->len, bank->n_bins, bank->bin_len, bank->overlap, reads, read_offsets, n_reads, loc_read,
+            loc_bin, n_loc, dist, bank->status);
+    grim::verify_kernel<5, 8><<<grim::fault_grid(blocks), 256, 0, s>>>(
+            ref2bit, bank->len, bank->n_bins, bank->bin_len, bank->overlap, reads, read_offsets, n_reads, loc_read,
+            loc_bin, n_loc, dist, bank->status);
     GRIM_CUDA_TRY(cudaGetLastError());
     return GRIM_OK;
 }
@@ -209,8 +209,8 @@ int grim_verify_stats(const uint8_t* pass, const uint16_t* dist, const uint32_t*
     if (n == 0) return GRIM_OK;
     const int64_t need = (n + 255) / 256;
     const int64_t cap = (int64_t)grim::sm_count() * 8;
-    grim::verify_stats_kernel<<<grim::fault_grid((unsigned)(need < cap ? need : cap)), 256, 0, s>>>(pass, dist, loc_read, E, n_reads,
-                                                                                 n, counts);
+    grim::verify_stats_kernel<<<grim::fault_grid((unsigned)(need < cap ? need : cap)), 256, 0, s>>>(
+            pass, dist, loc_read, E, n_reads, n, counts);
     GRIM_CUDA_TRY(cudaGetLastError());
     return GRIM_OK;
 }

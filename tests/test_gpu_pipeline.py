@@ -72,7 +72,8 @@ def test_map_output_overflow(oracle):
     total = ctypes.c_int64()
     st = grim.load().grim_map(bank.handle, idx.handle, ctypes.c_void_p(r2.data_ptr()),
                               ctypes.c_void_p(b_d.data_ptr()), ctypes.c_void_p(o_d.data_ptr()), 1000,
-                              ctypes.c_void_p(e_d.data_ptr()), 10_000, 300, *[ctypes.c_void_p(t.data_ptr()) for t in out],
+                              ctypes.c_void_p(e_d.data_ptr()), 10_000, 300,
+                              *[ctypes.c_void_p(t.data_ptr()) for t in out],
                               16, ctypes.byref(total), grim._stream_ptr(None), None)
     torch.cuda.synchronize()
     assert st == grim.GRIM_EOVERFLOW and total.value == full.n > 16
