@@ -144,9 +144,10 @@ template <int Q>
 __device__ __forceinline__ void prefetch_row(uint32_t id, const uint32_t* __restrict__ bank, uint32_t n_bins32,
                                              int s) {
     using G = GatherGeo<Q>;
-    if ((s & 7) != 0) return;
-    const uint32_t b = id < n_bins32 ? id : 0u;
-    const uint4* row = reinterpret_cast<const uint4*>(bank) + (size_t)b * G::kRowVecs + s;
+    // past the read's end (or an invalid id) there is nothing to fetch; a
+    // stand-in row would send every warp's requests to the same lines
+    if ((s & 7) != 0 || id >= n_bins32) return;
+    const uint4* row = reinterpret_cast<const uint4*>(bank) + (size_t)id * G::kRowVecs + s;
 #pragma unroll
     for (int u = 0; u < G::kVPL; u++) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + u * G::kLPB));
 }
