@@ -840,7 +840,8 @@ def run_mixed(args, ctx, primary, peaks):
 def q_sweep(args, ctx):
     """Token sizes 4-6 on the same 100 Mbp reads and seed candidates (the
     paper sweeps them in Sec. 6.1): bank size and build time, gather time,
-    checks/s, fraction of HBM and the share of candidates that pass."""
+    checks/s, fraction of HBM and the share of candidates that pass; then
+    bin counts of 3, 6 and 12 x 2^16 at q = 5."""
     import torch
 
     import paper_1711_01177_gb300 as grim
@@ -869,7 +870,42 @@ def q_sweep(args, ctx):
                                "hbm_frac": sig(alg / (avg / 1e3) / 1e9 / hbm, 3),
                                "pass_rate": sig(float(pass_d.float().mean().item()), 3)}
         bank.free()
-    del ins, pass_d, ref_d
+    del pass_d
+    # bin counts as multiples of 2^16 (the paper's banks hold 450 x 2^16
+    # bins, Sec. 6.1): q = 5, the bin length that gives k x 2^16 bins, the
+    # candidates rebuilt for it from the GPU seed table
+    out["bin_count_workload"] = (f"same reads, q=5, overlap {w.overlap} bp, 12-mer seed candidates (cap 1000) "
+                                 f"rebuilt on the GPU for each bin length")
+    out["by_bin_count"] = {}
+    idx = grim.grim_seed_index_build(ref_d, w.ref_len, 12, stream=s)
+    for k in (3, 6, 12):
+        bin_len = -(-w.ref_len // (k << 16))
+        bank = grim.grim_build_bank(ref_d, w.ref_len, 5, bin_len, w.overlap, stream=s)
+        bms, _ = ctx.timed(lambda: grim.grim_build_bank_into(bank, ref_d, stream=s), 2, 1, clocks=False)
+        with torch.cuda.stream(s):
+            cb, co = grim.grim_seed_candidates(idx, ins[0], ins[1], bin_len, bank.n_bins, 1000,
+                                               capacity=w.n_reads * 1000, stream=s)
+        n_checks = int(cb.numel())
+        pd = torch.empty(max(n_checks, 1), dtype=torch.uint8, device="cuda")
+        kins = [ins[0], ins[1], cb, co, ins[4]]
+        ms, _ = ctx.timed(lambda: grim.grim_filter(bank, *kins, pass_out=pd, stream=s), args.sub_steps, 2,
+                          clocks=False)
+        st, flags = grim.grim_bank_status(bank, s)
+        assert st == grim.GRIM_OK, (st, flags)
+        avg = float(np.mean(ms))
+        row = bank.row_words * 4
+        alg = gather_bytes(n_checks, w, row)
+        out["by_bin_count"][f"{k}x2^16"] = {
+            "n_bins": bank.n_bins, "bin_len": bin_len, "bank_bytes": bank.n_bins * row,
+            "bank_build_ms": sig(float(np.median(bms))), "checks": n_checks,
+            "cands_per_read": sig(n_checks / w.n_reads, 3), "ms_per_step": sig(avg),
+            "checks_per_s": sig(n_checks / (avg / 1e3)), "reads_per_s": sig(w.n_reads / (avg / 1e3)),
+            "hbm_frac": sig(alg / (avg / 1e3) / 1e9 / hbm, 3),
+            "pass_rate": sig(float(pd[:n_checks].float().mean().item()), 3)}
+        bank.free()
+        del cb, co, pd, kins
+    idx.free()
+    del ins, ref_d
     torch.cuda.empty_cache()
     return out
 
