@@ -61,6 +61,21 @@ def test_bank_matches_oracle(oracle, q, bin_len, overlap, n):
     bank.free()
 
 
+@pytest.mark.parametrize("bin_len,k", [(19, 1), (16, 2)])
+def test_bank_at_bin_counts_multiple_of_2_16(oracle, bin_len, k):
+    """Banks of exactly k x 2^16 bins (the paper's banks hold 450 x 2^16,
+    Sec. 6.1): a 19-base bin length takes the run-per-CTA build, a 16-base
+    one the lane-per-core build; every row against the oracle."""
+    n = k * (1 << 16) * bin_len
+    codes = synth.ref_with_repeats(n, 77 + k, 0.3, n_fam=20, fam_min=100, fam_max=2000)
+    r2 = synth.pack2bit(codes)
+    bank = gpu_bank(r2, n, 5, bin_len, 150)
+    assert bank.n_bins == k << 16
+    want = pack_rows(oracle.build_bank(r2, n, 5, bin_len, 150), bank.row_words)
+    assert np.array_equal(bank.bits().cpu().numpy().view(np.uint32), want)
+    bank.free()
+
+
 def test_bank_from_unaligned_reference(oracle):
     """A reference buffer that does not start on a 4-byte boundary takes the
     byte-wise build; the rows are the same."""
