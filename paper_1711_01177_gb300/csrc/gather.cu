@@ -208,6 +208,26 @@ struct StepReducer {
         }
         total = v;
     }
+    // The same for a window run as passes of P unrolled steps: step
+    // h * P + tl, tl a constant, h the pass (only the levels above log2 P
+    // look at it, and only at a pass's last step).
+    template <int P>
+    __device__ __forceinline__ void add_split(int tl, int h, uint32_t v, int s) {
+        constexpr int kPassLevels = P >= 16 ? 4 : P >= 8 ? 3 : P >= 4 ? 2 : P >= 2 ? 1 : 0;
+#pragma unroll
+        for (int l = 0; l < kLevels; l++) {
+            const int bit = l < kPassLevels ? ((tl >> l) & 1) : ((h >> (l - kPassLevels)) & 1);
+            if (bit == 0) {
+                stk[l] = v;
+                return;
+            }
+            const uint32_t lo = stk[l], hi = v;
+            const bool upper = (s >> l) & 1;
+            const uint32_t send = upper ? lo : hi;
+            v = (upper ? hi : lo) + __shfl_xor_sync(kFull, send, 1 << l);
+        }
+        total = v;
+    }
 };
 
 // Score the read's candidates.  NP > 0: NP planes held in registers;
@@ -233,8 +253,15 @@ __device__ __forceinline__ void score_read(Stream<Q, DEEP>& st, const uint4* __r
     for (int w0 = 0; w0 < n; w0 += 32) {
         const uint32_t win_after = window_id(cands, w0 + 64 + lane, n);  // two windows ahead
         StepReducer<S::kWinSteps> red;
+        // 16-step windows (q = 6) run as two passes of one unrolled 8-step
+        // body: half the code of the scoring loop, for the instruction cache
+        constexpr int kPass = S::kWinSteps >= 16 ? 8 : S::kWinSteps;
+        static_assert(kPass % S::kBufs == 0, "register buffers must rotate within a pass");
+#pragma unroll 1
+        for (int h = 0; h < S::kWinSteps / kPass; h++) {
 #pragma unroll
-        for (int t = 0; t < S::kWinSteps; t++) {
+        for (int tl = 0; tl < kPass; tl++) {
+            const int t = h * kPass + tl;
             const int c0 = w0 + t * G::kBPS;
             uint32_t part = 0;
             if (c0 < n) {  // warp-uniform
@@ -244,7 +271,7 @@ __device__ __forceinline__ void score_read(Stream<Q, DEEP>& st, const uint4* __r
                     const int idx = (ahead % S::kWinSteps) * G::kBPS + g;
                     const uint32_t src = ahead < S::kWinSteps ? st.win_cur : st.win_next;
                     const uint32_t id = __shfl_sync(kFull, src, idx);
-                    fetch_row<Q>(st.r[(t + S::kAhead) % S::kBufs], id, bank, n_bins32, s);
+                    fetch_row<Q>(st.r[(tl + S::kAhead) % S::kBufs], id, bank, n_bins32, s);
                 }
                 if constexpr (S::kPrefetch > 0) {
                     const int ahead = t + S::kPrefetch;
@@ -254,7 +281,7 @@ __device__ __forceinline__ void score_read(Stream<Q, DEEP>& st, const uint4* __r
                     prefetch_row<Q>(id, bank, n_bins32, s);
                 }
                 // score this step's rows
-                const uint4 (&v)[G::kVPL] = st.r[t % S::kBufs];
+                const uint4 (&v)[G::kVPL] = st.r[tl % S::kBufs];
                 if constexpr (NP > 0 && NP <= 2 && Q >= 6 && G::kVPL == 2) {
                     part = row_sum_csa<NP>(v, pl);
                 } else if (NP > 0) {
@@ -275,7 +302,9 @@ __device__ __forceinline__ void score_read(Stream<Q, DEEP>& st, const uint4* __r
                     }
                 }
             }
-            red.add(t, part, s);
+            if constexpr (kPass == S::kWinSteps) red.add(t, part, s);
+            else red.template add_split<kPass>(tl, h, part, s);
+        }
         }
         // this lane's row: step s, group g
         const int j = s * G::kBPS + g;
