@@ -59,17 +59,17 @@ SUMMARY_KEY = {"plain": "1_plain_1Mbp", "gather": "2_gather_100Mbp", "fullscan":
 # {source hash: {form: {"bytes": per launch, "reads": reads per launch,
 #                       "checks": checks of the launch where it is scaled by checks}}}
 TRAFFIC_BY_SOURCE: dict[str, dict] = {
-    "c4a935581dff4968": {
+    "1577e08671b4a735": {
         # gather_kernel<5,4,DEEP>, one 262,144-read batch of the 3.1 Gbp dispatcher
-        # workload, 438,575,706 checks: 54,620,761,344 B read + 446,145,792 B written
-        "mixed": {"bytes": 55_066_907_136, "reads": 262_144, "checks": 438_575_706},
-        # gather_kernel<5,8>, 100 Mbp, 1M reads, 74.8M checks: 655,237,120 B read + 71,795,712 B written
-        "gather": {"bytes": 727_032_832, "reads": 1_000_000},
-        # gather_kernel<5,8>, 1 Mbp, 10,000 reads, 320,000 checks: 3,017,728 B read, the output stays in L2
-        "plain": {"bytes": 3_017_728, "reads": 10_000},
+        # workload, 438,575,706 checks: 54,668,177,664 B read + 440,018,176 B written
+        "mixed": {"bytes": 55_108_195_840, "reads": 262_144, "checks": 438_575_706},
+        # gather_kernel<5,8>, 100 Mbp, 1M reads, 74.8M checks: 655,405,568 B read + 71,852,544 B written
+        "gather": {"bytes": 727_258_112, "reads": 1_000_000},
+        # gather_kernel<5,8>, 1 Mbp, 10,000 reads, 320,000 checks: 3,017,216 B read, the output stays in L2
+        "plain": {"bytes": 3_017_216, "reads": 10_000},
         # gather_kernel<6,8>, one 262,144-read batch of the q=6 workload, 153,942,833 checks:
-        # 47,251,119,872 B read + 163,791,616 B written
-        "batched": {"bytes": 47_414_911_488, "reads": 262_144, "checks": 153_942_833},
+        # 47,292,314,112 B read + 163,915,776 B written
+        "batched": {"bytes": 47_456_229_888, "reads": 262_144, "checks": 153_942_833},
     },
 }
 
